@@ -1,0 +1,240 @@
+/*
+ * t3f.h -- C ABI of the GB300 (sm_103a) Tensor-Train sweep library.
+ *
+ * The library computes the batched, core-by-core transfer-matrix sweeps of the T3F method
+ * (Novikov et al., "Tensor Train decomposition on TensorFlow", JMLR 2020) on one GPU:
+ * inner products / Gram matrices / norms, element gather with the completion loss,
+ * TT-matrix x TT-vector, Householder orthogonalisation and the Riemannian tangent-space
+ * projection project_sum, each with a hand-written adjoint.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - TT format (paper, Section 1): core k of a TT-vector has shape (r_{k-1}, n_k, r_k),
+ *    of a TT-matrix (r_{k-1}, m_k, n_k, r_k), with r_0 = r_d = 1; indices are 0-based.
+ *  - Batch layout ("packed"): a t3f_tt describes `batch` objects of identical shape whose
+ *    cores live in ONE device buffer. Core k of all objects forms a contiguous block of
+ *    batch * r_{k-1} * m_k * n_k * r_k elements (m_k = 1 for TT-vectors), row-major in
+ *    [batch][r_{k-1}][m_k][n_k][r_k]; the blocks follow each other for k = 0..d-1 with no
+ *    padding. t3f_packed_size() gives the element count.
+ *  - Ownership: the caller owns every device buffer (inputs, outputs, workspace). The
+ *    library allocates nothing and keeps no state between calls. Host arrays inside a
+ *    descriptor (n, m, ranks) are read during the call only.
+ *  - Streams: all device work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream). Calls are asynchronous; a returned status reports argument checks
+ *    and launch errors only. Outputs are overwritten, never accumulated.
+ *  - Workspace: t3f_workspace_size() returns the bytes an operation needs for the given
+ *    descriptors; a smaller `ws_bytes` returns T3F_ERR_WORKSPACE before any launch. The
+ *    workspace must be 256-byte aligned.
+ *  - Errors: every entry point validates its descriptors (NULL pointers, d range, rank
+ *    boundary conditions, shape agreement, dtype) and returns a negative t3f_status without
+ *    launching anything when a check fails. t3f_status_string() names a status.
+ *  - Precision: storage dtype is per descriptor. The sweeps accumulate in FP32; the QR of
+ *    t3f_orthogonalize and the final norm / loss reductions run in FP64.
+ */
+#ifndef T3F_H
+#define T3F_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* t3f_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  T3F_OK = 0,
+  T3F_ERR_ARG = -1,         /* NULL pointer, negative size, d out of range, bad enum */
+  T3F_ERR_SHAPE = -2,       /* ranks/modes/batches of the operands disagree */
+  T3F_ERR_DTYPE = -3,       /* storage type not supported by this entry point */
+  T3F_ERR_WORKSPACE = -4,   /* ws_bytes below t3f_workspace_size() or misaligned ws */
+  T3F_ERR_CUDA = -5,        /* a CUDA launch or runtime call failed */
+  T3F_ERR_TIMEOUT = -6,     /* a bounded device-side wait ran out (see t3f_device_status) */
+  T3F_ERR_UNSUPPORTED = -7  /* valid request beyond this build's kernel limits (e.g. rank) */
+} t3f_status;
+
+typedef enum { T3F_F32 = 0, T3F_F64 = 1, T3F_BF16 = 2 } t3f_dtype;
+
+/* Arithmetic of the bulk sweeps: FP32 CUDA cores, or tensor cores with FP32 accumulation. */
+typedef enum { T3F_MATH_FP32 = 0, T3F_MATH_TF32 = 1, T3F_MATH_BF16 = 2 } t3f_math;
+
+#define T3F_MAX_D 64      /* maximum number of cores */
+#define T3F_MAX_RANK 64   /* maximum TT-rank handled by the sweep kernels */
+#define T3F_MAX_MODE 4096 /* maximum mode size n_k (and m_k) */
+
+/* A batch of TT-vectors (m == NULL) or TT-matrices (m != NULL) of one shape. */
+typedef struct {
+  int32_t batch;          /* number of objects, >= 1 */
+  int32_t d;              /* number of cores, 1 <= d <= T3F_MAX_D */
+  const int32_t* m;       /* host [d] row modes of a TT-matrix, or NULL for a TT-vector */
+  const int32_t* n;       /* host [d] (column) modes, each in [1, T3F_MAX_MODE] */
+  const int32_t* ranks;   /* host [d+1] TT-ranks, ranks[0] = ranks[d] = 1 */
+  void* cores;            /* device pointer to the packed cores (layout above) */
+  int32_t dtype;          /* t3f_dtype of the cores */
+} t3f_tt;
+
+/* Operation ids for t3f_workspace_size(). */
+typedef enum {
+  T3F_OP_GRAM = 1, T3F_OP_GRAM_BWD = 2, T3F_OP_NORM = 3,
+  T3F_OP_GATHER = 4, T3F_OP_GATHER_BWD = 5, T3F_OP_RGATHER_BWD = 6,
+  T3F_OP_MATVEC = 7, T3F_OP_MATVEC_BWD = 8,
+  T3F_OP_ORTH = 9, T3F_OP_PSUM = 10, T3F_OP_PSUM_BWD = 11
+} t3f_op;
+
+/* Name of a status code (static string). */
+const char* t3f_status_string(int32_t status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t t3f_version(void);
+
+/* Number of elements of the packed cores of `t` (0 if the descriptor is invalid). */
+int64_t t3f_packed_size(const t3f_tt* t);
+
+/*
+ * Workspace bytes for operation `op`:
+ *   GRAM, GRAM_BWD: a = A, b = B.          NORM: a = A, b unused.
+ *   GATHER, GATHER_BWD: a = X, n_items = N tuples.
+ *   RGATHER_BWD: a = U (left-orthogonal form), b = V, n_items = N.
+ *   MATVEC, MATVEC_BWD: a = A (TT-matrix), b = x.
+ *   ORTH: a = X.    PSUM, PSUM_BWD: a = U, b = Z (the batch being projected).
+ * Returns 0 for an invalid request (check with the call itself for the status).
+ */
+size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* b, int64_t n_items);
+
+/*
+ * Gram matrix (paper Section 4, 'gram'; batch broadcasting of Section 3.1):
+ * G[a * B->batch + b] = <A_a, B_b> = sum over all elements of full(A_a) * full(B_b),
+ * computed by the left transfer sweep M_0 = 1, M_k = sum_i A_k[:,i,:]^T M_{k-1} B_k[:,i,:].
+ * A, B: TT-vectors with equal d and n_k (else T3F_ERR_SHAPE); F32 or BF16 cores; ranks may
+ * differ between A and B. G: device float [A->batch][B->batch]. math: t3f_math.
+ */
+t3f_status t3f_gram(const t3f_tt* A, const t3f_tt* B, float* G, int32_t math,
+                    void* ws, size_t ws_bytes, t3f_stream_t stream);
+
+/*
+ * Frobenius norms (paper Section 4, 'norm'): out[a] = sqrt(<A_a, A_a>) in FP64.
+ * out: device double [A->batch].
+ */
+t3f_status t3f_norm(const t3f_tt* A, double* out, void* ws, size_t ws_bytes,
+                    t3f_stream_t stream);
+
+/*
+ * Adjoint of t3f_gram: given dG (device float [A->batch][B->batch]), writes the cotangents
+ * of sum_ab dG[a,b] <A_a, B_b>:
+ *   dA_a^k[:,i,:] = sum_b dG[a,b] M^{ab}_{k-1} B_b^k[:,i,:] (R^{ab}_{k+1})^T,
+ *   dB_b^k[:,i,:] = sum_a dG[a,b] (M^{ab}_{k-1})^T A_a^k[:,i,:] R^{ab}_{k+1},
+ * with R the right transfer sweep. The left partials are recomputed inside (nothing is kept
+ * from the forward call). dA, dB: F32 descriptors with the shapes of A and B. Either may be
+ * NULL to skip it.
+ */
+t3f_status t3f_gram_backward(const t3f_tt* A, const t3f_tt* B, const float* dG,
+                             t3f_tt* dA, t3f_tt* dB, void* ws, size_t ws_bytes,
+                             t3f_stream_t stream);
+
+/*
+ * Element gather (paper Section 1, completion example): for N index tuples
+ * idx (device int32, layout [d][N]), vals[t] = X(idx[0][t], ..., idx[d-1][t]) for the
+ * single TT X (X->batch must be 1, F32 cores). Indices out of [0, n_k) give T3F_ERR_ARG
+ * only if detected on the host; on the device they are clamped into range and counted in
+ * the workspace error word (t3f_device_status).
+ * y: device float [N] or NULL. vals: device float [N] or NULL. loss: device double [1] or
+ * NULL; when given, loss = 1/2 sum_t (vals_t - y_t)^2 (y required).
+ */
+t3f_status t3f_gather(const t3f_tt* X, const int32_t* idx, int64_t N, const float* y,
+                      float* vals, double* loss, void* ws, size_t ws_bytes,
+                      t3f_stream_t stream);
+
+/*
+ * Adjoint of the gather (paper Section 3.2, Riemannian autodiff, for the completion loss).
+ * Weights: w (device float [N]) if non-NULL, else the residual w_t = X(i_t) - y_t (y
+ * required; loss, if non-NULL, receives 1/2 sum w_t^2 in FP64).
+ *  riemannian == 0: dX (F32, shape of X) = cotangent of sum_t w_t X(i_t):
+ *      dX^k[:,i,:] = sum_{t: i_{t,k}=i} w_t l_{t,k-1} (outer) rho_{t,k+1}
+ *    (l = prefix row through X's cores, rho = suffix column).
+ *  riemannian == 1: X is ignored (may be NULL); U, V are the left-/right-orthogonal forms
+ *    from t3f_orthogonalize; X(i_t) is evaluated from V. dX (F32, ranks of U) receives the
+ *    tangent coordinates dU_k of P_X(sum_t w_t e_{i_t}): the same scatter with U-prefixes
+ *    and V-suffixes, followed by the gauge projection dU_k <- (I - U_k U_k^T) dU_k (k < d).
+ */
+t3f_status t3f_gather_backward(const t3f_tt* X, const int32_t* idx, int64_t N,
+                               const float* w, const float* y, double* loss, t3f_tt* dX,
+                               int32_t riemannian, const t3f_tt* U, const t3f_tt* V,
+                               void* ws, size_t ws_bytes, t3f_stream_t stream);
+
+/*
+ * TT-matrix by TT-vector (paper Section 4, 'matvec'): zip over the batch (C_p = A_p x_p),
+ * a batch of 1 on either side broadcasts (Section 3.1). No rounding:
+ *   C^k[(a*r_x+b), i, (a'*r_x+b')] = sum_j A^k[a,i,j,a'] x^k[b,j,b'],
+ * so C has ranks r^A_k * r^x_k and modes m_k. A: TT-matrix (m != NULL), x: TT-vector with
+ * n_k equal to A's column modes; C: F32 TT-vector descriptor of the product's shape.
+ */
+t3f_status t3f_matvec(const t3f_tt* A, const t3f_tt* x, t3f_tt* C, void* ws,
+                      size_t ws_bytes, t3f_stream_t stream);
+
+/* Adjoint of t3f_matvec: dA^k[a,i,j,a'] = sum_{b,b'} dC^k[(a,b),i,(a',b')] x^k[b,j,b'],
+ * dx^k[b,j,b'] = sum_{a,a',i} dC^k[(a,b),i,(a',b')] A^k[a,i,j,a'] (summed over the batch on
+ * a broadcast side). dA or dx may be NULL. */
+t3f_status t3f_matvec_backward(const t3f_tt* A, const t3f_tt* x, const t3f_tt* dC,
+                               t3f_tt* dA, t3f_tt* dx, void* ws, size_t ws_bytes,
+                               t3f_stream_t stream);
+
+/*
+ * Ranks after orthogonalisation (host only, integer bookkeeping): right-to-left
+ * r'_{k-1} = min(r_{k-1}, n_k r'_k), then left-to-right r''_k = min(r''_{k-1} n_k, r'_k).
+ * out_ranks: host [d+1].
+ */
+t3f_status t3f_orth_ranks(int32_t d, const int32_t* n, const int32_t* ranks,
+                          int32_t* out_ranks);
+
+/*
+ * Orthogonal forms of X for the tangent space of the fixed-rank manifold (paper
+ * Section 3.2): three Householder sweeps in FP64 (right-to-left on X, left-to-right on the
+ * result giving U, right-to-left on U giving V), every QR normalised to diag(R) >= 0.
+ * U_1..U_{d-1} are left-orthogonal ((r_{k-1} n_k) x r_k unfoldings with orthonormal
+ * columns), U_d carries X; V_2..V_d are right-orthogonal, V_1 carries X; full(U) = full(V)
+ * = full(X). X: F32 or F64 cores, any batch. U, V: F32 or F64 descriptors of the same
+ * batch with ranks t3f_orth_ranks(X). Ranks up to T3F_MAX_RANK, r_{k-1} n_k <= 4096.
+ */
+t3f_status t3f_orthogonalize(const t3f_tt* X, t3f_tt* U, t3f_tt* V, void* ws,
+                             size_t ws_bytes, t3f_stream_t stream);
+
+/*
+ * project_sum (paper Section 3.2): tangent coordinates dU of S = P_X(sum_j c_j Z_j),
+ * computed as sum_j c_j P_X Z_j:
+ *   Zhat_k[:,i,:] = sum_j c_j L^{(j)}_{k-1} Z_j^k[:,i,:] (R^{(j)}_{k+1})^T,
+ *   L^{(j)} = left partials of (U, Z_j), R^{(j)} = right partials of (V, Z_j),
+ *   dU_k = (I - U_k U_k^T) Zhat_k for k < d (left unfoldings), dU_d = Zhat_d.
+ * U, V: F32 orthogonal forms (batch 1); Z: F32 batch with the modes of U; c: device float
+ * [Z->batch]; dU: F32 descriptor with U's shape. With Z->batch = 1 and c = 1 this is the
+ * projection P_X Z ('project' in Table 1). The TT of S has cores [dU_1, U_1],
+ * [[V_k, 0], [dU_k, U_k]], [[V_d], [dU_d]] (ranks <= 2 r).
+ */
+t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3f_tt* Z,
+                           const float* c, t3f_tt* dU, int32_t math, void* ws,
+                           size_t ws_bytes, t3f_stream_t stream);
+
+/*
+ * Adjoint of t3f_project_sum with X (U, V) held fixed: given dUbar (F32, U's shape), the
+ * cotangent of phi = sum_k <dUbar_k, dU_k>. With W = gauge projection of dUbar and T_W the
+ * rank-2r TT of (U, V, W): dc[j] = <T_W, Z_j>, dZ_j = c_j d<T_W, Z_j>/dZ_j. The partial
+ * products are recomputed, not taken from the forward call. dZ (F32, Z's shape) or dc
+ * (device float [Z->batch]) may be NULL.
+ */
+t3f_status t3f_project_sum_backward(const t3f_tt* U, const t3f_tt* V, const t3f_tt* Z,
+                                    const float* c, const t3f_tt* dUbar, t3f_tt* dZ,
+                                    float* dc, void* ws, size_t ws_bytes,
+                                    t3f_stream_t stream);
+
+/*
+ * Device-side error word of the last call that used `ws` (enqueued on `stream`, read after
+ * a synchronisation): 0 = none, T3F_ERR_ARG = an index tuple was out of range,
+ * T3F_ERR_TIMEOUT = a bounded wait ran out. Synchronises `stream`.
+ */
+t3f_status t3f_device_status(const void* ws, t3f_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* T3F_H */

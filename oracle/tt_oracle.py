@@ -132,7 +132,7 @@ def left_partials(A, B):
     A, B = _as_list(A), _as_list(B)
     M = [np.ones((1, 1))]
     for a, b in zip(A, B):
-        M.append(np.einsum("aib,ac,cid->bd", a, M[-1], b))
+        M.append(np.einsum("aib,ac,cid->bd", a, M[-1], b, optimize=True))
     return M
 
 
@@ -145,7 +145,7 @@ def right_partials(A, B):
     R = [None] * (d + 2)
     R[d + 1] = np.ones((1, 1))
     for k in range(d, 0, -1):
-        R[k] = np.einsum("aib,bd,cid->ac", A[k - 1], R[k + 1], B[k - 1])
+        R[k] = np.einsum("aib,bd,cid->ac", A[k - 1], R[k + 1], B[k - 1], optimize=True)
     return R
 
 
@@ -184,8 +184,8 @@ def gram_vjp(As, Bs, Gbar):
             M = left_partials(A, B)
             R = right_partials(A, B)
             for k in range(len(A)):
-                dAs[a][k] += g * np.einsum("ac,cid,bd->aib", M[k], np.asarray(B[k], float), R[k + 2])
-                dBs[b][k] += g * np.einsum("ac,aib,bd->cid", M[k], np.asarray(A[k], float), R[k + 2])
+                dAs[a][k] += g * np.einsum("ac,cid,bd->aib", M[k], np.asarray(B[k], float), R[k + 2], optimize=True)
+                dBs[b][k] += g * np.einsum("ac,aib,bd->cid", M[k], np.asarray(A[k], float), R[k + 2], optimize=True)
     return dAs, dBs
 
 
@@ -217,6 +217,15 @@ def _suffixes(cores, idx):
     return rs
 
 
+def _scatter_outer(w, left, right, ik, shape):
+    """g[:, i, :] = sum over the tuples t with ik[t] = i of w_t left_t (outer) right_t."""
+    g = np.zeros(shape)
+    for i in range(shape[1]):
+        sel = ik == i
+        g[:, i, :] = (w[sel][:, None] * left[sel]).T @ right[sel]
+    return g
+
+
 def gather(cores, idx) -> np.ndarray:
     """X(i_t) for index tuples idx of shape (d, N)."""
     cores = _as_list(cores)
@@ -232,13 +241,7 @@ def gather_vjp(cores, idx, w):
     w = np.asarray(w, dtype=np.float64)
     ls = _prefixes(cores, idx)
     rs = _suffixes(cores, idx)
-    grads = []
-    for k, G in enumerate(cores):
-        g = np.zeros_like(G)
-        outer = w[:, None, None] * ls[k][:, :, None] * rs[k + 2][:, None, :]
-        np.add.at(g.transpose(1, 0, 2), idx[k], outer)
-        grads.append(g)
-    return grads
+    return [_scatter_outer(w, ls[k], rs[k + 2], idx[k], G.shape) for k, G in enumerate(cores)]
 
 
 def completion_loss(cores, idx, y) -> float:
@@ -355,7 +358,7 @@ def tangent_coords(U, V, Z):
     d = len(Z)
     L = left_partials(U, Z)          # L[k] : r_k x s_k
     R = right_partials(V, Z)         # R[k] : r_{k-1} x s_{k-1}
-    return [np.einsum("ac,cid,bd->aib", L[k], Z[k], R[k + 2]) for k in range(d)]
+    return [np.einsum("ac,cid,bd->aib", L[k], Z[k], R[k + 2], optimize=True) for k in range(d)]
 
 
 def gauge_project(U, Zhat):
@@ -427,25 +430,25 @@ def project_sum_vjp(U, V, Zs, c, dUbar):
         # P_k = sum_i V_k^T P_{k-1} Z_k + W_k^T L_{k-1} Z_k, P_0 = 0
         P = [np.zeros((1, 1))]
         for k in range(d):
-            nxt = np.einsum("aib,ac,cid->bd", W[k], L[k], Z[k])
+            nxt = np.einsum("aib,ac,cid->bd", W[k], L[k], Z[k], optimize=True)
             if k > 0:
-                nxt = nxt + np.einsum("aib,ac,cid->bd", V[k], P[k], Z[k])
+                nxt = nxt + np.einsum("aib,ac,cid->bd", V[k], P[k], Z[k], optimize=True)
             P.append(nxt)
         # Q_k = sum_i U_k Q_{k+1} Z_k^T + W_k R_{k+1} Z_k^T, Q_{d+1} = 0
         Q = [None] * (d + 2)
         Q[d + 1] = np.zeros((1, 1))
         for k in range(d, 0, -1):
-            nxt = np.einsum("aib,bd,cid->ac", W[k - 1], R[k + 1], Z[k - 1])
+            nxt = np.einsum("aib,bd,cid->ac", W[k - 1], R[k + 1], Z[k - 1], optimize=True)
             if k < d:
-                nxt = nxt + np.einsum("aib,bd,cid->ac", U[k - 1], Q[k + 1], Z[k - 1])
+                nxt = nxt + np.einsum("aib,bd,cid->ac", U[k - 1], Q[k + 1], Z[k - 1], optimize=True)
             Q[k] = nxt
         dZ = []
         for k in range(d):
-            g = np.einsum("ac,aib,bd->cid", L[k], W[k], R[k + 2])
+            g = np.einsum("ac,aib,bd->cid", L[k], W[k], R[k + 2], optimize=True)
             if k > 0:
-                g = g + np.einsum("ac,aib,bd->cid", P[k], V[k], R[k + 2])
+                g = g + np.einsum("ac,aib,bd->cid", P[k], V[k], R[k + 2], optimize=True)
             if k < d - 1:
-                g = g + np.einsum("ac,aib,bd->cid", L[k], U[k], Q[k + 2])
+                g = g + np.einsum("ac,aib,bd->cid", L[k], U[k], Q[k + 2], optimize=True)
             dZ.append(ci * g)
         dZs.append(dZ)
         dc.append(float(P[d][0, 0]))
@@ -462,12 +465,8 @@ def riemannian_grad_completion(U, V, idx, y):
     res = gather(U, idx) - np.asarray(y, dtype=np.float64)
     ls = _prefixes(U, idx)
     rs = _suffixes(V, idx)
-    Zhat = []
-    for k in range(len(U)):
-        g = np.zeros((U[k].shape[0], U[k].shape[1], V[k].shape[2]))
-        outer = res[:, None, None] * ls[k][:, :, None] * rs[k + 2][:, None, :]
-        np.add.at(g.transpose(1, 0, 2), idx[k], outer)
-        Zhat.append(g)
+    Zhat = [_scatter_outer(res, ls[k], rs[k + 2], idx[k],
+                           (U[k].shape[0], U[k].shape[1], V[k].shape[2])) for k in range(len(U))]
     return float(0.5 * np.sum(res * res)), gauge_project(U, Zhat)
 
 

@@ -1,0 +1,13 @@
+"""GB300-native (sm_103a) Tensor-Train sweep library: the data-parallel hot path of T3F
+(Novikov et al., JMLR 2020) -- Gram matrices and norms, element gather with the completion
+loss, TT-matrix x TT-vector, FP64 orthogonalisation and the Riemannian project_sum, each with
+a hand-written adjoint -- behind the C ABI of include/t3f.h.
+
+The Python layer is argument marshalling over libt3f.so; import fails loudly at call time if
+the library has not been built (``python -m paper_1801_01928_gb300.build``).
+"""
+from ._binding import (  # noqa: F401
+    BF16, EXPORTS, F32, F64, LIB_PATH, T3FError, TT, device_status, gather, gather_backward,
+    gram, gram_backward, load, matvec, matvec_backward, norm, orth_ranks, orthogonalize,
+    project_sum, project_sum_backward,
+)

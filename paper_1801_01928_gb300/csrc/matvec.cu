@@ -1,0 +1,235 @@
+// TT-matrix by TT-vector product without rounding (paper Section 4 'matvec'; zip batches
+// with broadcasting, Section 3.1) and its adjoint.
+//
+//   C^k[(a r_x + b), i, (a' r_x + b')] = sum_j A^k[a, i, j, a'] x^k[b, j, b']
+//
+// One CTA per (pair, core): both cores are staged in shared memory and the product core is
+// streamed out row by row; for a fixed output row (a, b) the (i, a', b') block is
+// contiguous, so consecutive threads write consecutive addresses.
+#include "t3f_internal.cuh"
+
+namespace t3f {
+
+struct MatvecArgs {
+  TTV A, x, C;
+  int bA, bx, P;       // batches; P = number of products
+  int maxA, maxX;      // staged floats per core (max over k)
+};
+
+__global__ void __launch_bounds__(256) k_matvec(const __grid_constant__ MatvecArgs a) {
+  extern __shared__ float sm[];
+  const int p = blockIdx.x / a.A.d, k = blockIdx.x % a.A.d;
+  const TTV& A = a.A;
+  const TTV& X = a.x;
+  const int ra0 = A.r[k], ra1 = A.r[k + 1], rx0 = X.r[k], rx1 = X.r[k + 1];
+  const int m = A.m[k], n = A.n[k];
+  float* As = sm;             // [ra0][m][n][ra1]
+  float* Xs = sm + a.maxA;    // [rx0][n][rx1]
+  const float* Ap = static_cast<const float*>(A.p) + core_base(A, k, a.bA == 1 ? 0 : p);
+  const float* Xp = static_cast<const float*>(X.p) + core_base(X, k, a.bx == 1 ? 0 : p);
+  const int sa = ra0 * m * n * ra1, sx = rx0 * n * rx1;
+  for (int e = threadIdx.x; e < sa; e += blockDim.x) As[e] = __ldg(Ap + e);
+  for (int e = threadIdx.x; e < sx; e += blockDim.x) Xs[e] = __ldg(Xp + e);
+  __syncthreads();
+  float* Cp = static_cast<float*>(a.C.p) + core_base(a.C, k, p);
+  const int rowlen = m * ra1 * rx1;            // contiguous (i, a', b') block of one row
+  const int nrows = ra0 * rx0;
+  const long long total = (long long)nrows * rowlen;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+    const int row = (int)(e / rowlen), q = (int)(e % rowlen);
+    const int al = row / rx0, be = row % rx0;
+    const int i = q / (ra1 * rx1), c1 = q % (ra1 * rx1);
+    const int ap = c1 / rx1, bp = c1 % rx1;
+    const float* Ar = As + ((al * m + i) * n) * ra1 + ap;  // A[al, i, j, ap] at j * ra1
+    const float* Xr = Xs + (be * n) * rx1 + bp;            // x[be, j, bp] at j * rx1
+    float s = 0.0f;
+    for (int j = 0; j < n; ++j) s = fmaf(Ar[j * ra1], Xr[j * rx1], s);
+    Cp[e] = s;
+  }
+}
+
+// Adjoint: one CTA per (pair, core). Rows a of dC are staged in shared memory in turn.
+struct MatvecBwdArgs {
+  TTV A, x, dC;
+  int bA, bx, P;
+  int maxA, maxX, maxRow;
+  float* dA;   // packed like A, nullable
+  float* dx;   // packed like x, nullable
+  int atomicA, atomicX;  // a broadcast side sums over the batch with atomics
+};
+
+__global__ void __launch_bounds__(256) k_matvec_bwd(const __grid_constant__ MatvecBwdArgs a) {
+  extern __shared__ float sm[];
+  const int p = blockIdx.x / a.A.d, k = blockIdx.x % a.A.d;
+  const TTV& A = a.A;
+  const TTV& X = a.x;
+  const int ra0 = A.r[k], ra1 = A.r[k + 1], rx0 = X.r[k], rx1 = X.r[k + 1];
+  const int m = A.m[k], n = A.n[k];
+  float* As = sm;                     // [ra0][m][n][ra1]
+  float* Xs = As + a.maxA;            // [rx0][n][rx1]
+  float* Gs = Xs + a.maxX;            // one dC row block a: [rx0][m][ra1][rx1]
+  float* dXs = Gs + a.maxRow;         // [rx0][n][rx1] accumulator
+  const int oa = a.bA == 1 ? 0 : p, ox = a.bx == 1 ? 0 : p;
+  const float* Ap = static_cast<const float*>(A.p) + core_base(A, k, oa);
+  const float* Xp = static_cast<const float*>(X.p) + core_base(X, k, ox);
+  const float* Gp = static_cast<const float*>(a.dC.p) + core_base(a.dC, k, p);
+  const int sa = ra0 * m * n * ra1, sx = rx0 * n * rx1;
+  for (int e = threadIdx.x; e < sa; e += blockDim.x) As[e] = __ldg(Ap + e);
+  for (int e = threadIdx.x; e < sx; e += blockDim.x) {
+    Xs[e] = __ldg(Xp + e);
+    dXs[e] = 0.0f;
+  }
+  const int rowlen = m * ra1 * rx1;
+  const int blk = rx0 * rowlen;  // rows (al, 0..rx0-1) are contiguous in dC
+  for (int al = 0; al < ra0; ++al) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < blk; e += blockDim.x) Gs[e] = __ldg(Gp + (long long)al * blk + e);
+    __syncthreads();
+    if (a.dA) {
+      // dA[al, i, j, ap] = sum_{b, bp} G[b][i][ap][bp] x[b][j][bp]
+      float* dAp = a.dA + core_base(A, k, oa);
+      for (int e = threadIdx.x; e < m * n * ra1; e += blockDim.x) {
+        const int ap = e % ra1, j = (e / ra1) % n, i = e / (ra1 * n);
+        float s = 0.0f;
+        for (int be = 0; be < rx0; ++be) {
+          const float* g = Gs + ((be * m + i) * ra1 + ap) * rx1;
+          const float* xv = Xs + (be * n + j) * rx1;
+          for (int bp = 0; bp < rx1; ++bp) s = fmaf(g[bp], xv[bp], s);
+        }
+        float* dst = dAp + ((al * m + i) * n + j) * ra1 + ap;
+        if (a.atomicA) atomicAdd(dst, s); else *dst = s;
+      }
+    }
+    if (a.dx) {
+      // dx[b, j, bp] += sum_{i, ap} G[b][i][ap][bp] A[al, i, j, ap]
+      for (int e = threadIdx.x; e < sx; e += blockDim.x) {
+        const int bp = e % rx1, j = (e / rx1) % n, be = e / (rx1 * n);
+        float s = 0.0f;
+        for (int i = 0; i < m; ++i) {
+          const float* g = Gs + ((be * m + i) * ra1) * rx1 + bp;
+          const float* av = As + ((al * m + i) * n + j) * ra1;
+          for (int ap = 0; ap < ra1; ++ap) s = fmaf(g[ap * rx1], av[ap], s);
+        }
+        dXs[e] += s;
+      }
+    }
+  }
+  if (a.dx) {
+    float* dXp = a.dx + core_base(X, k, ox);
+    for (int e = threadIdx.x; e < sx; e += blockDim.x) {
+      if (a.atomicX) atomicAdd(dXp + e, dXs[e]); else dXp[e] = dXs[e];
+    }
+  }
+}
+
+static t3f_status matvec_views(const t3f_tt* A, const t3f_tt* x, TTV* va, TTV* vx, int* P) {
+  T3F_CHECK(make_view(A, va, T3F_F32, true));
+  T3F_CHECK(make_view(x, vx, T3F_F32, false));
+  if (va->d != vx->d) return T3F_ERR_SHAPE;
+  for (int k = 0; k < va->d; ++k)
+    if (va->n[k] != vx->n[k]) return T3F_ERR_SHAPE;
+  if (va->batch != vx->batch && va->batch != 1 && vx->batch != 1) return T3F_ERR_SHAPE;
+  *P = va->batch > vx->batch ? va->batch : vx->batch;
+  return T3F_OK;
+}
+
+static t3f_status check_product(const TTV& A, const TTV& X, int P, const t3f_tt* C, TTV* vc) {
+  T3F_CHECK(make_view(C, vc, T3F_F32, false));
+  if (vc->d != A.d || vc->batch != P) return T3F_ERR_SHAPE;
+  for (int k = 0; k <= A.d; ++k) {
+    if ((long long)vc->r[k] != (long long)A.r[k] * X.r[k]) return T3F_ERR_SHAPE;
+    if (k < A.d && vc->n[k] != A.m[k]) return T3F_ERR_SHAPE;
+  }
+  return T3F_OK;
+}
+
+}  // namespace t3f
+
+using namespace t3f;
+
+extern "C" t3f_status t3f_matvec(const t3f_tt* A, const t3f_tt* x, t3f_tt* C, void* ws,
+                                 size_t ws_bytes, t3f_stream_t stream) {
+  TTV va, vx, vc;
+  int P;
+  T3F_CHECK(matvec_views(A, x, &va, &vx, &P));
+  T3F_CHECK(check_product(va, vx, P, C, &vc));
+  (void)ws;
+  (void)ws_bytes;
+  MatvecArgs args;
+  args.A = va;
+  args.x = vx;
+  args.C = vc;
+  args.bA = va.batch;
+  args.bx = vx.batch;
+  args.P = P;
+  args.maxA = 0;
+  args.maxX = 0;
+  for (int k = 0; k < va.d; ++k) {
+    if (va.osz[k] > args.maxA) args.maxA = (int)va.osz[k];
+    if (vx.osz[k] > args.maxX) args.maxX = (int)vx.osz[k];
+  }
+  args.maxA = (args.maxA + 3) & ~3;
+  const size_t smem = sizeof(float) * ((size_t)args.maxA + args.maxX);
+  if (smem > 200 * 1024) return T3F_ERR_UNSUPPORTED;
+  const long long grid = (long long)P * va.d;
+  if (grid > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaFuncSetAttribute(k_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return T3F_ERR_CUDA;
+  k_matvec<<<(unsigned)grid, 256, smem, s>>>(args);
+  return launch_status();
+}
+
+extern "C" t3f_status t3f_matvec_backward(const t3f_tt* A, const t3f_tt* x, const t3f_tt* dC,
+                                          t3f_tt* dA, t3f_tt* dx, void* ws, size_t ws_bytes,
+                                          t3f_stream_t stream) {
+  TTV va, vx, vg, vda, vdx;
+  int P;
+  T3F_CHECK(matvec_views(A, x, &va, &vx, &P));
+  T3F_CHECK(check_product(va, vx, P, dC, &vg));
+  (void)ws;
+  (void)ws_bytes;
+  cudaStream_t s = (cudaStream_t)stream;
+  MatvecBwdArgs args;
+  memset(&args, 0, sizeof(args));
+  if (dA) {
+    T3F_CHECK(make_view(dA, &vda, T3F_F32, true));
+    if (vda.batch != va.batch || vda.d != va.d) return T3F_ERR_SHAPE;
+    for (int k = 0; k < va.d; ++k)
+      if (vda.osz[k] != va.osz[k] || vda.r[k] != va.r[k] || vda.m[k] != va.m[k]) return T3F_ERR_SHAPE;
+    args.dA = static_cast<float*>(vda.p);
+  }
+  if (dx) {
+    T3F_CHECK(make_view(dx, &vdx, T3F_F32, false));
+    if (vdx.batch != vx.batch || vdx.d != vx.d) return T3F_ERR_SHAPE;
+    for (int k = 0; k < vx.d; ++k)
+      if (vdx.osz[k] != vx.osz[k] || vdx.r[k] != vx.r[k]) return T3F_ERR_SHAPE;
+    args.dx = static_cast<float*>(vdx.p);
+  }
+  if (!args.dA && !args.dx) return T3F_OK;
+  args.A = va;
+  args.x = vx;
+  args.dC = vg;
+  args.bA = va.batch;
+  args.bx = vx.batch;
+  args.P = P;
+  args.atomicA = (va.batch == 1 && P > 1);
+  args.atomicX = (vx.batch == 1 && P > 1);
+  for (int k = 0; k < va.d; ++k) {
+    if (va.osz[k] > args.maxA) args.maxA = (int)va.osz[k];
+    if (vx.osz[k] > args.maxX) args.maxX = (int)vx.osz[k];
+    const int row = vx.r[k] * va.m[k] * va.r[k + 1] * vx.r[k + 1];
+    if (row > args.maxRow) args.maxRow = row;
+  }
+  const size_t smem = sizeof(float) * ((size_t)args.maxA + 2 * (size_t)args.maxX + args.maxRow);
+  if (smem > 200 * 1024) return T3F_ERR_UNSUPPORTED;
+  if (args.atomicA && cudaMemsetAsync(args.dA, 0, sizeof(float) * t3f_packed_size(dA), s) != cudaSuccess)
+    return T3F_ERR_CUDA;
+  if (args.atomicX && cudaMemsetAsync(args.dx, 0, sizeof(float) * t3f_packed_size(dx), s) != cudaSuccess)
+    return T3F_ERR_CUDA;
+  const long long grid = (long long)P * va.d;
+  if (cudaFuncSetAttribute(k_matvec_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return T3F_ERR_CUDA;
+  k_matvec_bwd<<<(unsigned)grid, 256, smem, s>>>(args);
+  return launch_status();
+}

@@ -1,0 +1,88 @@
+// Internal declarations shared by the translation units of libt3f (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "t3f.h"
+
+namespace t3f {
+
+// Device view of a packed batch of TT objects, passed to kernels by value.
+struct TTV {
+  int d;
+  int batch;
+  int dtype;
+  int is_matrix;
+  int r[T3F_MAX_D + 1];
+  int n[T3F_MAX_D];
+  int m[T3F_MAX_D];                 // 1 for TT-vectors
+  long long off[T3F_MAX_D];         // element offset of the block of core k
+  long long osz[T3F_MAX_D];         // elements of core k of one object
+  void* p;
+  int rmax;                         // max_k r_k
+  int nmax;                         // max_k n_k
+};
+
+// Host-side validation and conversion of a descriptor. `want_dtype` < 0 accepts any.
+t3f_status make_view(const t3f_tt* t, TTV* v, int want_dtype, bool matrix_expected);
+
+// Element offset of object b's core k.
+__host__ __device__ inline long long core_base(const TTV& v, int k, int b) {
+  return v.off[k] + (long long)b * v.osz[k];
+}
+
+template <typename T>
+__device__ __forceinline__ float ldf(const T* p, long long i);
+template <>
+__device__ __forceinline__ float ldf<float>(const float* p, long long i) { return __ldg(p + i); }
+template <>
+__device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p, long long i) {
+  return __bfloat162float(p[i]);
+}
+
+// Workspace header: the first 256 bytes of every workspace hold the device error word.
+constexpr size_t kWsHeader = 256;
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+t3f_status check_ws(void* ws, size_t ws_bytes, size_t need);
+t3f_status launch_status();  // cudaGetLastError() mapped to a status
+
+// Pair-sweep machinery (sweep.cu) -------------------------------------------------------
+struct SweepPlan {
+  int TA, TB;          // objects per tile on each side
+  size_t smem;         // dynamic shared memory bytes
+};
+SweepPlan plan_sweep(const TTV& A, const TTV& B, int max_pairs);
+
+// Left (dir = 0) or right (dir = 1) transfer sweep over all pairs (a, b) of A x B, tiled
+// TA x TB. out[a * bB + b] receives <A_a, B_b> (nullable). store (nullable) receives the
+// partial of every interface j = 0..d for every pair at store + ioff[j] + pair * rA_j rB_j.
+t3f_status run_pair_sweep(const TTV& A, const TTV& B, int dir, float* out, float* store,
+                          const long long* ioff, cudaStream_t s);
+
+// Diagonal pairs (a, a): out[a] = <A_a, B_a> (A and B of equal batch).
+t3f_status run_zip_sweep(const TTV& A, const TTV& B, float* out, cudaStream_t s);
+
+// Interface offsets for a partial store of bA*bB pairs; returns total floats.
+long long partial_offsets(const TTV& A, const TTV& B, long long pairs, long long* ioff);
+
+// Gauge projection dU_k <- (I - U_k U_k^T) Z_k for k < d, copy for k = d (project.cu).
+t3f_status run_gauge_project(const TTV& U, const float* Z, float* out, cudaStream_t s);
+
+// Workspace sizes (bytes, header included) of the operations.
+size_t ws_gram_bwd(const TTV& A, const TTV& B);
+size_t ws_norm(const TTV& A);
+size_t ws_gather(const TTV& X, long long N, bool bwd);
+size_t ws_rgather(const TTV& U, const TTV& V, long long N);
+size_t ws_orth(const TTV& X);
+size_t ws_psum(const TTV& U, const TTV& Z, bool bwd);
+
+}  // namespace t3f
+
+#define T3F_CHECK(x)                       \
+  do {                                     \
+    t3f_status _st = (x);                  \
+    if (_st != T3F_OK) return _st;         \
+  } while (0)
