@@ -370,7 +370,7 @@ extern "C" t3f_status t3f_gather(const t3f_tt* X, const int32_t* idx, int64_t N,
   TTV vx;
   T3F_CHECK(make_view(X, &vx, T3F_F32, false));
   if (vx.batch != 1) return T3F_ERR_SHAPE;
-  if (N < 0 || (N > 0 && !idx) || (loss && !y)) return T3F_ERR_ARG;
+  if (N < 0 || (N > 0 && !idx) || (loss && !y && N > 0)) return T3F_ERR_ARG;
   GatherLayout lay = gather_layout(vx, vx, N, false, true);
   if (!lay.R || lay.smem > 200 * 1024) return T3F_ERR_UNSUPPORTED;
   T3F_CHECK(check_ws(ws, ws_bytes, lay.total));
@@ -428,7 +428,7 @@ extern "C" t3f_status t3f_gather_backward(const t3f_tt* X, const int32_t* idx, i
   for (int k = 0; k <= vl.d; ++k)
     if (vd.r[k] != vl.r[k] || (k < vl.d && vd.n[k] != vl.n[k])) return T3F_ERR_SHAPE;
   if (N < 0 || (N > 0 && !idx)) return T3F_ERR_ARG;
-  if (!w && !y) return T3F_ERR_ARG;
+  if (N > 0 && !w && !y) return T3F_ERR_ARG;
   if (w && loss) return T3F_ERR_ARG;
   const bool same = !riemannian;
   GatherLayout lay = gather_layout(vl, vr, N, true, same);
