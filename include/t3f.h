@@ -88,6 +88,10 @@ const char* t3f_status_string(int32_t status);
 /* Library version, major*10000 + minor*100 + patch. */
 int32_t t3f_version(void);
 
+/* Number of CUDA kernels this library has launched in the process so far (every launch
+ * site counts one, successful or not); used to report kernel launch counts. */
+int64_t t3f_launch_count(void);
+
 /* Number of elements of the packed cores of `t` (0 if the descriptor is invalid). */
 int64_t t3f_packed_size(const t3f_tt* t);
 

@@ -8,6 +8,6 @@ the library has not been built (``python -m paper_1801_01928_gb300.build``).
 """
 from ._binding import (  # noqa: F401
     BF16, EXPORTS, F32, F64, LIB_PATH, T3FError, TT, device_status, gather, gather_backward,
-    gram, gram_backward, load, matvec, matvec_backward, norm, orth_ranks, orthogonalize,
+    gram, gram_backward, launch_count, load, matvec, matvec_backward, norm, orth_ranks, orthogonalize,
     project_sum, project_sum_backward,
 )

@@ -47,6 +47,7 @@ _SZ = ctypes.c_size_t
 _SIGS = {
     "t3f_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "t3f_version": (ctypes.c_int32, []),
+    "t3f_launch_count": (ctypes.c_int64, []),
     "t3f_packed_size": (ctypes.c_int64, [_P]),
     "t3f_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, _P, _P, ctypes.c_int64]),
     "t3f_gram": (ctypes.c_int32, [_P, _P, _VP, ctypes.c_int32, _VP, _SZ, _VP]),
@@ -310,3 +311,8 @@ def project_sum_backward(U: TT, V: TT, Z: TT, c: torch.Tensor, dUbar: TT, need_Z
 
 def device_status(ws: torch.Tensor) -> int:
     return int(_lib().t3f_device_status(_ptr(ws), _stream(ws.device)))
+
+
+def launch_count() -> int:
+    """Kernels launched by libt3f in this process so far."""
+    return int(_lib().t3f_launch_count())

@@ -1,6 +1,8 @@
 // Descriptor validation, status strings and small host-only entry points of libt3f.
 #include <string.h>
 
+#include <atomic>
+
 #include "t3f_internal.cuh"
 
 namespace t3f {
@@ -48,7 +50,10 @@ t3f_status check_ws(void* ws, size_t ws_bytes, size_t need) {
   return T3F_OK;
 }
 
+static std::atomic<long long> g_launches{0};
+
 t3f_status launch_status() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? T3F_OK : T3F_ERR_CUDA;
 }
@@ -141,3 +146,5 @@ extern "C" size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* 
     default: return 0;
   }
 }
+
+extern "C" int64_t t3f_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
