@@ -1,16 +1,27 @@
 // FP64 Householder orthogonalisation of TT-cores (the left- and right-orthogonal forms that
 // the tangent-space operations of the paper's Section 3.2 are built on).
 //
-// One CTA per TT object runs three sweeps on an FP64 copy of the cores in the workspace:
-//   right-to-left on X (LQ steps: QR of the transposed r_{k-1} x (n_k r_k) unfolding,
-//   R^T pushed into core k-1), left-to-right on the result (QR of the (r_{k-1} n_k) x r_k
-//   unfolding, R pushed into core k+1) giving U, and right-to-left on U giving V.
-// Every QR is a textbook Householder factorisation (Golub & Van Loan, Algorithm 5.2.1)
-// followed by the sign normalisation diag(R) >= 0, which makes Q and R unique for a
-// full-rank unfolding.
+// Three sweeps over an FP64 working copy of the cores: right-to-left on X (LQ steps: QR of
+// the transposed r_{k-1} x (n_k r_k) unfolding, R^T pushed into core k-1), left-to-right on
+// the result (QR of the (r_{k-1} n_k) x r_k unfolding, R pushed into core k+1) giving U, and
+// right-to-left on U giving V. Every QR normalises diag(R) >= 0, which makes the factors of a
+// full-rank unfolding unique.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so one QR is spread over a cluster
+// of P CTAs (P = 16 when the device allows it, else 8): the m rows of the unfolding W are
+// split into P contiguous blocks held in shared memory. Column j's Householder reflector
+// (LAPACK dlarfg convention, Golub & Van Loan Algorithm 5.1.1) needs two cluster-wide
+// reductions -- the norm below the diagonal and the dot products with the trailing columns
+// -- read across CTAs through distributed shared memory. R is then broadcast to every CTA
+// and Q = W R^{-1} is recovered row by row (a triangular solve that needs no further
+// communication). The working cores keep their original row strides so every in-place
+// update touches only the rows or columns its CTA owns.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "t3f_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace t3f {
 
@@ -19,231 +30,345 @@ constexpr int kOrthMaxRows = 4096;
 
 struct OrthArgs {
   TTV X, U, V;
-  int ru[T3F_MAX_D + 1];     // ranks after the sweeps
-  double* work;              // per object: cores region + scratch
-  long long obj_stride;      // doubles per object
-  long long coff[T3F_MAX_D]; // offset of working core k within the object region
-  long long scratch_off;     // offset of the scratch within the object region
+  int P;                      // CTAs per cluster
+  int rows_per;               // max rows of W per CTA (ceil(kOrthMaxRows / P) bound)
+  double* work;               // per object: padded working cores
+  long long obj_stride;       // doubles per object
+  long long coff[T3F_MAX_D];  // offset of working core k
+  int R1[T3F_MAX_D];          // padded row stride of core k (= original r_{k+1})
 };
 
-__device__ double cta_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  return s;
-}
-
-// Householder QR of the column-major m x c matrix W (leading dimension m) in place.
-// On exit Q (m x kk, column-major) and R (kk x c, row-major) hold the sign-normalised
-// factors, kk = min(m, c). Hv (m x kk) receives the unit Householder vectors.
-__device__ void cta_qr(double* W, int m, int c, double* Q, double* R, double* Hv, double* red,
-                       double* bcast) {
-  const int kk = m < c ? m : c;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
-  for (int j = 0; j < kk; ++j) {
-    double* x = W + (long long)j * m;
-    double part = 0.0;
-    for (int r = j + tid; r < m; r += nth) part += x[r] * x[r];
-    const double nrm2 = cta_sum(part, red);
-    const double x0 = x[j];
-    const double nrm = sqrt(nrm2);
-    const double alpha = x0 >= 0.0 ? -nrm : nrm;
-    const double v0 = x0 - alpha;
-    const double vn2 = nrm2 - x0 * x0 + v0 * v0;
-    const double inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
-    double* v = Hv + (long long)j * m;
-    for (int r = tid; r < m; r += nth) v[r] = r < j ? 0.0 : (r == j ? v0 : x[r]) * inv;
-    __syncthreads();
-    // apply H = I - 2 v v^T to columns j..c-1, one warp per column
-    for (int l = j + wid; l < c; l += nw) {
-      double* col = W + (long long)l * m;
-      double s = 0.0;
-      for (int r = j + lane; r < m; r += 32) s += v[r] * col[r];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      for (int r = j + lane; r < m; r += 32) col[r] -= 2.0 * v[r] * s;
-    }
-    __syncthreads();
-    (void)bcast;
-  }
-  // Q = H_0 ... H_{kk-1} [I; 0]
-  for (int e = tid; e < m * kk; e += nth) {
-    const int r = e % m, l = e / m;
-    Q[e] = r == l ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  for (int j = kk - 1; j >= 0; --j) {
-    const double* v = Hv + (long long)j * m;
-    for (int l = wid; l < kk; l += nw) {
-      double* col = Q + (long long)l * m;
-      double s = 0.0;
-      for (int r = j + lane; r < m; r += 32) s += v[r] * col[r];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      for (int r = j + lane; r < m; r += 32) col[r] -= 2.0 * v[r] * s;
-    }
-    __syncthreads();
-  }
-  // R = upper triangle of W; sign normalisation diag(R) >= 0
-  for (int e = tid; e < kk * c; e += nth) {
-    const int r = e / c, l = e % c;
-    const double sgn = W[(long long)r * m + r] < 0.0 ? -1.0 : 1.0;
-    R[e] = l < r ? 0.0 : sgn * W[(long long)l * m + r];
-  }
-  for (int e = tid; e < m * kk; e += nth) {
-    const int l = e / m;
-    if (W[(long long)l * m + l] < 0.0) Q[e] = -Q[e];
-  }
-  __syncthreads();
-}
-
-struct CoreDims {
+struct Dims {
   int r0, n, r1;
 };
 
-// Right-to-left sweep over the working cores (dims updated in place).
-__device__ void sweep_rl(double* base, const long long* coff, CoreDims* dims, int d,
-                         double* Wm, double* Q, double* R, double* Hv, double* red, double* bc) {
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int k = d - 1; k >= 1; --k) {
-    const int r0 = dims[k].r0, n = dims[k].n, r1 = dims[k].r1;
-    const int m = n * r1, c = r0, kk = m < c ? m : c;
-    double* core = base + coff[k];
-    // W = core^T, column-major m x c: W[(i r1 + b) + a m] = core[a][i][b]
-    for (int e = tid; e < m * c; e += nth) {
-      const int a = e / m, q = e % m;
-      Wm[e] = core[(long long)a * m + q];
-    }
-    __syncthreads();
-    cta_qr(Wm, m, c, Q, R, Hv, red, bc);
-    // new core k (kk x n x r1) = Q^T
-    for (int e = tid; e < kk * m; e += nth) {
-      const int a = e / m, q = e % m;
-      core[e] = Q[(long long)a * m + q];
-    }
-    // core k-1 (p0 x n' x r0) <- core_{k-1} R^T  -> (p0 x n' x kk)
-    double* prev = base + coff[k - 1];
-    const int rows = dims[k - 1].r0 * dims[k - 1].n;
-    __syncthreads();
-    // compute into Wm then copy back (Wm is free now)
-    for (int e = tid; e < rows * kk; e += nth) {
-      const int row = e / kk, a2 = e % kk;
-      double s = 0.0;
-      for (int a = 0; a < c; ++a) s += prev[(long long)row * c + a] * R[(long long)a2 * c + a];
-      Wm[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < rows * kk; e += nth) prev[e] = Wm[e];
+struct OrthSmem {
+  double* W;      // rows_per x c working block (row-major, ld = c)
+  double* Rs;     // T3F_MAX_RANK x T3F_MAX_RANK
+  double* v;      // rows_per
+  double* dots;   // T3F_MAX_RANK (published partial dots)
+  double* wsum;   // T3F_MAX_RANK
+  double* red;    // 4 (published partial norm, x0) + scratch
+  double* wred;   // kOrthThreads / 32
+};
+
+__device__ __forceinline__ double block_reduce(double v, double* wred) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) wred[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += wred[i];
+  return s;
+}
+
+// Address of element (row q, col l) of W inside the padded working core.
+//   lr = 1: W = left unfolding, row q = a * n + i, col l = b   -> (a n + i) R1 + l
+//   lr = 0: W = transposed right unfolding, row q = i * r1 + b, col l = a
+__device__ __forceinline__ long long w_addr(int lr, int q, int l, const Dims& dm, int R1) {
+  if (lr) return (long long)q * R1 + l;
+  const int i = q / dm.r1, b = q % dm.r1;
+  return ((long long)l * dm.n + i) * R1 + b;
+}
+
+// One QR step of a sweep on core k. Returns kk via dims updates done by the caller.
+__device__ void qr_step(const OrthArgs& a, double* base, Dims* dims, int k, int lr,
+                        const OrthSmem& s, cg::cluster_group& cluster) {
+  const int P = a.P;
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  const Dims dm = dims[k];
+  const int m = lr ? dm.r0 * dm.n : dm.n * dm.r1;
+  const int c = lr ? dm.r1 : dm.r0;
+  const int kk = m < c ? m : c;
+  const int rp = (m + P - 1) / P;
+  const int row0 = rank * rp;
+  const int nrow = max(0, min(m, row0 + rp) - row0);
+  double* core = base + a.coff[k];
+  const int R1 = a.R1[k];
+
+  cluster.sync();  // previous step's global writes are visible; remote smem reads are done
+  for (int e = tid; e < nrow * c; e += nth) {
+    const int q = e / c, l = e % c;
+    s.W[e] = core[w_addr(lr, row0 + q, l, dm, R1)];
+  }
+  __syncthreads();
+
+  for (int j = 0; j < kk; ++j) {
+    // (A) partial squared norm of column j below the diagonal, and x0 = W[j][j]
+    double part = 0.0;
+    for (int q = tid; q < nrow; q += nth)
+      if (row0 + q > j) part += s.W[q * c + j] * s.W[q * c + j];
+    part = block_reduce(part, s.wred);
     if (tid == 0) {
+      s.red[0] = part;
+      s.red[1] = (j >= row0 && j < row0 + nrow) ? s.W[(j - row0) * c + j] : 0.0;
+    }
+    cluster.sync();
+    double xn2 = 0.0, x0 = 0.0;
+    if (wid == 0) {
+      double p0 = 0.0, p1 = 0.0;
+      if (lane < P) {
+        const double* rr = cluster.map_shared_rank(s.red, lane);
+        p0 = rr[0];
+        p1 = rr[1];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+        p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+      }
+      if (lane == 0) {
+        s.red[2] = p0;
+        s.red[3] = p1;
+      }
+    }
+    __syncthreads();
+    xn2 = s.red[2];
+    x0 = s.red[3];
+    double beta, tau, scale;
+    if (xn2 == 0.0) {
+      beta = x0;
+      tau = 0.0;
+      scale = 0.0;
+    } else {
+      const double nrm = sqrt(x0 * x0 + xn2);
+      beta = x0 >= 0.0 ? -nrm : nrm;
+      tau = (beta - x0) / beta;
+      scale = 1.0 / (x0 - beta);
+    }
+    // (B) reflector v (v_j = 1) on the owned rows, partial dots with the trailing columns
+    for (int q = tid; q < nrow; q += nth) {
+      const int r = row0 + q;
+      s.v[q] = r < j ? 0.0 : (r == j ? 1.0 : s.W[q * c + j] * scale);
+    }
+    __syncthreads();
+    for (int l = j + 1 + wid; l < c; l += nw) {
+      double d = 0.0;
+      for (int q = lane; q < nrow; q += 32) d += s.v[q] * s.W[q * c + l];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) s.dots[l] = d;
+    }
+    cluster.sync();
+    for (int l = j + 1 + wid; l < c; l += nw) {
+      double d = 0.0;
+      if (lane < P) d = cluster.map_shared_rank(s.dots, lane)[l];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) s.wsum[l] = d;
+    }
+    __syncthreads();
+    for (int e = tid; e < nrow * c; e += nth) {
+      const int q = e / c, l = e % c;
+      if (l > j && row0 + q >= j) s.W[e] -= tau * s.v[q] * s.wsum[l];
+    }
+    if (tid == 0 && j >= row0 && j < row0 + nrow) s.W[(j - row0) * c + j] = beta;
+    __syncthreads();
+  }
+  cluster.sync();  // every row of R is final
+  // (C) R (kk x c) from the owners of rows 0..kk-1, normalised to diag(R) >= 0
+  for (int e = tid; e < kk * c; e += nth) {
+    const int j = e / c, l = e % c;
+    double v = 0.0;
+    if (l >= j) {
+      const int own = j / rp;
+      v = cluster.map_shared_rank(s.W, own)[(j - own * rp) * c + l];
+    }
+    s.Rs[j * T3F_MAX_RANK + l] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < kk * c; e += nth) {
+    const int j = e / c, l = e % c;
+    if (s.Rs[j * T3F_MAX_RANK + j] < 0.0 && l != j) s.Rs[j * T3F_MAX_RANK + l] = -s.Rs[j * T3F_MAX_RANK + l];
+  }
+  __syncthreads();
+  for (int j = tid; j < kk; j += nth)
+    if (s.Rs[j * T3F_MAX_RANK + j] < 0.0) s.Rs[j * T3F_MAX_RANK + j] = -s.Rs[j * T3F_MAX_RANK + j];
+  cluster.sync();  // all CTAs are done reading remote W before it is reused below
+  // (D) Q rows = W rows R[:kk,:kk]^{-1} (forward substitution), written in place
+  for (int q = tid; q < nrow; q += nth) {
+    const int r = row0 + q;
+    double* qr = s.W + q * c;
+    for (int l = 0; l < kk; ++l) qr[l] = core[w_addr(lr, r, l, dm, R1)];
+    for (int l = 0; l < kk; ++l) {
+      double acc = qr[l];
+      for (int b = 0; b < l; ++b) acc -= qr[b] * s.Rs[b * T3F_MAX_RANK + l];
+      qr[l] = acc / s.Rs[l * T3F_MAX_RANK + l];
+    }
+  }
+  __syncthreads();
+  Dims nd = dm;
+  if (lr) nd.r1 = kk; else nd.r0 = kk;
+  for (int e = tid; e < nrow * kk; e += nth) {
+    const int q = e / kk, l = e % kk;
+    // L->R: new core (r0, n, kk) row q col l; R->L: new core (kk, n, r1) = Q^T
+    core[w_addr(lr, row0 + q, l, nd, R1)] = s.W[q * c + l];
+  }
+  __syncthreads();
+  // (E) push R into the neighbour core, split across the cluster
+  if (lr) {
+    const Dims nx = dims[k + 1];  // (c, n', r2)
+    double* nb = base + a.coff[k + 1];
+    const int R1n = a.R1[k + 1];
+    const int cols = nx.n * nx.r1;
+    const int cp = (cols + P - 1) / P, c0 = rank * cp, nc = max(0, min(cols, c0 + cp) - c0);
+    for (int e = tid; e < kk * nc; e += nth) {
+      const int a2 = e / nc, q = c0 + e % nc;
+      const int i = q / nx.r1, b = q % nx.r1;
+      double acc = 0.0;
+      for (int al = a2; al < c; ++al) acc += s.Rs[a2 * T3F_MAX_RANK + al] * nb[((long long)al * nx.n + i) * R1n + b];
+      s.W[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < kk * nc; e += nth) {
+      const int a2 = e / nc, q = c0 + e % nc;
+      const int i = q / nx.r1, b = q % nx.r1;
+      nb[((long long)a2 * nx.n + i) * R1n + b] = s.W[e];
+    }
+  } else {
+    const Dims pv = dims[k - 1];  // (r0', n', c)
+    double* pb = base + a.coff[k - 1];
+    const int R1p = a.R1[k - 1];
+    const int rows = pv.r0 * pv.n;
+    const int rq = (rows + P - 1) / P, q0 = rank * rq, nq = max(0, min(rows, q0 + rq) - q0);
+    for (int e = tid; e < nq * kk; e += nth) {
+      const int q = q0 + e / kk, a2 = e % kk;
+      double acc = 0.0;
+      for (int b = a2; b < c; ++b) acc += pb[(long long)q * R1p + b] * s.Rs[a2 * T3F_MAX_RANK + b];
+      s.W[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < nq * kk; e += nth) {
+      const int q = q0 + e / kk, a2 = e % kk;
+      pb[(long long)q * R1p + a2] = s.W[e];
+    }
+  }
+  __syncthreads();
+  __threadfence();
+  if (tid == 0) {
+    if (lr) {
+      dims[k].r1 = kk;
+      dims[k + 1].r0 = kk;
+    } else {
       dims[k].r0 = kk;
       dims[k - 1].r1 = kk;
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
-// Left-to-right sweep over the working cores.
-__device__ void sweep_lr(double* base, const long long* coff, CoreDims* dims, int d,
-                         double* Wm, double* Q, double* R, double* Hv, double* red, double* bc) {
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int k = 0; k < d - 1; ++k) {
-    const int r0 = dims[k].r0, n = dims[k].n, r1 = dims[k].r1;
-    const int m = r0 * n, c = r1, kk = m < c ? m : c;
-    double* core = base + coff[k];
-    // W column-major m x c: W[q + l m] = core[q * c + l]
-    for (int e = tid; e < m * c; e += nth) {
-      const int l = e / m, q = e % m;
-      Wm[e] = core[(long long)q * c + l];
-    }
-    __syncthreads();
-    cta_qr(Wm, m, c, Q, R, Hv, red, bc);
-    for (int e = tid; e < m * kk; e += nth) {
-      const int q = e / kk, l = e % kk;
-      core[e] = Q[(long long)l * m + q];
-    }
-    // core k+1 (r1 x n' x r2) <- R (kk x r1) core_{k+1}
-    double* next = base + coff[k + 1];
-    const int cols = dims[k + 1].n * dims[k + 1].r1;
-    __syncthreads();
-    for (int e = tid; e < kk * cols; e += nth) {
-      const int a2 = e / cols, q = e % cols;
-      double s = 0.0;
-      for (int a = 0; a < c; ++a) s += R[(long long)a2 * c + a] * next[(long long)a * cols + q];
-      Wm[e] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < kk * cols; e += nth) next[e] = Wm[e];
-    if (tid == 0) {
-      dims[k].r1 = kk;
-      dims[k + 1].r0 = kk;
-    }
-    __syncthreads();
-  }
-}
-
-__device__ void write_out(const TTV& O, int obj, const double* base, const long long* coff,
-                          const CoreDims* dims, int d) {
-  for (int k = 0; k < d; ++k) {
-    const long long sz = (long long)dims[k].r0 * dims[k].n * dims[k].r1;
+__device__ void write_out(const OrthArgs& a, const TTV& O, int obj, const double* base,
+                          const Dims* dims, cg::cluster_group& cluster) {
+  cluster.sync();
+  const int P = a.P, rank = (int)cluster.block_rank();
+  for (int k = 0; k < O.d; ++k) {
+    const Dims dm = dims[k];
+    const long long sz = (long long)dm.r0 * dm.n * dm.r1;
     const long long ob = core_base(O, k, obj);
-    if (O.dtype == T3F_F64) {
-      double* o = static_cast<double*>(O.p) + ob;
-      for (long long e = threadIdx.x; e < sz; e += blockDim.x) o[e] = base[coff[k] + e];
-    } else {
-      float* o = static_cast<float*>(O.p) + ob;
-      for (long long e = threadIdx.x; e < sz; e += blockDim.x) o[e] = (float)base[coff[k] + e];
+    for (long long e = (long long)rank * blockDim.x + threadIdx.x; e < sz; e += (long long)P * blockDim.x) {
+      const int b = (int)(e % dm.r1);
+      const long long ai = e / dm.r1;
+      const double v = base[a.coff[k] + ai * a.R1[k] + b];
+      if (O.dtype == T3F_F64) static_cast<double*>(O.p)[ob + e] = v;
+      else static_cast<float*>(O.p)[ob + e] = (float)v;
     }
   }
 }
 
 __global__ void __launch_bounds__(kOrthThreads) k_orth(const __grid_constant__ OrthArgs a) {
-  __shared__ double red[kOrthThreads / 32];
-  __shared__ double bc[2];
-  __shared__ CoreDims dims[T3F_MAX_D];
-  const int obj = blockIdx.x;
+  extern __shared__ double smd[];
+  __shared__ Dims dims[T3F_MAX_D];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int obj = blockIdx.x / a.P;
+  const int rank = (int)cluster.block_rank();
   const TTV& X = a.X;
   const int d = X.d;
+  OrthSmem s;
+  s.W = smd;
+  s.Rs = s.W + (size_t)a.rows_per * T3F_MAX_RANK;
+  s.v = s.Rs + T3F_MAX_RANK * T3F_MAX_RANK;
+  s.dots = s.v + a.rows_per;
+  s.wsum = s.dots + T3F_MAX_RANK;
+  s.red = s.wsum + T3F_MAX_RANK;
+  s.wred = s.red + 8;
   double* base = a.work + (long long)obj * a.obj_stride;
-  double* scr = base + a.scratch_off;
-  double* Wm = scr;
-  double* Q = Wm + (long long)kOrthMaxRows * T3F_MAX_RANK;
-  double* Hv = Q + (long long)kOrthMaxRows * T3F_MAX_RANK;
-  double* R = Hv + (long long)kOrthMaxRows * T3F_MAX_RANK;
-  for (int k = threadIdx.x; k < d; k += blockDim.x) dims[k] = CoreDims{X.r[k], X.n[k], X.r[k + 1]};
-  // load X into the FP64 working cores
+  for (int k = threadIdx.x; k < d; k += blockDim.x) dims[k] = Dims{X.r[k], X.n[k], X.r[k + 1]};
+  // load X (split across the cluster) into the padded FP64 working cores
   for (int k = 0; k < d; ++k) {
-    const long long ob = core_base(X, k, obj);
     const long long sz = X.osz[k];
-    if (X.dtype == T3F_F64) {
-      const double* xp = static_cast<const double*>(X.p) + ob;
-      for (long long e = threadIdx.x; e < sz; e += blockDim.x) base[a.coff[k] + e] = xp[e];
-    } else {
-      const float* xp = static_cast<const float*>(X.p) + ob;
-      for (long long e = threadIdx.x; e < sz; e += blockDim.x) base[a.coff[k] + e] = (double)xp[e];
+    const long long ob = core_base(X, k, obj);
+    for (long long e = (long long)rank * blockDim.x + threadIdx.x; e < sz; e += (long long)a.P * blockDim.x) {
+      const double v = X.dtype == T3F_F64 ? static_cast<const double*>(X.p)[ob + e]
+                                          : (double)static_cast<const float*>(X.p)[ob + e];
+      base[a.coff[k] + e] = v;  // the padded stride equals the original one for X
     }
   }
+  __threadfence();
   __syncthreads();
-  sweep_rl(base, a.coff, dims, d, Wm, Q, R, Hv, red, bc);
-  sweep_lr(base, a.coff, dims, d, Wm, Q, R, Hv, red, bc);
-  write_out(a.U, obj, base, a.coff, dims, d);
-  __syncthreads();
-  sweep_rl(base, a.coff, dims, d, Wm, Q, R, Hv, red, bc);
-  write_out(a.V, obj, base, a.coff, dims, d);
+  for (int k = d - 1; k >= 1; --k) qr_step(a, base, dims, k, 0, s, cluster);
+  for (int k = 0; k < d - 1; ++k) qr_step(a, base, dims, k, 1, s, cluster);
+  __threadfence();
+  write_out(a, a.U, obj, base, dims, cluster);
+  for (int k = d - 1; k >= 1; --k) qr_step(a, base, dims, k, 0, s, cluster);
+  __threadfence();
+  write_out(a, a.V, obj, base, dims, cluster);
 }
 
-static long long orth_obj_stride(const TTV& X, long long* coff, long long* scratch_off) {
+static long long orth_obj_stride(const TTV& X, long long* coff, int* R1) {
   long long o = 0;
   for (int k = 0; k < X.d; ++k) {
     if (coff) coff[k] = o;
+    if (R1) R1[k] = X.r[k + 1];
     o += X.osz[k];
   }
-  o = (o + 31) & ~31LL;
-  if (scratch_off) *scratch_off = o;
-  o += 3LL * kOrthMaxRows * T3F_MAX_RANK + (long long)T3F_MAX_RANK * T3F_MAX_RANK;
   return (o + 31) & ~31LL;
+}
+
+static size_t orth_smem(int rows_per) {
+  return sizeof(double) * ((size_t)rows_per * T3F_MAX_RANK + T3F_MAX_RANK * T3F_MAX_RANK + rows_per +
+                           2 * T3F_MAX_RANK + 8 + kOrthThreads / 32);
+}
+
+// Largest supported cluster size (16 if allowed, else 8), cached per process.
+static int orth_cluster_size(size_t* smem_out) {
+  static int P = -1;
+  static size_t smem = 0;
+  if (P >= 0) {
+    *smem_out = smem;
+    return P;
+  }
+  P = 0;
+  for (int cand : {16, 8}) {
+    const int rows_per = (kOrthMaxRows + cand - 1) / cand;
+    const size_t sm = orth_smem(rows_per);
+    if (cudaFuncSetAttribute(k_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (cand > 8 && cudaFuncSetAttribute(k_orth, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cand;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cand);
+    cfg.blockDim = dim3(kOrthThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_orth, &cfg) == cudaSuccess && nclusters > 0) {
+      P = cand;
+      smem = sm;
+      break;
+    }
+    cudaGetLastError();
+  }
+  *smem_out = smem;
+  return P;
 }
 
 size_t ws_orth(const TTV& X) {
@@ -278,14 +403,33 @@ extern "C" t3f_status t3f_orthogonalize(const t3f_tt* X, t3f_tt* U, t3f_tt* V, v
       if (o->r[k] != ru[k] || (k < vx.d && o->n[k] != vx.n[k])) return T3F_ERR_SHAPE;
   }
   T3F_CHECK(check_ws(ws, ws_bytes, ws_orth(vx)));
+  size_t smem = 0;
+  const int P = orth_cluster_size(&smem);
+  if (P == 0) return T3F_ERR_UNSUPPORTED;
   OrthArgs args;
   memset(&args, 0, sizeof(args));
   args.X = vx;
   args.U = vu;
   args.V = vv;
-  for (int k = 0; k <= vx.d; ++k) args.ru[k] = ru[k];
+  args.P = P;
+  args.rows_per = (kOrthMaxRows + P - 1) / P;
   args.work = reinterpret_cast<double*>(static_cast<char*>(ws) + kWsHeader);
-  args.obj_stride = orth_obj_stride(vx, args.coff, &args.scratch_off);
-  k_orth<<<vx.batch, kOrthThreads, 0, (cudaStream_t)stream>>>(args);
+  args.obj_stride = orth_obj_stride(vx, args.coff, args.R1);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(P * vx.batch));
+  cfg.blockDim = dim3(kOrthThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = (cudaStream_t)stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_orth, args) != cudaSuccess) {
+    cudaGetLastError();
+    return T3F_ERR_CUDA;
+  }
   return launch_status();
 }
