@@ -150,6 +150,25 @@ t3f_status t3f_gather(const t3f_tt* X, const int32_t* idx, int64_t N, const floa
                       t3f_stream_t stream);
 
 /*
+ * Allocation-free t3f_gather (no counterpart in the paper; an interface convenience).
+ * Same arguments and results as t3f_gather without the workspace: for callers that cannot
+ * allocate device memory -- e.g. a plugin whose host framework owns all device memory
+ * through its own pool or a hard cap, or code that must avoid the implicit device
+ * synchronisation of cudaMalloc/cudaFree. The scratch is a device array of
+ * T3F_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads it until the
+ * process exits. The first call on a device looks up the array's address with that device
+ * current (make it before any stream capture). Every call uses the same array, which keeps
+ * the previous call's contents; each call clears the error word and overwrites every
+ * partial it reads. Calls whose work overlaps on the GPU (e.g. issued on two streams with no
+ * ordering between them) race on the array. Returns T3F_ERR_WORKSPACE when a launch would
+ * need more scratch than T3F_NOALLOC_SCRATCH_BYTES (a device with more than about 1000
+ * SMs). Calls no allocating routine.
+ */
+#define T3F_NOALLOC_SCRATCH_BYTES 65536
+t3f_status t3f_gather_noalloc(const t3f_tt* X, const int32_t* idx, int64_t N, const float* y,
+                              float* vals, double* loss, t3f_stream_t stream);
+
+/*
  * Adjoint of the gather (paper Section 3.2, Riemannian autodiff, for the completion loss).
  * Weights: w (device float [N]) if non-NULL, else the residual w_t = X(i_t) - y_t (y
  * required; loss, if non-NULL, receives 1/2 sum w_t^2 in FP64).

@@ -11,6 +11,8 @@
 // suffix vectors of its tuple in shared memory, evaluates the residual, then walks the
 // prefix and scatters the outer products into a per-CTA shared accumulator; a second
 // kernel reduces the per-CTA partials in a fixed order.
+#include <mutex>
+
 #include "t3f_internal.cuh"
 
 namespace t3f {
@@ -477,4 +479,56 @@ extern "C" t3f_status t3f_gather_backward(const t3f_tt* X, const int32_t* idx, i
   }
   if (riemannian) T3F_CHECK(run_gauge_project(vl, gp, out, s));
   return T3F_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of t3f_gather.
+//
+// Some callers cannot allocate device memory for the workspace: a plugin whose host
+// framework owns every byte of device memory through its own pool or a hard memory cap
+// (a cudaMalloc there either fails or escapes the host's accounting), or code that must
+// not risk the implicit device synchronisation that cudaMalloc/cudaFree can cause. This
+// entry point needs no workspace: its scratch (the device error word and the per-CTA loss
+// partials) lives in one file-scope device array of T3F_NOALLOC_SCRATCH_BYTES that every
+// GPU which loads the library keeps until the process exits.
+// ---------------------------------------------------------------------------------------
+
+namespace t3f {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[T3F_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::once_flag g_noalloc_once[kNoAllocMaxDevices];
+static void* g_noalloc_ptr[kNoAllocMaxDevices];
+static cudaError_t g_noalloc_err[kNoAllocMaxDevices];
+
+// Device address of the scratch array on the current device. The array's name in host
+// code is only a host-side stand-in, so the address is looked up once per device (with
+// that device current) and cached.
+static t3f_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return T3F_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return T3F_ERR_UNSUPPORTED;
+  std::call_once(g_noalloc_once[dev], [dev]() {
+    g_noalloc_err[dev] = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+  });
+  if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_ptr[dev]) return T3F_ERR_CUDA;
+  *out = g_noalloc_ptr[dev];
+  return T3F_OK;
+}
+
+}  // namespace t3f
+
+extern "C" t3f_status t3f_gather_noalloc(const t3f_tt* X, const int32_t* idx, int64_t N,
+                                         const float* y, float* vals, double* loss,
+                                         t3f_stream_t stream) {
+  TTV vx;
+  T3F_CHECK(make_view(X, &vx, T3F_F32, false));
+  if (N < 0) return T3F_ERR_ARG;
+  if (gather_layout(vx, vx, N, false, true).total > (size_t)T3F_NOALLOC_SCRATCH_BYTES)
+    return T3F_ERR_WORKSPACE;
+  void* scratch = nullptr;
+  T3F_CHECK(noalloc_scratch(&scratch));
+  // the existing entry point clears the error word and overwrites every partial it reads
+  return t3f_gather(X, idx, N, y, vals, loss, scratch, T3F_NOALLOC_SCRATCH_BYTES, stream);
 }
