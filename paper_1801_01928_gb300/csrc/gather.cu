@@ -243,6 +243,266 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_bwd(const __grid_cons
   }
 }
 
+// Bucketed adjoint (the main path for ranks <= 8). Per chunk of T = blockDim tuples:
+//  (1) a deterministic counting sort of the chunk's tuples by slice, for every core (warp
+//      match + per-warp prefix sums), giving each tuple its bucket position at core k;
+//  (2) thread per tuple: suffix chain storing rho_{k+1} and prefix chain (scaled by the
+//      weight) storing w l_k, both written into the bucket order of core k;
+//  (3) thread per item (core k, slice s, part): a persistent R x R register accumulator
+//      adds w l_k rho_{k+1}^T over the item's share of the bucket; consecutive lanes read
+//      consecutive bucket rows.
+// No atomics in the loop; the per-CTA partial is summed in a fixed order by a second kernel.
+struct CompletionArgs {
+  GatherArgs g;
+  int T;                      // tuples per chunk (= blockDim.x)
+  int NB;                     // buckets per core (nmax + 1; the last holds invalid tuples)
+  int parts[T3F_MAX_D];       // items per slice at core k
+  int item0[T3F_MAX_D + 1];   // first item of core k
+};
+
+template <int R>
+__global__ void __launch_bounds__(256, 1) k_completion(const __grid_constant__ CompletionArgs ca) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ double red[8];
+  const GatherArgs& g = ca.g;
+  const int d = g.d, nmax = g.nmax, T = ca.T, NB = ca.NB;
+  constexpr int SS = R * R + 4;  // padded slice stride (breaks same-bank slices)
+  constexpr int H = R / 4;       // float4 planes of a rank vector
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = (T + 31) >> 5;
+  const int SL = d * nmax * SS;
+  float* Ls = sm;
+  float* Rs = g.same ? Ls : Ls + SL;
+  float4* RH = reinterpret_cast<float4*>(Ls + (g.same ? SL : 2 * SL));  // [d][H][T]
+  float4* LW = RH + (size_t)d * H * T;                                     // [d][H][T]
+  unsigned short* POS = reinterpret_cast<unsigned short*>(LW + (size_t)d * H * T);  // [d][T]
+  unsigned char* IDX = reinterpret_cast<unsigned char*>(POS + (size_t)d * T);       // [d][T]
+  int* WC = reinterpret_cast<int*>(IDX + (((size_t)d * T + 15) & ~(size_t)15));    // [d][NB][NW]
+  int* CNT = WC + (size_t)d * NB * NW;                                              // [d][NB]
+  int* BO = CNT + (size_t)d * NB;                                                   // [d][NB+1]
+
+  // stage the cores as zero-padded R x R slices with stride SS
+  for (int e = tid; e < d * nmax * SS; e += blockDim.x) {
+    const int q = e % SS, i = (e / SS) % nmax, k = e / (SS * nmax);
+    const int a = q / R, b = q % R;
+    float vl = 0.0f, vr = 0.0f;
+    if (q < R * R && i < g.n[k]) {
+      if (a < g.rl[k] && b < g.rl[k + 1]) vl = __ldg(g.L + g.Loff[k] + ((long long)a * g.n[k] + i) * g.rl[k + 1] + b);
+      if (!g.same && a < g.rr[k] && b < g.rr[k + 1])
+        vr = __ldg(g.Rg + g.Roff[k] + ((long long)a * g.n[k] + i) * g.rr[k + 1] + b);
+    }
+    Ls[e] = vl;
+    if (!g.same) Rs[e] = vr;
+  }
+  // this thread's item (core ik, slice is, part ip) of the accumulation phase
+  int ik = -1, is = 0, ip = 0, np = 1;
+  for (int k = 0; k < d; ++k)
+    if (tid >= ca.item0[k] && tid < ca.item0[k + 1]) {
+      ik = k;
+      is = (tid - ca.item0[k]) / ca.parts[k];
+      ip = (tid - ca.item0[k]) % ca.parts[k];
+      np = ca.parts[k];
+    }
+  float acc[R][R];
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) acc[a][b] = 0.0f;
+  double lsum = 0.0;
+  __syncthreads();
+
+  for (long long base = (long long)blockIdx.x * T; base < g.N; base += (long long)gridDim.x * T) {
+    const long long t = base + tid;
+    const bool valid = tid < T && t < g.N;
+    // (1) counting sort by slice, per core
+    for (int e = tid; e < d * NB * NW; e += blockDim.x) WC[e] = 0;
+    __syncthreads();
+    for (int k = 0; k < d; ++k) {
+      const int sl = valid ? load_index(g, k, t) : nmax;
+      const unsigned m = __match_any_sync(0xffffffffu, sl);
+      const int rank = __popc(m & ((1u << lane) - 1u));
+      if (tid < T) {
+        IDX[k * T + tid] = (unsigned char)sl;
+        POS[k * T + tid] = (unsigned short)rank;
+        if (rank == 0) WC[(k * NB + sl) * NW + warp] = __popc(m);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < d * NB; e += blockDim.x) {
+      int run = 0;
+      for (int w = 0; w < NW; ++w) {
+        const int c = WC[e * NW + w];
+        WC[e * NW + w] = run;
+        run += c;
+      }
+      CNT[e] = run;
+    }
+    __syncthreads();
+    for (int k = tid; k < d; k += blockDim.x) {
+      int run = 0;
+      for (int sl = 0; sl < NB; ++sl) {
+        BO[k * (NB + 1) + sl] = run;
+        run += CNT[k * NB + sl];
+      }
+      BO[k * (NB + 1) + NB] = run;
+    }
+    __syncthreads();
+    if (tid < T)
+      for (int k = 0; k < d; ++k) {
+        const int sl = IDX[k * T + tid];
+        POS[k * T + tid] = (unsigned short)(BO[k * (NB + 1) + sl] + WC[(k * NB + sl) * NW + warp] + POS[k * T + tid]);
+      }
+    __syncthreads();
+    // (2) chains of this thread's tuple
+    if (valid) {
+      float rho[R];
+#pragma unroll
+      for (int a = 0; a < R; ++a) rho[a] = a == 0 ? 1.0f : 0.0f;
+      for (int k = d - 1; k >= 1; --k) {
+        const int p = POS[k * T + tid];
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+          RH[((size_t)k * H + h) * T + p] = make_float4(rho[4 * h], rho[4 * h + 1], rho[4 * h + 2], rho[4 * h + 3]);
+        const float* S = Rs + (k * nmax + IDX[k * T + tid]) * SS;
+        float nr[R];
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+          float acc1 = 0.0f;
+#pragma unroll
+          for (int b = 0; b < R; b += 4) {
+            const float4 s4 = *reinterpret_cast<const float4*>(S + a * R + b);
+            acc1 = fmaf(s4.x, rho[b], acc1);
+            acc1 = fmaf(s4.y, rho[b + 1], acc1);
+            acc1 = fmaf(s4.z, rho[b + 2], acc1);
+            acc1 = fmaf(s4.w, rho[b + 3], acc1);
+          }
+          nr[a] = acc1;
+        }
+#pragma unroll
+        for (int a = 0; a < R; ++a) rho[a] = nr[a];
+      }
+      {
+        const int p = POS[tid];
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+          RH[(size_t)h * T + p] = make_float4(rho[4 * h], rho[4 * h + 1], rho[4 * h + 2], rho[4 * h + 3]);
+      }
+      const float* S0 = Rs + IDX[tid] * SS;
+      float x = 0.0f;
+#pragma unroll
+      for (int b = 0; b < R; ++b) x = fmaf(S0[b], rho[b], x);
+      float wt;
+      if (g.w) {
+        wt = g.w[t];
+      } else {
+        const double res = (double)x - (double)g.y[t];
+        lsum += 0.5 * res * res;
+        wt = (float)res;
+      }
+      float l[R];
+#pragma unroll
+      for (int a = 0; a < R; ++a) l[a] = a == 0 ? wt : 0.0f;
+      for (int k = 0; k < d; ++k) {
+        const int p = POS[k * T + tid];
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+          LW[((size_t)k * H + h) * T + p] = make_float4(l[4 * h], l[4 * h + 1], l[4 * h + 2], l[4 * h + 3]);
+        if (k + 1 == d) break;
+        const float* S = Ls + (k * nmax + IDX[k * T + tid]) * SS;
+        float nl[R];
+#pragma unroll
+        for (int b = 0; b < R; ++b) nl[b] = 0.0f;
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+#pragma unroll
+          for (int b = 0; b < R; b += 4) {
+            const float4 s4 = *reinterpret_cast<const float4*>(S + a * R + b);
+            nl[b] = fmaf(l[a], s4.x, nl[b]);
+            nl[b + 1] = fmaf(l[a], s4.y, nl[b + 1]);
+            nl[b + 2] = fmaf(l[a], s4.z, nl[b + 2]);
+            nl[b + 3] = fmaf(l[a], s4.w, nl[b + 3]);
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < R; ++b) l[b] = nl[b];
+      }
+    }
+    __syncthreads();
+    // (3) accumulation: this thread's item over its share of the bucket
+    if (ik >= 0) {
+      const int p0 = BO[ik * (NB + 1) + is], p1 = BO[ik * (NB + 1) + is + 1];
+      const float4* lw = LW + (size_t)ik * H * T;
+      const float4* rh = RH + (size_t)ik * H * T;
+      if (ik == 0 || ik == d - 1) {
+        for (int p = p0 + ip; p < p1; p += np) {
+          float lv[R], rv[R];
+#pragma unroll
+          for (int h = 0; h < H; ++h) {
+            const float4 a4 = lw[(size_t)h * T + p];
+            const float4 b4 = rh[(size_t)h * T + p];
+            lv[4 * h] = a4.x; lv[4 * h + 1] = a4.y; lv[4 * h + 2] = a4.z; lv[4 * h + 3] = a4.w;
+            rv[4 * h] = b4.x; rv[4 * h + 1] = b4.y; rv[4 * h + 2] = b4.z; rv[4 * h + 3] = b4.w;
+          }
+          if (ik == 0) {
+#pragma unroll
+            for (int b = 0; b < R; ++b) acc[0][b] = fmaf(lv[0], rv[b], acc[0][b]);
+          } else {
+#pragma unroll
+            for (int a = 0; a < R; ++a) acc[a][0] = fmaf(lv[a], rv[0], acc[a][0]);
+          }
+        }
+      } else {
+        for (int p = p0 + ip; p < p1; p += np) {
+          float lv[R], rv[R];
+#pragma unroll
+          for (int h = 0; h < H; ++h) {
+            const float4 a4 = lw[(size_t)h * T + p];
+            const float4 b4 = rh[(size_t)h * T + p];
+            lv[4 * h] = a4.x; lv[4 * h + 1] = a4.y; lv[4 * h + 2] = a4.z; lv[4 * h + 3] = a4.w;
+            rv[4 * h] = b4.x; rv[4 * h + 1] = b4.y; rv[4 * h + 2] = b4.z; rv[4 * h + 3] = b4.w;
+          }
+#pragma unroll
+          for (int a = 0; a < R; ++a)
+#pragma unroll
+            for (int b = 0; b < R; ++b) acc[a][b] = fmaf(lv[a], rv[b], acc[a][b]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // sum the parts of every (core, slice) in shared memory, then write the CTA's partial
+  float* cacc = reinterpret_cast<float*>(RH);  // d * nmax * R * R floats (fits in RH)
+  for (int e = tid; e < d * nmax * R * R; e += blockDim.x) cacc[e] = 0.0f;
+  __syncthreads();
+  if (ik >= 0) {
+    float* dst = cacc + (ik * nmax + is) * R * R;
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b)
+        if (acc[a][b] != 0.0f) atomicAdd(dst + a * R + b, acc[a][b]);
+  }
+  __syncthreads();
+  float* out = g.grad_part + (long long)blockIdx.x * g.gsize;
+  for (int k = 0; k < d; ++k) {
+    const int ra = g.rl[k], rb = g.rr[k + 1], nk = g.n[k];
+    for (int e = tid; e < ra * nk * rb; e += blockDim.x) {
+      const int b = e % rb, i = (e / rb) % nk, a = e / (rb * nk);
+      out[g.goff[k] + e] = cacc[(k * nmax + i) * R * R + a * R + b];
+    }
+  }
+  if (g.loss_part) {
+    double v = lsum;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double s2 = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s2 += red[i];
+      g.loss_part[blockIdx.x] = s2;
+    }
+  }
+}
+
 __global__ void k_reduce_partials(const float* part, int nparts, long long size, float* out) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < size;
        e += (long long)gridDim.x * blockDim.x) {
@@ -293,7 +553,53 @@ struct GatherLayout {
   int grid;
   size_t smem;
   size_t loss_off, grad_off, total;
+  // bucketed adjoint
+  int bucketed, T, NB;
+  int parts[T3F_MAX_D];
+  int item0[T3F_MAX_D + 1];
 };
+
+static size_t completion_smem(int d, int nmax, int R, int T, bool same) {
+  const size_t SS = (size_t)R * R + 4;
+  const int NB = nmax + 1, NW = (T + 31) / 32;
+  size_t b = sizeof(float) * ((same ? 1 : 2) * (size_t)d * nmax * SS + 2 * (size_t)d * R * T);
+  b += 2 * (size_t)d * T;                           // POS
+  b += ((size_t)d * T + 15) & ~(size_t)15;          // IDX
+  b += sizeof(int) * ((size_t)d * NB * NW + (size_t)d * NB + (size_t)d * (NB + 1));
+  return b;
+}
+
+// Choose the bucketed adjoint when its items fit one CTA and its buffers fit shared memory.
+static bool plan_completion(const TTV& L, bool same, int R, GatherLayout* lay) {
+  if (R > 8 || L.nmax > 254) return false;
+  const int d = L.d;
+  for (int T = 256; T >= 128; T -= 32) {
+    if (L.nmax * R > T) continue;
+    if (completion_smem(d, L.nmax, R, T, same) > 220 * 1024) continue;
+    // boundary cores take one item per slice, interior cores share the rest evenly
+    int bnd = 0, inner = 0;
+    for (int k = 0; k < d; ++k) {
+      if (k == 0 || k == d - 1) bnd += L.n[k];
+      else inner += L.n[k];
+    }
+    const int P2 = inner ? (T - bnd) / inner : 1;
+    if (P2 < 1) continue;
+    int it = 0;
+    for (int k = 0; k < d; ++k) {
+      lay->item0[k] = it;
+      lay->parts[k] = (k == 0 || k == d - 1) ? 1 : P2;
+      it += L.n[k] * lay->parts[k];
+    }
+    lay->item0[d] = it;
+    if (it > T) continue;
+    lay->bucketed = 1;
+    lay->T = T;
+    lay->NB = L.nmax + 1;
+    lay->smem = completion_smem(d, L.nmax, R, T, same);
+    return true;
+  }
+  return false;
+}
 
 static GatherLayout gather_layout(const TTV& L, const TTV& Rv, long long N, bool bwd, bool same) {
   GatherLayout lay{};
@@ -304,6 +610,10 @@ static GatherLayout gather_layout(const TTV& L, const TTV& Rv, long long N, bool
   if (!bwd) {
     lay.smem = sizeof(float) * SL;
     lay.grid = gather_grid(N, num_sms() * 8);
+  } else if (lay.R && plan_completion(L, same, R, &lay)) {
+    long long g = (N + lay.T - 1) / lay.T;
+    if (g > num_sms()) g = num_sms();
+    lay.grid = (int)(g < 1 ? 1 : g);
   } else {
     lay.smem = sizeof(float) * ((same ? 1 : 2) * SL + (size_t)L.d * nmax * (R * R + 1) +
                                 (size_t)L.d * R * kGatherThreads);
@@ -354,7 +664,24 @@ static t3f_status launch_fwd(const GatherArgs& g, const GatherLayout& lay, cudaS
 }
 
 template <int R>
+static t3f_status launch_completion(const GatherArgs& g, const GatherLayout& lay, cudaStream_t s) {
+  CompletionArgs ca;
+  memset(&ca, 0, sizeof(ca));
+  ca.g = g;
+  ca.T = lay.T;
+  ca.NB = lay.NB;
+  for (int k = 0; k < g.d; ++k) ca.parts[k] = lay.parts[k];
+  for (int k = 0; k <= g.d; ++k) ca.item0[k] = lay.item0[k];
+  auto kern = k_completion<R>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem) != cudaSuccess)
+    return T3F_ERR_CUDA;
+  kern<<<lay.grid, lay.T, lay.smem, s>>>(ca);
+  return launch_status();
+}
+
+template <int R>
 static t3f_status launch_bwd(const GatherArgs& g, const GatherLayout& lay, cudaStream_t s) {
+  if (lay.bucketed) return launch_completion<(R <= 4 ? 4 : 8)>(g, lay, s);
   auto kern = k_gather_bwd<R>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem) != cudaSuccess)
     return T3F_ERR_CUDA;
@@ -374,7 +701,7 @@ extern "C" t3f_status t3f_gather(const t3f_tt* X, const int32_t* idx, int64_t N,
   if (vx.batch != 1) return T3F_ERR_SHAPE;
   if (N < 0 || (N > 0 && !idx) || (loss && !y && N > 0)) return T3F_ERR_ARG;
   GatherLayout lay = gather_layout(vx, vx, N, false, true);
-  if (!lay.R || lay.smem > 200 * 1024) return T3F_ERR_UNSUPPORTED;
+  if (!lay.R || lay.smem > 227 * 1024) return T3F_ERR_UNSUPPORTED;
   T3F_CHECK(check_ws(ws, ws_bytes, lay.total));
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(ws, 0, sizeof(int32_t), s) != cudaSuccess) return T3F_ERR_CUDA;
@@ -434,7 +761,7 @@ extern "C" t3f_status t3f_gather_backward(const t3f_tt* X, const int32_t* idx, i
   if (w && loss) return T3F_ERR_ARG;
   const bool same = !riemannian;
   GatherLayout lay = gather_layout(vl, vr, N, true, same);
-  if (!lay.R || lay.smem > 200 * 1024) return T3F_ERR_UNSUPPORTED;
+  if (!lay.R || lay.smem > 227 * 1024) return T3F_ERR_UNSUPPORTED;
   T3F_CHECK(check_ws(ws, ws_bytes, lay.total));
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(ws, 0, sizeof(int32_t), s) != cudaSuccess) return T3F_ERR_CUDA;

@@ -317,3 +317,16 @@ def test_matvec_config3b_sampled(lib):
     Ao, xo = objects(A), objects(x)
     for p in (0, 41, 99):
         assert rel_err_cores(hc[p], O.matvec(Ao[p], xo[p])) < TOL["fp32"]
+
+
+def test_riemannian_grad_config2_full(lib):
+    cfg = S.config2()
+    X, y = _completion_inputs(cfg.T, cfg.X, cfg.idx, cfg.noise)
+    U, V = _orth(lib, X, torch.float32)
+    dU, loss = lib.gather_backward(None, torch.tensor(cfg.idx, device="cuda"),
+                                   y=torch.tensor(y, dtype=torch.float32, device="cuda"),
+                                   want_loss=True, riemannian=True, U=U, V=V)
+    Uo, Vo, _ = O.orthogonalize(objects(X)[0])
+    L, ref = O.riemannian_grad_completion(Uo, Vo, cfg.idx, y)
+    assert abs(loss.item() - L) <= TOL["fp32"] * L
+    assert rel_err_cores(host_objects(dU)[0], ref) < TOL["fp32"]
