@@ -377,6 +377,12 @@ static PsumLayout psum_layout(const TTV& U, const TTV& Z, bool bwd) {
     l.jchunk = 0;
     l.nchunks = 0;
     l.offPart = 0;
+  } else if (psweep_supported(U, Z)) {
+    l.nchunks = passemble_ranges(Z);
+    l.jchunk = (Z.batch + l.nchunks - 1) / l.nchunks;
+    l.offPart = o;
+    o += align256(sizeof(float) * l.gsize * l.nchunks);
+    l.offP = l.offQ = l.offW = 0;
   } else {
     // split the batch so that (sum_k n_k) * nchunks CTAs cover the GPU a few times
     long long slices = 0;
@@ -425,6 +431,14 @@ extern "C" t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3
   float* Lst = reinterpret_cast<float*>(w + l.offL);
   float* Rst = reinterpret_cast<float*>(w + l.offR);
   float* part = reinterpret_cast<float*>(w + l.offPart);
+  if (psweep_supported(vu, vz)) {
+    T3F_CHECK(run_psweep(vu, vz, 0, static_cast<const float*>(vu.p), nullptr, nullptr, Lst, nullptr, l.ioffL, s));
+    T3F_CHECK(run_psweep(vv, vz, 1, static_cast<const float*>(vv.p), nullptr, nullptr, Rst, nullptr, l.ioffR, s));
+    T3F_CHECK(run_passemble(vu, vz, Lst, Rst, l.ioffL, c, part, l.nchunks, s));
+    k_reduce_chunks<<<256, 256, 0, s>>>(part, l.nchunks, l.gsize, part);
+    T3F_CHECK(launch_status());
+    return run_gauge_project(vu, part, static_cast<float*>(vd.p), s);
+  }
   T3F_CHECK(run_pair_sweep(vu, vz, 0, nullptr, Lst, l.ioffL, s));
   T3F_CHECK(run_pair_sweep(vv, vz, 1, nullptr, Rst, l.ioffR, s));
   AssembleArgs a;
@@ -477,6 +491,14 @@ extern "C" t3f_status t3f_project_sum_backward(const t3f_tt* U, const t3f_tt* V,
   T3F_CHECK(run_gauge_project(vu, static_cast<const float*>(vb.p), Wc, s));
   TTV vw = vu;
   vw.p = Wc;
+  if (psweep_supported(vu, vz)) {
+    const float* Up = static_cast<const float*>(vu.p);
+    const float* Vp = static_cast<const float*>(vv.p);
+    T3F_CHECK(run_psweep(vu, vz, 0, Up, Vp, Wc, Lst, Pst, l.ioffL, s));
+    T3F_CHECK(run_psweep(vu, vz, 1, Vp, Up, Wc, Rst, Qst, l.ioffL, s));
+    return run_pgrad(vu, vz, Up, Vp, Wc, Lst, Rst, Pst, Qst, l.ioffL, c, dZ ? static_cast<float*>(vdz.p) : nullptr,
+                     dc, s);
+  }
   T3F_CHECK(run_pair_sweep(vu, vz, 0, nullptr, Lst, l.ioffL, s));
   T3F_CHECK(run_pair_sweep(vv, vz, 1, nullptr, Rst, l.ioffR, s));
   // mixed sweeps

@@ -71,6 +71,17 @@ long long partial_offsets(const TTV& A, const TTV& B, long long pairs, long long
 // Gauge projection dU_k <- (I - U_k U_k^T) Z_k for k < d, copy for k = d (project.cu).
 t3f_status run_gauge_project(const TTV& U, const float* Z, float* out, cudaStream_t s);
 
+// Register-tiled project_sum sweeps (psweep.cu): X side ranks <= 32, Z ranks <= 8.
+bool psweep_supported(const TTV& X, const TTV& Z);
+t3f_status run_psweep(const TTV& X, const TTV& Z, int dir, const float* A, const float* B1, const float* B2,
+                      float* st1, float* st2, const long long* ioff, cudaStream_t s);
+int passemble_ranges(const TTV& Z);
+t3f_status run_passemble(const TTV& X, const TTV& Z, const float* L, const float* R, const long long* ioff,
+                         const float* c, float* part, int nranges, cudaStream_t s);
+t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V, const float* W, const float* L,
+                     const float* R, const float* P, const float* Q, const long long* ioff, const float* c, float* dZ,
+                     float* dc, cudaStream_t s);
+
 // Workspace sizes (bytes, header included) of the operations.
 size_t ws_gram_bwd(const TTV& A, const TTV& B);
 size_t ws_norm(const TTV& A);

@@ -330,3 +330,24 @@ def test_riemannian_grad_config2_full(lib):
     L, ref = O.riemannian_grad_completion(Uo, Vo, cfg.idx, y)
     assert abs(loss.item() - L) <= TOL["fp32"] * L
     assert rel_err_cores(host_objects(dU)[0], ref) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("shape", [dict(batch=160, d=20, n=16, rX=32, rZ=8),   # config-5 shape
+                                   dict(batch=23, d=5, n=4, rX=12, rZ=5),     # rank-16 tiles
+                                   dict(batch=9, d=3, n=7, rX=20, rZ=8)])
+def test_project_sum_fwd_bwd_shapes(lib, shape):
+    cfg = S.config5(**shape)
+    X, Z = round32(cfg.X), round32(cfg.Z)
+    c = cfg.c.astype(np.float32)
+    U, V = _orth(lib, X, torch.float32)
+    Zd = dev_tt(lib, Z)
+    ct = torch.tensor(c, device="cuda")
+    dU = lib.project_sum(U, V, Zd, ct)
+    Uo, Vo, r = O.orthogonalize(objects(X)[0])
+    ref = O.project_sum(Uo, Vo, objects(Z), c.astype(np.float64))
+    assert rel_err_cores(host_objects(dU)[0], ref) < TOL["fp32"]
+    # adjoint of 1/2 ||S||^2: the cotangent of the coordinates is the forward output
+    dZ, dc = lib.project_sum_backward(U, V, Zd, ct, dU)
+    rZ, rc = O.project_sum_vjp(Uo, Vo, objects(Z), c.astype(np.float64), host_objects(dU)[0])
+    assert rel_err_cores(host_cores(dZ), batched(rZ)) < TOL["fp32"]
+    assert rel_err(dc.cpu().numpy(), rc) < TOL["fp32"]
