@@ -10,12 +10,14 @@
 // GB300 runs FP64 at a small fraction of its FP32 rate, so one QR is spread over a cluster
 // of P CTAs (P = 16 when the device allows it, else 8): the m rows of the unfolding W are
 // split into P contiguous blocks held in shared memory. Column j's Householder reflector
-// (LAPACK dlarfg convention, Golub & Van Loan Algorithm 5.1.1) needs two cluster-wide
-// reductions -- the norm below the diagonal and the dot products with the trailing columns
-// -- read across CTAs through distributed shared memory. R is then broadcast to every CTA
-// and Q = W R^{-1} is recovered row by row (a triangular solve that needs no further
-// communication). The working cores keep their original row strides so every in-place
-// update touches only the rows or columns its CTA owns.
+// (LAPACK dlarfg convention, Golub & Van Loan Algorithm 5.1.1) needs the norm of x = W[j:, j]
+// and the products v . W[:, l] with the trailing columns; both follow from one set of
+// partial sums per CTA (x.x and x.W[:, l] below the diagonal, plus row j), exchanged through
+// distributed shared memory behind a single cluster barrier per column (the publish slots
+// alternate between two buffers). R is then broadcast to every CTA and Q = W R^{-1} is
+// recovered row by row by a triangular solve that needs no further communication. The
+// working cores keep their original row strides so every in-place update touches only the
+// rows or columns its CTA owns.
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -45,23 +47,14 @@ struct Dims {
 struct OrthSmem {
   double* W;      // rows_per x c working block (row-major, ld = c)
   double* Rs;     // T3F_MAX_RANK x T3F_MAX_RANK
-  double* v;      // rows_per
-  double* dots;   // T3F_MAX_RANK (published partial dots)
-  double* wsum;   // T3F_MAX_RANK
-  double* red;    // 4 (published partial norm, x0) + scratch
-  double* wred;   // kOrthThreads / 32
+  double* pub;    // [2][T3F_MAX_RANK] published partial dots (index j holds the squared norm)
+  double* rowj;   // [2][T3F_MAX_RANK] published row j (owner only)
+  double* gsum;   // T3F_MAX_RANK gathered dots
+  double* wj;     // T3F_MAX_RANK row j of W
+  double* rinv;   // T3F_MAX_RANK reciprocals of diag(R)
+  double* tv;     // rows_per: tau * v_r of the owned rows
+  double* refl;   // 4: beta, tau, scale of the current reflector
 };
-
-__device__ __forceinline__ double block_reduce(double v, double* wred) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) wred[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += wred[i];
-  return s;
-}
 
 // Address of element (row q, col l) of W inside the padded working core.
 //   lr = 1: W = left unfolding, row q = a * n + i, col l = b   -> (a n + i) R1 + l
@@ -72,12 +65,12 @@ __device__ __forceinline__ long long w_addr(int lr, int q, int l, const Dims& dm
   return ((long long)l * dm.n + i) * R1 + b;
 }
 
-// One QR step of a sweep on core k. Returns kk via dims updates done by the caller.
+// One QR step of a sweep on core k (updates dims for core k and its neighbour).
 __device__ void qr_step(const OrthArgs& a, double* base, Dims* dims, int k, int lr,
                         const OrthSmem& s, cg::cluster_group& cluster) {
   const int P = a.P;
   const int rank = (int)cluster.block_rank();
-  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  const int tid = threadIdx.x, nth = blockDim.x;
   const Dims dm = dims[k];
   const int m = lr ? dm.r0 * dm.n : dm.n * dm.r1;
   const int c = lr ? dm.r1 : dm.r0;
@@ -96,75 +89,72 @@ __device__ void qr_step(const OrthArgs& a, double* base, Dims* dims, int k, int 
   __syncthreads();
 
   for (int j = 0; j < kk; ++j) {
-    // (A) partial squared norm of column j below the diagonal, and x0 = W[j][j]
-    double part = 0.0;
-    for (int q = tid; q < nrow; q += nth)
-      if (row0 + q > j) part += s.W[q * c + j] * s.W[q * c + j];
-    part = block_reduce(part, s.wred);
-    if (tid == 0) {
-      s.red[0] = part;
-      s.red[1] = (j >= row0 && j < row0 + nrow) ? s.W[(j - row0) * c + j] : 0.0;
+    const int par = j & 1;
+    double* pub = s.pub + par * T3F_MAX_RANK;
+    double* rowj = s.rowj + par * T3F_MAX_RANK;
+    const bool own_j = j >= row0 && j < row0 + nrow;
+    // (1) partials over the owned rows strictly below the diagonal:
+    //     pub[j] = sum x_r^2, pub[l] = sum x_r W[r][l] (l > j); the owner publishes row j.
+    //     Eight lanes per column split the rows and combine with three shuffles.
+    const int q_lo = max(0, j + 1 - row0);
+    for (int cb = j; cb < c; cb += nth / 8) {
+      const int l = cb + tid / 8, g = tid % 8;
+      double acc = 0.0;
+      if (l < c)
+        for (int q = q_lo + g; q < nrow; q += 8) acc = fma(s.W[q * c + j], s.W[q * c + l], acc);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4, 8);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2, 8);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1, 8);
+      if (g == 0 && l < c) pub[l] = acc;
     }
+    if (own_j)
+      for (int l = j + tid; l < c; l += nth) rowj[l] = s.W[(j - row0) * c + l];
+    __syncthreads();
     cluster.sync();
-    double xn2 = 0.0, x0 = 0.0;
-    if (wid == 0) {
-      double p0 = 0.0, p1 = 0.0;
-      if (lane < P) {
-        const double* rr = cluster.map_shared_rank(s.red, lane);
-        p0 = rr[0];
-        p1 = rr[1];
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        p0 += __shfl_xor_sync(0xffffffffu, p0, o);
-        p1 += __shfl_xor_sync(0xffffffffu, p1, o);
-      }
-      if (lane == 0) {
-        s.red[2] = p0;
-        s.red[3] = p1;
+    // (2) gather the cluster sums (16 lanes per column, one per rank); the lane that owns
+    //     column j also forms the reflector (LAPACK dlarfg convention)
+    const int jown = j / rp;
+    const int ng = ((c - j) * 16 + 31) & ~31;  // whole warps take part in the shuffles
+    for (int e = tid; e < ng; e += nth) {
+      const int l = j + e / 16, p = e % 16;
+      double v = 0.0, wl = 0.0;
+      if (p < P && l < c) v = cluster.map_shared_rank(pub, p)[l];
+      if (p == 0 && l < c) wl = cluster.map_shared_rank(rowj, jown)[l];  // issued with v
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
+      if (p == 0 && l < c) {
+        s.gsum[l] = v;
+        s.wj[l] = wl;
+        if (l == j) {
+          double beta = wl, tau = 0.0, scale = 0.0;
+          if (v != 0.0) {
+            const double nrm = sqrt(wl * wl + v);
+            beta = wl >= 0.0 ? -nrm : nrm;
+            tau = (beta - wl) / beta;
+            scale = 1.0 / (wl - beta);
+          }
+          s.refl[0] = beta;
+          s.refl[1] = tau;
+          s.refl[2] = scale;
+        }
       }
     }
     __syncthreads();
-    xn2 = s.red[2];
-    x0 = s.red[3];
-    double beta, tau, scale;
-    if (xn2 == 0.0) {
-      beta = x0;
-      tau = 0.0;
-      scale = 0.0;
-    } else {
-      const double nrm = sqrt(x0 * x0 + xn2);
-      beta = x0 >= 0.0 ? -nrm : nrm;
-      tau = (beta - x0) / beta;
-      scale = 1.0 / (x0 - beta);
-    }
-    // (B) reflector v (v_j = 1) on the owned rows, partial dots with the trailing columns
-    for (int q = tid; q < nrow; q += nth) {
-      const int r = row0 + q;
-      s.v[q] = r < j ? 0.0 : (r == j ? 1.0 : s.W[q * c + j] * scale);
-    }
+    const double beta = s.refl[0], tau = s.refl[1], scale = s.refl[2];
+    // (3) w_l = v . W[:, l] for the trailing columns and tau v_r for the owned rows, then the
+    //     rank-one update of the owned rows
+    for (int l = j + 1 + tid; l < c; l += nth) s.gsum[l] = s.wj[l] + scale * s.gsum[l];
+    const int q_j = max(0, j - row0);
+    for (int q = q_j + tid; q < nrow; q += nth) s.tv[q] = row0 + q == j ? tau : tau * scale * s.W[q * c + j];
     __syncthreads();
-    for (int l = j + 1 + wid; l < c; l += nw) {
-      double d = 0.0;
-      for (int q = lane; q < nrow; q += 32) d += s.v[q] * s.W[q * c + l];
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if (lane == 0) s.dots[l] = d;
+    const int wc = c - j - 1, wr = nrow - q_j;
+    for (int e = tid; e < wr * wc; e += nth) {
+      const int q = q_j + e / wc, l = j + 1 + e % wc;
+      s.W[q * c + l] -= s.tv[q] * s.gsum[l];
     }
-    cluster.sync();
-    for (int l = j + 1 + wid; l < c; l += nw) {
-      double d = 0.0;
-      if (lane < P) d = cluster.map_shared_rank(s.dots, lane)[l];
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if (lane == 0) s.wsum[l] = d;
-    }
-    __syncthreads();
-    for (int e = tid; e < nrow * c; e += nth) {
-      const int q = e / c, l = e % c;
-      if (l > j && row0 + q >= j) s.W[e] -= tau * s.v[q] * s.wsum[l];
-    }
-    if (tid == 0 && j >= row0 && j < row0 + nrow) s.W[(j - row0) * c + j] = beta;
+    if (own_j && tid == 0) s.W[(j - row0) * c + j] = beta;
     __syncthreads();
   }
-  cluster.sync();  // every row of R is final
+  cluster.sync();  // every row of R is final in its owner's shared memory
   // (C) R (kk x c) from the owners of rows 0..kk-1, normalised to diag(R) >= 0
   for (int e = tid; e < kk * c; e += nth) {
     const int j = e / c, l = e % c;
@@ -181,18 +171,60 @@ __device__ void qr_step(const OrthArgs& a, double* base, Dims* dims, int k, int 
     if (s.Rs[j * T3F_MAX_RANK + j] < 0.0 && l != j) s.Rs[j * T3F_MAX_RANK + l] = -s.Rs[j * T3F_MAX_RANK + l];
   }
   __syncthreads();
-  for (int j = tid; j < kk; j += nth)
-    if (s.Rs[j * T3F_MAX_RANK + j] < 0.0) s.Rs[j * T3F_MAX_RANK + j] = -s.Rs[j * T3F_MAX_RANK + j];
+  for (int j = tid; j < kk; j += nth) {
+    const double dg = fabs(s.Rs[j * T3F_MAX_RANK + j]);
+    s.Rs[j * T3F_MAX_RANK + j] = dg;
+    s.rinv[j] = 1.0 / dg;
+  }
   cluster.sync();  // all CTAs are done reading remote W before it is reused below
-  // (D) Q rows = W rows R[:kk,:kk]^{-1} (forward substitution), written in place
-  for (int q = tid; q < nrow; q += nth) {
-    const int r = row0 + q;
-    double* qr = s.W + q * c;
-    for (int l = 0; l < kk; ++l) qr[l] = core[w_addr(lr, r, l, dm, R1)];
-    for (int l = 0; l < kk; ++l) {
-      double acc = qr[l];
-      for (int b = 0; b < l; ++b) acc -= qr[b] * s.Rs[b * T3F_MAX_RANK + l];
-      qr[l] = acc / s.Rs[l * T3F_MAX_RANK + l];
+  // (D) Q rows = W rows R[:kk,:kk]^{-1}: reload the original rows, forward substitution
+  for (int e = tid; e < nrow * kk; e += nth) {
+    const int q = e / kk, l = e % kk;
+    s.W[q * c + l] = core[w_addr(lr, row0 + q, l, dm, R1)];
+  }
+  __syncthreads();
+  // right-looking substitution: once q_b is known it is removed from every later column.
+  // Eight lanes share a row: lane g keeps the columns l = g (mod 8) of the row in registers
+  // and the owner of column b broadcasts q_b with a shuffle.
+  if (kk <= 64) {
+    const int g = tid % 8;
+    const int nq = (nrow + (nth / 8) - 1) / (nth / 8);
+    for (int it = 0; it < nq; ++it) {
+      const int q = it * (nth / 8) + tid / 8;
+      const bool qv = q < nrow;
+      double* qr = s.W + (qv ? q : 0) * c;
+      double x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int l = g + 8 * u;
+        x[u] = (qv && l < kk) ? qr[l] : 0.0;
+      }
+      for (int b = 0; b < kk; ++b) {
+        const int ob = b % 8, ub = b / 8;
+        double xb = 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u == ub) xb = x[u];
+        xb = __shfl_sync(0xffffffffu, xb * s.rinv[b], ob, 8);
+        if (g == ob) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (u == ub) x[u] = xb;
+        }
+        const double* rb = s.Rs + b * T3F_MAX_RANK;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int l = g + 8 * u;
+          if (l > b && l < kk) x[u] = fma(-xb, rb[l], x[u]);
+        }
+      }
+      if (qv) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int l = g + 8 * u;
+          if (l < kk) qr[l] = x[u];
+        }
+      }
     }
   }
   __syncthreads();
@@ -204,25 +236,25 @@ __device__ void qr_step(const OrthArgs& a, double* base, Dims* dims, int k, int 
     core[w_addr(lr, row0 + q, l, nd, R1)] = s.W[q * c + l];
   }
   __syncthreads();
-  // (E) push R into the neighbour core, split across the cluster
+  // (E) push R into the neighbour core, split across the cluster; operands staged in smem
   if (lr) {
     const Dims nx = dims[k + 1];  // (c, n', r2)
     double* nb = base + a.coff[k + 1];
     const int R1n = a.R1[k + 1];
     const int cols = nx.n * nx.r1;
     const int cp = (cols + P - 1) / P, c0 = rank * cp, nc = max(0, min(cols, c0 + cp) - c0);
-    for (int e = tid; e < kk * nc; e += nth) {
-      const int a2 = e / nc, q = c0 + e % nc;
+    for (int e = tid; e < c * nc; e += nth) {
+      const int al = e / nc, q = c0 + e % nc;
       const int i = q / nx.r1, b = q % nx.r1;
-      double acc = 0.0;
-      for (int al = a2; al < c; ++al) acc += s.Rs[a2 * T3F_MAX_RANK + al] * nb[((long long)al * nx.n + i) * R1n + b];
-      s.W[e] = acc;
+      s.W[e] = nb[((long long)al * nx.n + i) * R1n + b];
     }
     __syncthreads();
     for (int e = tid; e < kk * nc; e += nth) {
-      const int a2 = e / nc, q = c0 + e % nc;
+      const int a2 = e / nc, qq = e % nc, q = c0 + qq;
       const int i = q / nx.r1, b = q % nx.r1;
-      nb[((long long)a2 * nx.n + i) * R1n + b] = s.W[e];
+      double acc = 0.0;
+      for (int al = a2; al < c; ++al) acc += s.Rs[a2 * T3F_MAX_RANK + al] * s.W[al * nc + qq];
+      nb[((long long)a2 * nx.n + i) * R1n + b] = acc;
     }
   } else {
     const Dims pv = dims[k - 1];  // (r0', n', c)
@@ -230,16 +262,16 @@ __device__ void qr_step(const OrthArgs& a, double* base, Dims* dims, int k, int 
     const int R1p = a.R1[k - 1];
     const int rows = pv.r0 * pv.n;
     const int rq = (rows + P - 1) / P, q0 = rank * rq, nq = max(0, min(rows, q0 + rq) - q0);
-    for (int e = tid; e < nq * kk; e += nth) {
-      const int q = q0 + e / kk, a2 = e % kk;
-      double acc = 0.0;
-      for (int b = a2; b < c; ++b) acc += pb[(long long)q * R1p + b] * s.Rs[a2 * T3F_MAX_RANK + b];
-      s.W[e] = acc;
+    for (int e = tid; e < nq * c; e += nth) {
+      const int q = e / c, b = e % c;
+      s.W[e] = pb[(long long)(q0 + q) * R1p + b];
     }
     __syncthreads();
     for (int e = tid; e < nq * kk; e += nth) {
-      const int q = q0 + e / kk, a2 = e % kk;
-      pb[(long long)q * R1p + a2] = s.W[e];
+      const int q = e / kk, a2 = e % kk;
+      double acc = 0.0;
+      for (int b = a2; b < c; ++b) acc += s.W[q * c + b] * s.Rs[a2 * T3F_MAX_RANK + b];
+      pb[(long long)(q0 + q) * R1p + a2] = acc;
     }
   }
   __syncthreads();
@@ -285,11 +317,13 @@ __global__ void __launch_bounds__(kOrthThreads) k_orth(const __grid_constant__ O
   OrthSmem s;
   s.W = smd;
   s.Rs = s.W + (size_t)a.rows_per * T3F_MAX_RANK;
-  s.v = s.Rs + T3F_MAX_RANK * T3F_MAX_RANK;
-  s.dots = s.v + a.rows_per;
-  s.wsum = s.dots + T3F_MAX_RANK;
-  s.red = s.wsum + T3F_MAX_RANK;
-  s.wred = s.red + 8;
+  s.pub = s.Rs + T3F_MAX_RANK * T3F_MAX_RANK;
+  s.rowj = s.pub + 2 * T3F_MAX_RANK;
+  s.gsum = s.rowj + 2 * T3F_MAX_RANK;
+  s.wj = s.gsum + T3F_MAX_RANK;
+  s.rinv = s.wj + T3F_MAX_RANK;
+  s.tv = s.rinv + T3F_MAX_RANK;
+  s.refl = s.tv + a.rows_per;
   double* base = a.work + (long long)obj * a.obj_stride;
   for (int k = threadIdx.x; k < d; k += blockDim.x) dims[k] = Dims{X.r[k], X.n[k], X.r[k + 1]};
   // load X (split across the cluster) into the padded FP64 working cores
@@ -324,8 +358,7 @@ static long long orth_obj_stride(const TTV& X, long long* coff, int* R1) {
 }
 
 static size_t orth_smem(int rows_per) {
-  return sizeof(double) * ((size_t)rows_per * T3F_MAX_RANK + T3F_MAX_RANK * T3F_MAX_RANK + rows_per +
-                           2 * T3F_MAX_RANK + 8 + kOrthThreads / 32);
+  return sizeof(double) * ((size_t)rows_per * T3F_MAX_RANK + T3F_MAX_RANK * T3F_MAX_RANK + 7 * T3F_MAX_RANK + rows_per + 4);
 }
 
 // Largest supported cluster size (16 if allowed, else 8), cached per process.
