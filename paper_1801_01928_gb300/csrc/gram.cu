@@ -222,6 +222,7 @@ extern "C" t3f_status t3f_gram(const t3f_tt* A, const t3f_tt* B, float* G, int32
   if (math != T3F_MATH_FP32) return T3F_ERR_UNSUPPORTED;
   (void)ws;
   (void)ws_bytes;
+  if (gram_tile_supported(va, vb)) return run_gram_tile(va, vb, G, (cudaStream_t)stream);
   return run_pair_sweep(va, vb, 0, G, nullptr, nullptr, (cudaStream_t)stream);
 }
 

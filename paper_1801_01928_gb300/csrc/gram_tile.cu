@@ -1,0 +1,426 @@
+// Tiled Gram sweep (paper Section 4, 'gram' / 'norm'; batches of Section 3.1).
+//
+// A CTA owns a tile of na x nb pairs (a, b) and carries their left partials
+// M^{ab} (r^A_k x r^B_k) in shared memory through the whole sweep. Per mode slice i of core k
+// the update M' = sum_i A_i^T (M B_i) is two batched products with 4 x 4 register blocks:
+//   GEMM1  T[a][al][b][bp]   = sum_be M[a][al][b][be] B_b,i[be][bp]     (stacked over a)
+//   GEMM2  M'[a][ap][b][bp] += sum_al A_a,i[al][ap] T[a][al][b][bp]     (stacked over b)
+// Ranks are zero-padded to multiples of 4 (RA, RB). The operands of the next slice are
+// loaded into registers while the current slice computes. The same kernel serves uniform
+// batches (tile from blockIdx) and ragged, rank-bucketed groups of objects (tiles taken from
+// a work list by persistent CTAs, see gram_groups.cu).
+#include "t3f_internal.cuh"
+
+namespace t3f {
+
+// Per-object core access: uniform batch (TTV) or a table of per-object offsets and ranks.
+struct ObjTable {
+  const long long* off;   // [obj][d] element offset of core k
+  const int* rk;          // [obj][d + 1] ranks
+  int d;
+};
+
+struct GramTileArgs {
+  // uniform mode
+  TTV A, B;
+  int TA, TB;           // tile objects (uniform mode)
+  int RA, RB;           // padded ranks (uniform mode)
+  // table mode (groups)
+  ObjTable tab;
+  const void* gcores;   // cores of all objects
+  const int* nmodes;    // [group][d] modes
+  const int* items;     // work list: [item][8] = group, a0, na, b0, nb, RA, RB, sym
+  int nitems;
+  int* head;            // queue head (table mode)
+  const int* gstart;    // [group + 1] first object of each group
+  const int* gd;        // [group] d of the group
+  float* gout;          // [group][S][S] Gram matrices (S = objects of the group)
+  const long long* gout_off;  // [group] offset of the group's matrix
+  // common
+  float* out;           // uniform: [bA][bB]
+  int mode;             // 0 uniform, 1 table
+  int dtype;
+  int maxTA, maxTB, maxRA, maxRB;
+};
+
+__device__ __forceinline__ void fma44(float (&acc)[4][4], const float4 a, const float4 b) {
+  const float av[4] = {a.x, a.y, a.z, a.w};
+  const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+}
+
+template <typename T>
+__device__ __forceinline__ float ldv(const void* p, long long i) {
+  return ldf<T>(static_cast<const T*>(p), i);
+}
+
+constexpr int kGTMaxBlk = 2;   // output blocks per thread
+constexpr int kGTMaxPF = 16;   // staging elements per thread and slice
+
+template <typename ST>
+__global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramTileArgs g) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_item[8];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  // staging buffers sized for the largest tile of the launch
+  float* MT = sm;                                                        // [nb][RB][na][RA]
+  float* TT = MT + (size_t)g.maxTA * g.maxRA * g.maxTB * g.maxRB;        // [na][RA][TR]
+  float* As = TT + (size_t)g.maxTA * g.maxRA * (((g.maxTB * g.maxRB + 31) / 32) * 32);  // [na][RA][RA]
+  float* Bs = As + (size_t)g.maxTA * g.maxRA * g.maxRA;                  // [nb][RB][RB]
+
+  for (int it = 0;; ++it) {
+    int grp = 0, a0, na, b0, nb, RA, RB, sym = 0, d;
+    if (g.mode == 0) {
+      if (it > 0) break;
+      const int ntb = (g.B.batch + g.TB - 1) / g.TB;
+      a0 = (blockIdx.x / ntb) * g.TA;
+      b0 = (blockIdx.x % ntb) * g.TB;
+      na = min(g.TA, g.A.batch - a0);
+      nb = min(g.TB, g.B.batch - b0);
+      RA = g.RA;
+      RB = g.RB;
+      d = g.A.d;
+    } else {
+      __syncthreads();
+      if (tid == 0) {
+        const int w = atomicAdd(g.head, 1);
+        s_item[7] = w;
+        if (w < g.nitems)
+          for (int q = 0; q < 7; ++q) s_item[q] = g.items[w * 8 + q];
+      }
+      __syncthreads();
+      if (s_item[7] >= g.nitems) break;
+      grp = s_item[0];
+      a0 = s_item[1];
+      na = s_item[2];
+      b0 = s_item[3];
+      nb = s_item[4];
+      RA = s_item[5];
+      RB = s_item[6];
+      sym = g.items[s_item[7] * 8 + 7];
+      d = g.gd[grp];
+    }
+    const int QA = RA / 4, QB = RB / 4;
+    const int nblk = na * QA * nb * QB;           // 4x4 blocks of one partial tile
+    // T rows are padded to whole 128-byte lines and their 16-byte units XOR-swizzled by
+    // (row / 4) mod 8, so lanes storing consecutive 4-row blocks hit different banks while
+    // lanes reading one row still read a permutation of consecutive units
+    const int TR = ((nb * RB + 31) / 32) * 32;
+    const int szM = na * RA * nb * RB;
+    // initial partials: M = 1 at (al, be) = (0, 0) of every pair
+    for (int e = tid; e < szM; e += nth) {
+      const int al = e % RA, a = (e / RA) % na, be = (e / (RA * na)) % RB;
+      MT[e] = (al == 0 && be == 0) ? 1.0f : 0.0f;
+      (void)a;
+    }
+    // per-object access helpers
+    auto objA = [&](int t, int k, long long* base, int* r0, int* r1, int* n) {
+      if (g.mode == 0) {
+        *base = core_base(g.A, k, a0 + t);
+        *r0 = g.A.r[k];
+        *r1 = g.A.r[k + 1];
+        *n = g.A.n[k];
+      } else {
+        const int o = a0 + t;
+        *base = g.tab.off[(long long)o * g.tab.d + k];
+        *r0 = g.tab.rk[(long long)o * (g.tab.d + 1) + k];
+        *r1 = g.tab.rk[(long long)o * (g.tab.d + 1) + k + 1];
+        *n = g.nmodes[grp * g.tab.d + k];
+      }
+    };
+    auto objB = [&](int t, int k, long long* base, int* r0, int* r1, int* n) {
+      if (g.mode == 0) {
+        *base = core_base(g.B, k, b0 + t);
+        *r0 = g.B.r[k];
+        *r1 = g.B.r[k + 1];
+        *n = g.B.n[k];
+      } else {
+        const int o = b0 + t;
+        *base = g.tab.off[(long long)o * g.tab.d + k];
+        *r0 = g.tab.rk[(long long)o * (g.tab.d + 1) + k];
+        *r1 = g.tab.rk[(long long)o * (g.tab.d + 1) + k + 1];
+        *n = g.nmodes[grp * g.tab.d + k];
+      }
+    };
+    const void* Ap = g.mode == 0 ? g.A.p : g.gcores;
+    const void* Bp = g.mode == 0 ? g.B.p : g.gcores;
+    const int szA = na * RA * RA, szS = szA + nb * RB * RB;
+    // this thread's staging elements (fixed for the tile): side, object, row, col
+    int sdesc[kGTMaxPF];
+#pragma unroll
+    for (int u = 0; u < kGTMaxPF; ++u) {
+      const int e = tid + u * nth;
+      int dsc = -1;
+      if (e < szS) {
+        if (e < szA) {
+          const int t = e / (RA * RA), q = e % (RA * RA);
+          dsc = (0 << 30) | (t << 16) | ((q / RA) << 8) | (q % RA);
+        } else {
+          const int e2 = e - szA;
+          const int t = e2 / (RB * RB), q = e2 % (RB * RB);
+          dsc = (1 << 30) | (t << 16) | ((q / RB) << 8) | (q % RB);
+        }
+      }
+      sdesc[u] = dsc;
+    }
+    // stage slice i of core k into `buf` (zero-padded): FP32 cores are copied asynchronously
+    // (cp.async, 4 bytes, zero-fill outside the ranks), BF16 cores converted on the way
+    auto stage = [&](int k, int i, float* buf) {
+      int rA0, rA1, nA, rB0, rB1, nB;
+      long long bA0, bB0;
+      objA(0, k, &bA0, &rA0, &rA1, &nA);
+      objB(0, k, &bB0, &rB0, &rB1, &nB);
+#pragma unroll
+      for (int u = 0; u < kGTMaxPF; ++u) {
+        const int dsc = sdesc[u];
+        if (dsc < 0) continue;
+        const int side = dsc >> 30, t = (dsc >> 16) & 0x3fff, row = (dsc >> 8) & 0xff, col = dsc & 0xff;
+        long long base;
+        int r0, r1, n;
+        if (side == 0) objA(t, k, &base, &r0, &r1, &n);
+        else objB(t, k, &base, &r0, &r1, &n);
+        const bool ok = row < r0 && col < r1 && i < n;
+        const long long idx = ok ? base + ((long long)row * n + i) * r1 + col : base;
+        const void* src = side == 0 ? Ap : Bp;
+        float* dst = buf + tid + u * nth;
+        if (sizeof(ST) == 4) {
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+          const float* gp = static_cast<const float*>(src) + idx;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gp), "r"(ok ? 4 : 0));
+        } else {
+          *dst = ok ? ldv<ST>(src, idx) : 0.0f;
+        }
+      }
+      if (sizeof(ST) == 4) asm volatile("cp.async.commit_group;\n" ::);
+    };
+    // this thread's output blocks: GEMM1 in row-major order, GEMM2 in column-major order
+    int g1m[kGTMaxBlk], g1b[kGTMaxBlk], g1t[kGTMaxBlk];
+    int g2a[kGTMaxBlk], g2t[kGTMaxBlk], g2w[kGTMaxBlk];
+#pragma unroll
+    for (int q = 0; q < kGTMaxBlk; ++q) {
+      const int blk = tid + q * nth;
+      g1m[q] = g1b[q] = g1t[q] = g2a[q] = g2t[q] = g2w[q] = -1;
+      if (blk < nblk) {
+        {
+          const int qa = blk % QA, a = (blk / QA) % na, qb = (blk / (QA * na)) % QB, b = blk / (QA * na * QB);
+          g1m[q] = (b * RB * na + a) * RA + 4 * qa;
+          g1b[q] = b * RB * RB + 4 * qb;
+          g1t[q] = (a * RA + 4 * qa) * TR;                 // row base; unit = b * QB + qb
+          g1b[q] |= (b * QB + qb) << 20;
+        }
+        {
+          const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+          g2a[q] = a * RA * RA + 4 * qa;
+          g2t[q] = (a * RA) * TR;                          // row base of al = 0
+          g2a[q] |= (b * QB + qb) << 20;
+          g2w[q] = ((b * RB + 4 * qb) * na + a) * RA + 4 * qa;
+        }
+      }
+    }
+    const int mstep = na * RA;
+    const int stride = g.maxTA * g.maxRA * g.maxRA + g.maxTB * g.maxRB * g.maxRB;
+    float* stg[2] = {As, As + stride};
+    int k = 0, i = 0, cur = 0;
+    stage(0, 0, stg[0]);
+    float acc[kGTMaxBlk][4][4];
+    while (k < d) {
+      int nk;
+      {
+        long long bb;
+        int r0, r1;
+        objA(0, k, &bb, &r0, &r1, &nk);
+      }
+      if (i == 0) {
+#pragma unroll
+        for (int q = 0; q < kGTMaxBlk; ++q)
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[q][x][y] = 0.0f;
+      }
+      // issue the next slice, then wait for the current one
+      {
+        int k2 = k, i2 = i + 1;
+        if (i2 >= nk) {
+          k2 = k + 1;
+          i2 = 0;
+        }
+        if (k2 < d) {
+          stage(k2, i2, stg[cur ^ 1]);
+          if (sizeof(ST) == 4) asm volatile("cp.async.wait_group 1;\n" ::);
+        } else if (sizeof(ST) == 4) {
+          asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+      }
+      __syncthreads();
+      const float* Asb = stg[cur];
+      const float* Bsb = stg[cur] + szA;
+      // GEMM1: T[a][al][b][bp] = sum_be MT[b][be][a][al] Bs[b][be][bp]
+#pragma unroll
+      for (int q = 0; q < kGTMaxBlk; ++q) {
+        if (g1m[q] < 0) continue;
+        float t4[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
+        const float* mrow = MT + g1m[q];
+        const float* brow = Bsb + (g1b[q] & 0xfffff);
+        for (int be = 0; be < RB; ++be)
+          fma44(t4, *reinterpret_cast<const float4*>(mrow + be * mstep), *reinterpret_cast<const float4*>(brow + be * RB));
+        const int unit = g1b[q] >> 20;
+        const int row0t = g1t[q] / TR;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int r = row0t + x;
+          *reinterpret_cast<float4*>(TT + r * TR + 4 * (unit ^ ((r >> 2) & 7))) =
+              make_float4(t4[x][0], t4[x][1], t4[x][2], t4[x][3]);
+        }
+      }
+      __syncthreads();
+      // GEMM2: acc[a][ap][b][bp] += sum_al As[a][al][ap] T[a][al][b][bp]
+#pragma unroll
+      for (int q = 0; q < kGTMaxBlk; ++q) {
+        if (g2a[q] < 0) continue;
+        const float* arow = Asb + (g2a[q] & 0xfffff);
+        const int unit = g2a[q] >> 20;
+        const int rbase = g2t[q] / TR;
+        for (int al = 0; al < RA; ++al) {
+          const int r = rbase + al;
+          fma44(acc[q], *reinterpret_cast<const float4*>(arow + al * RA),
+                *reinterpret_cast<const float4*>(TT + r * TR + 4 * (unit ^ ((r >> 2) & 7))));
+        }
+      }
+      __syncthreads();  // stg[cur] and TT are free again
+      cur ^= 1;
+      if (++i >= nk) {
+        // end of core k: the accumulated blocks become the next partial (transposed layout)
+#pragma unroll
+        for (int q = 0; q < kGTMaxBlk; ++q) {
+          if (g2w[q] < 0) continue;
+#pragma unroll
+          for (int y = 0; y < 4; ++y)
+            *reinterpret_cast<float4*>(MT + g2w[q] + y * mstep) =
+                make_float4(acc[q][0][y], acc[q][1][y], acc[q][2][y], acc[q][3][y]);
+        }
+        i = 0;
+        ++k;
+      }
+    }
+    __syncthreads();
+    // <A_a, B_b> = M_d[0][0]
+    for (int p = tid; p < na * nb; p += nth) {
+      const int a = p / nb, b = p % nb;
+      const float v = MT[((size_t)b * RB * na + a) * RA];
+      if (g.mode == 0) {
+        g.out[(long long)(a0 + a) * g.B.batch + (b0 + b)] = v;
+      } else {
+        const int S = g.gstart[grp + 1] - g.gstart[grp];
+        const int la = a0 + a - g.gstart[grp], lb = b0 + b - g.gstart[grp];
+        float* o = g.gout + g.gout_off[grp];
+        o[(long long)la * S + lb] = v;
+        if (sym) o[(long long)lb * S + la] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+
+static int pad4(int r) { return (r + 3) & ~3; }
+
+size_t gram_tile_smem(int TA, int TB, int RA, int RB) {
+  const size_t TR = ((size_t)(TB * RB + 31) / 32) * 32;
+  return sizeof(float) * ((size_t)TA * RA * TB * RB + (size_t)TA * RA * TR + 2 * ((size_t)TA * RA * RA + (size_t)TB * RB * RB));
+}
+
+// Largest tile (TA = TB) whose blocks and staging fit one CTA of `threads`.
+void plan_gram_tile(int RA, int RB, int batchA, int batchB, int* TA, int* TB, int* threads) {
+  // cost model: pair-slots per SM of the most loaded SM (whole waves of CTAs), with a small
+  // preference for larger tiles (operand reuse)
+  *TA = 1;
+  *TB = 1;
+  *threads = 128;
+  double best = 1e300;
+  int sms = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      int v = 0;
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) sms = v;
+    }
+  }
+  for (int ta = 1; ta <= 16 && ta <= batchA; ++ta) {
+    for (int tb = 1; tb <= 16 && tb <= batchB; ++tb) {
+      const int nblk = ta * (RA / 4) * tb * (RB / 4);
+      for (int th = 128; th <= 512; th *= 2) {
+        if (th * kGTMaxBlk < nblk) continue;
+        if (ta * RA * RA + tb * RB * RB > th * kGTMaxPF) continue;
+        const size_t smem = gram_tile_smem(ta, tb, RA, RB);
+        if (smem > 200 * 1024) continue;
+        int cps = 65536 / (th * 128);
+        const int cps_smem = (int)((228 * 1024) / (smem + 2048));
+        if (cps_smem < cps) cps = cps_smem;
+        if (cps < 1) continue;
+        const long long tiles = (long long)((batchA + ta - 1) / ta) * ((batchB + tb - 1) / tb);
+        const long long per_sm = (tiles + (long long)sms * cps - 1) / ((long long)sms * cps) * cps;
+        // padded work of the most loaded SM, discounted for reuse of larger tiles
+        const int rounds = (nblk + th - 1) / th;               // blocks per thread (max)
+        const double balance = (double)nblk / ((double)rounds * th);
+        const double work = (double)per_sm * ta * tb * (1.0 + 0.5 / ta + 0.5 / tb) / balance;
+        if (work < best - 1e-9) {
+          best = work;
+          *TA = ta;
+          *TB = tb;
+          *threads = th;
+        }
+      }
+    }
+  }
+}
+
+bool gram_tile_supported(const TTV& A, const TTV& B) {
+  const int RA = pad4(A.rmax), RB = pad4(B.rmax);
+  if (RA > 64 || RB > 64) return false;
+  int ta, tb, th;
+  plan_gram_tile(RA, RB, A.batch, B.batch, &ta, &tb, &th);
+  return ta * RA * RA + tb * RB * RB <= th * kGTMaxPF && ta * (RA / 4) * tb * (RB / 4) <= th * kGTMaxBlk;
+}
+
+t3f_status run_gram_tile(const TTV& A, const TTV& B, float* out, cudaStream_t s) {
+  GramTileArgs g;
+  memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.B = B;
+  g.RA = pad4(A.rmax);
+  g.RB = pad4(B.rmax);
+  int threads;
+  plan_gram_tile(g.RA, g.RB, A.batch, B.batch, &g.TA, &g.TB, &threads);
+  g.maxTA = g.TA;
+  g.maxTB = g.TB;
+  g.maxRA = g.RA;
+  g.maxRB = g.RB;
+  g.out = out;
+  g.mode = 0;
+  g.dtype = A.dtype;
+  const size_t smem = gram_tile_smem(g.TA, g.TB, g.RA, g.RB);
+  const long long grid = (long long)((A.batch + g.TA - 1) / g.TA) * ((B.batch + g.TB - 1) / g.TB);
+  if (grid > 0x7fffffff) return T3F_ERR_UNSUPPORTED;
+  if (A.dtype == T3F_F32) {
+    auto kern = k_gram_tile<float>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<(unsigned)grid, threads, smem, s>>>(g);
+  } else {
+    auto kern = k_gram_tile<__nv_bfloat16>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<(unsigned)grid, threads, smem, s>>>(g);
+  }
+  return launch_status();
+}
+
+}  // namespace t3f

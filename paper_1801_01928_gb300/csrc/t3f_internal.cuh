@@ -82,6 +82,10 @@ t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V,
                      const float* R, const float* P, const float* Q, const long long* ioff, const float* c, float* dZ,
                      float* dc, cudaStream_t s);
 
+// Tiled Gram sweep (gram_tile.cu): ranks <= 64, F32 or BF16 cores.
+bool gram_tile_supported(const TTV& A, const TTV& B);
+t3f_status run_gram_tile(const TTV& A, const TTV& B, float* out, cudaStream_t s);
+
 // Workspace sizes (bytes, header included) of the operations.
 size_t ws_gram_bwd(const TTV& A, const TTV& B);
 size_t ws_norm(const TTV& A);
