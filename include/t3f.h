@@ -250,6 +250,60 @@ t3f_status t3f_project_sum_backward(const t3f_tt* U, const t3f_tt* V, const t3f_
                                     t3f_stream_t stream);
 
 /*
+ * A ragged collection of TT-vectors: object o has d[o] cores, modes
+ * n[noff_o .. noff_o + d[o]) and ranks ranks[roff_o .. roff_o + d[o] + 1), where noff_o and
+ * roff_o are the running sums of d and d + 1 over the preceding objects. Its core k is
+ * row-major [r_{k-1}][n_k][r_k] and starts at element obj_off[o] + sum_{j<k} r_j n_j r_{j+1}
+ * of `cores`. Host arrays are read during the call only.
+ */
+typedef struct {
+  int32_t count;            /* number of objects, >= 1 */
+  const int32_t* d;         /* host [count] */
+  const int32_t* n;         /* host [sum d] */
+  const int32_t* ranks;     /* host [sum (d + 1)], first and last rank of every object 1 */
+  const int64_t* obj_off;   /* host [count] element offset of each object's first core */
+  void* cores;              /* device */
+  int32_t dtype;            /* T3F_F32 or T3F_BF16 */
+} t3f_tt_ragged;
+
+/*
+ * Gram matrices within groups of a ragged collection (paper Section 4 'gram' / 'norm' over
+ * uneven batches, Section 3.1): objects [gstart[g], gstart[g+1]) form group g and must share
+ * d and modes; ranks may differ per object (<= T3F_MAX_RANK). Group g's output is the
+ * S_g x S_g matrix G_g[a][b] = <X_a, X_b> (local indices, row-major); the groups' matrices
+ * are concatenated in `out` (device float). norms (device double [count], nullable) receives
+ * sqrt(G_g[a][a]) in FP64.
+ * Scheduling: the objects of every group are ordered by rank into buckets {<=8, <=16, <=32,
+ * <=64}; tiles[b] (host int32[4], NULL = built-in defaults, each in 1..16) is the tile side
+ * used for bucket b. The upper triangle of pairs is cut into tiles, sorted by cost and drained
+ * by ONE persistent launch.
+ * t3f_gram_groups_prepare writes the work list and object tables into `ws` (host-to-device
+ * copies; call it once, outside stream capture). t3f_gram_groups and
+ * t3f_gram_groups_backward then only launch kernels (memsets + kernels), so they can be
+ * captured in a CUDA graph and replayed while X's shapes and `tiles` are unchanged.
+ * ws_bytes >= t3f_gram_groups_workspace_size(X, ngroups, gstart, tiles).
+ */
+size_t t3f_gram_groups_workspace_size(const t3f_tt_ragged* X, int32_t ngroups,
+                                      const int32_t* gstart, const int32_t* tiles);
+t3f_status t3f_gram_groups_prepare(const t3f_tt_ragged* X, int32_t ngroups,
+                                   const int32_t* gstart, const int32_t* tiles, void* ws,
+                                   size_t ws_bytes, t3f_stream_t stream);
+t3f_status t3f_gram_groups(const t3f_tt_ragged* X, int32_t ngroups, const int32_t* gstart,
+                           const int32_t* tiles, float* out, double* norms, void* ws,
+                           size_t ws_bytes, t3f_stream_t stream);
+
+/*
+ * Adjoint of t3f_gram_groups: dcores (device float, the layout of X's cores with F32
+ * elements) receives the cotangent of sum_g sum_ab dout_g[a][b] <X_a, X_b> for the
+ * concatenated per-group cotangents dout (device float, like `out`). Computed per group and
+ * pair of rank buckets on zero-padded uniform batches; requires the same prepared `ws`.
+ */
+t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t ngroups,
+                                    const int32_t* gstart, const int32_t* tiles,
+                                    const float* dout, float* dcores, void* ws,
+                                    size_t ws_bytes, t3f_stream_t stream);
+
+/*
  * Device-side error word of the last call that used `ws` (enqueued on `stream`, read after
  * a synchronisation): 0 = none, T3F_ERR_ARG = an index tuple was out of range,
  * T3F_ERR_TIMEOUT = a bounded wait ran out. Synchronises `stream`.

@@ -7,7 +7,8 @@ The Python layer is argument marshalling over libt3f.so; import fails loudly at 
 the library has not been built (``python -m paper_1801_01928_gb300.build``).
 """
 from ._binding import (  # noqa: F401
-    BF16, EXPORTS, F32, F64, LIB_PATH, T3FError, TT, device_status, gather, gather_backward,
+    BF16, DEFAULT_TILES, EXPORTS, F32, F64, LIB_PATH, RaggedTT, T3FError, TT, autotune_gram_groups,
+    device_status, gather, gather_backward, gram_groups, gram_groups_backward, gram_groups_prepare,
     gram, gram_backward, launch_count, load, matvec, matvec_backward, norm, orth_ranks, orthogonalize,
     project_sum, project_sum_backward,
 )

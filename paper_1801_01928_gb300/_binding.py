@@ -317,3 +317,153 @@ def device_status(ws: torch.Tensor) -> int:
 def launch_count() -> int:
     """Kernels launched by libt3f in this process so far."""
     return int(_lib().t3f_launch_count())
+
+
+# ---------------------------------------------------------------------------------------
+# Ragged collections and grouped Gram matrices
+# ---------------------------------------------------------------------------------------
+
+class _RDesc(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("d", ctypes.POINTER(ctypes.c_int32)),
+                ("n", ctypes.POINTER(ctypes.c_int32)), ("ranks", ctypes.POINTER(ctypes.c_int32)),
+                ("obj_off", ctypes.POINTER(ctypes.c_int64)), ("cores", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32)]
+
+
+_RP = ctypes.POINTER(_RDesc)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_SIGS.update({
+    "t3f_gram_groups_workspace_size": (ctypes.c_size_t, [_RP, ctypes.c_int32, _I32P, _I32P]),
+    "t3f_gram_groups_prepare": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, _VP, _SZ, _VP]),
+    "t3f_gram_groups": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, _VP, _VP, _VP, _SZ, _VP]),
+    "t3f_gram_groups_backward": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, _VP, _VP, _VP, _SZ, _VP]),
+})
+EXPORTS = tuple(_SIGS)
+
+
+class RaggedTT:
+    """TT-vectors of different d, modes and ranks stored back to back in one flat tensor:
+    object o's cores (r_{k-1}, n_k, r_k) follow each other starting at element offsets[o]."""
+
+    def __init__(self, data: torch.Tensor, dims, modes, ranks, offsets):
+        self.data = data
+        self.dims = [int(v) for v in dims]
+        self.modes = [[int(v) for v in m] for m in modes]
+        self.ranks = [[int(v) for v in r] for r in ranks]
+        self.offsets = [int(v) for v in offsets]
+        self.count = len(self.dims)
+        self._keep = None
+
+    @staticmethod
+    def object_numel(modes, ranks):
+        return sum(ranks[k] * modes[k] * ranks[k + 1] for k in range(len(modes)))
+
+    @classmethod
+    def from_objects(cls, objects, dtype=torch.float32, device="cuda"):
+        """objects: list of per-object core lists, core k shaped (r_{k-1}, n_k, r_k)."""
+        flat, dims, modes, ranks, offs, o = [], [], [], [], [], 0
+        for cores in objects:
+            ts = [torch.as_tensor(c) for c in cores]
+            dims.append(len(ts))
+            modes.append([t.shape[1] for t in ts])
+            ranks.append([ts[0].shape[0]] + [t.shape[2] for t in ts])
+            offs.append(o)
+            for t in ts:
+                flat.append(t.reshape(-1))
+                o += t.numel()
+        data = torch.cat(flat).to(dtype=dtype).to(device)
+        return cls(data, dims, modes, ranks, offs)
+
+    def object_cores(self, o):
+        out, off = [], self.offsets[o]
+        for k in range(self.dims[o]):
+            r0, n, r1 = self.ranks[o][k], self.modes[o][k], self.ranks[o][k + 1]
+            out.append(self.data[off:off + r0 * n * r1].view(r0, n, r1))
+            off += r0 * n * r1
+        return out
+
+    def desc(self) -> _RDesc:
+        d = _i32(self.dims)
+        n = _i32([v for m in self.modes for v in m])
+        r = _i32([v for rr in self.ranks for v in rr])
+        off = (ctypes.c_int64 * self.count)(*self.offsets)
+        self._keep = (d, n, r, off)
+        return _RDesc(self.count, d, n, r, off, ctypes.c_void_p(self.data.data_ptr()), _CODE[self.data.dtype])
+
+
+def _tiles_arg(tiles):
+    return None if tiles is None else _i32(tiles)
+
+
+def gram_groups_prepare(X: RaggedTT, gstart, tiles=None) -> torch.Tensor:
+    """Workspace holding the work list and object tables of the grouped Gram (host copies)."""
+    gs = _i32(gstart)
+    tl = _tiles_arg(tiles)
+    nbytes = _lib().t3f_gram_groups_workspace_size(ctypes.byref(X.desc()), len(gstart) - 1, gs, tl)
+    if nbytes == 0:
+        raise T3FError(-2, "t3f_gram_groups_workspace_size")
+    ws = torch.empty(int(nbytes), dtype=torch.uint8, device=X.data.device)
+    _check(_lib().t3f_gram_groups_prepare(ctypes.byref(X.desc()), len(gstart) - 1, gs, tl, _ptr(ws), ws.numel(),
+                                          _stream(X.data.device)), "t3f_gram_groups_prepare")
+    return ws
+
+
+def gram_groups(X: RaggedTT, gstart, ws: torch.Tensor, tiles=None, want_norms=True, out=None, norms=None):
+    """Concatenated per-group Gram matrices (and FP64 norms) from a prepared workspace."""
+    dev = X.data.device
+    total = sum((gstart[g + 1] - gstart[g]) ** 2 for g in range(len(gstart) - 1))
+    out = torch.empty(total, dtype=torch.float32, device=dev) if out is None else out
+    if want_norms and norms is None:
+        norms = torch.empty(X.count, dtype=torch.float64, device=dev)
+    _check(_lib().t3f_gram_groups(ctypes.byref(X.desc()), len(gstart) - 1, _i32(gstart), _tiles_arg(tiles), _ptr(out),
+                                  _ptr(norms) if want_norms else None, _ptr(ws), ws.numel(), _stream(dev)),
+           "t3f_gram_groups")
+    return out, (norms if want_norms else None)
+
+
+def gram_groups_backward(X: RaggedTT, gstart, ws: torch.Tensor, dout: torch.Tensor, tiles=None, dcores=None):
+    dev = X.data.device
+    dcores = torch.empty(X.data.numel(), dtype=torch.float32, device=dev) if dcores is None else dcores
+    _check(_lib().t3f_gram_groups_backward(ctypes.byref(X.desc()), len(gstart) - 1, _i32(gstart), _tiles_arg(tiles),
+                                           _ptr(dout), _ptr(dcores), _ptr(ws), ws.numel(), _stream(dev)),
+           "t3f_gram_groups_backward")
+    return dcores
+
+
+DEFAULT_TILES = (10, 6, 3, 1)
+
+
+def autotune_gram_groups(X: RaggedTT, gstart, candidates=(1, 2, 3, 4, 6, 8, 10, 12, 16), reps=3):
+    """Rank-bucket tile sides chosen by timing the grouped forward sweep on X itself:
+    coordinate search over the four buckets, starting from the defaults. Returns a tuple of
+    four tile sides; infeasible candidates (tiles that do not fit one CTA) are skipped."""
+    dev = X.data.device
+
+    def time_tiles(tl):
+        try:
+            ws = gram_groups_prepare(X, gstart, tl)
+        except T3FError:
+            return float("inf")
+        gram_groups(X, gstart, ws, tl, want_norms=False)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            gram_groups(X, gstart, ws, tl, want_norms=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    best = list(DEFAULT_TILES)
+    best_t = time_tiles(tuple(best))
+    for b in (3, 2, 1, 0):
+        for c in candidates:
+            if c == best[b]:
+                continue
+            trial = list(best)
+            trial[b] = c
+            t = time_tiles(tuple(trial))
+            if t < best_t:
+                best, best_t = trial, t
+    return tuple(best), best_t

@@ -209,6 +209,43 @@ __global__ void k_sqrt64(const float* in, double* out, int n) {
   if (i < n) out[i] = sqrt(fmax((double)in[i], 0.0));
 }
 
+// Adds the cotangents of sum_ab dG[a,b] <A_a, B_b> to dA and dB (either may be NULL):
+// left partials of every pair are recomputed into the workspace, then the right sweep
+// scatters with atomics.
+t3f_status gram_bwd_accumulate(const TTV& va, const TTV& vb, const float* dG, float* dA, float* dB, void* ws,
+                               size_t ws_bytes, cudaStream_t s) {
+  T3F_CHECK(check_ws(ws, ws_bytes, ws_gram_bwd(va, vb)));
+  GramBwdArgs args;
+  memset(&args, 0, sizeof(args));
+  args.dA = dA;
+  args.dB = dB;
+  if (!dA && !dB) return T3F_OK;
+  float* Mst = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeader);
+  partial_offsets(va, vb, (long long)va.batch * vb.batch, args.ioff);
+  T3F_CHECK(run_pair_sweep(va, vb, 0, nullptr, Mst, args.ioff, s));
+  args.A = va;
+  args.B = vb;
+  args.RA = va.rmax;
+  args.RB = vb.rmax;
+  args.dG = dG;
+  args.Mst = Mst;
+  size_t smem;
+  plan_gram_bwd(va, vb, &args.TA, &args.TB, &smem);
+  const long long grid = (long long)((va.batch + args.TA - 1) / args.TA) * ((vb.batch + args.TB - 1) / args.TB);
+  if (va.dtype == T3F_F32) {
+    auto kern = k_gram_bwd<float>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<(unsigned)grid, 256, smem, s>>>(args);
+  } else {
+    auto kern = k_gram_bwd<__nv_bfloat16>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<(unsigned)grid, 256, smem, s>>>(args);
+  }
+  return launch_status();
+}
+
 }  // namespace t3f
 
 using namespace t3f;
@@ -270,29 +307,6 @@ extern "C" t3f_status t3f_gram_backward(const t3f_tt* A, const t3f_tt* B, const 
   if (args.dB && cudaMemsetAsync(args.dB, 0, sizeof(float) * t3f_packed_size(dB), s) != cudaSuccess)
     return T3F_ERR_CUDA;
   if (!args.dA && !args.dB) return T3F_OK;
-  float* Mst = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeader);
-  partial_offsets(va, vb, (long long)va.batch * vb.batch, args.ioff);
-  // recompute the left partials of every pair (nothing is kept from the forward call)
-  T3F_CHECK(run_pair_sweep(va, vb, 0, nullptr, Mst, args.ioff, s));
-  args.A = va;
-  args.B = vb;
-  args.RA = va.rmax;
-  args.RB = vb.rmax;
-  args.dG = dG;
-  args.Mst = Mst;
-  size_t smem;
-  plan_gram_bwd(va, vb, &args.TA, &args.TB, &smem);
-  const long long grid = (long long)((va.batch + args.TA - 1) / args.TA) * ((vb.batch + args.TB - 1) / args.TB);
-  if (va.dtype == T3F_F32) {
-    auto kern = k_gram_bwd<float>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return T3F_ERR_CUDA;
-    kern<<<(unsigned)grid, 256, smem, s>>>(args);
-  } else {
-    auto kern = k_gram_bwd<__nv_bfloat16>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return T3F_ERR_CUDA;
-    kern<<<(unsigned)grid, 256, smem, s>>>(args);
-  }
-  return launch_status();
+  return gram_bwd_accumulate(va, vb, dG, args.dA, args.dB, ws, ws_bytes, s);
 }
+

@@ -36,6 +36,7 @@ struct GramTileArgs {
   const int* gd;        // [group] d of the group
   float* gout;          // [group][S][S] Gram matrices (S = objects of the group)
   const long long* gout_off;  // [group] offset of the group's matrix
+  const int* perm;            // [sorted object] local index of the object within its group
   // common
   float* out;           // uniform: [bA][bB]
   int mode;             // 0 uniform, 1 table
@@ -65,11 +66,6 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_item[8];
   const int tid = threadIdx.x, nth = blockDim.x;
-  // staging buffers sized for the largest tile of the launch
-  float* MT = sm;                                                        // [nb][RB][na][RA]
-  float* TT = MT + (size_t)g.maxTA * g.maxRA * g.maxTB * g.maxRB;        // [na][RA][TR]
-  float* As = TT + (size_t)g.maxTA * g.maxRA * (((g.maxTB * g.maxRB + 31) / 32) * 32);  // [na][RA][RA]
-  float* Bs = As + (size_t)g.maxTA * g.maxRA * g.maxRA;                  // [nb][RB][RB]
 
   for (int it = 0;; ++it) {
     int grp = 0, a0, na, b0, nb, RA, RB, sym = 0, d;
@@ -109,7 +105,12 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
     // (row / 4) mod 8, so lanes storing consecutive 4-row blocks hit different banks while
     // lanes reading one row still read a permutation of consecutive units
     const int TR = ((nb * RB + 31) / 32) * 32;
+
     const int szM = na * RA * nb * RB;
+    // shared memory of this tile: MT [nb][RB][na][RA], TT [na][RA][TR], two staging buffers
+    float* MT = sm;
+    float* TT = MT + szM;
+    float* As = TT + (size_t)na * RA * TR;
     // initial partials: M = 1 at (al, be) = (0, 0) of every pair
     for (int e = tid; e < szM; e += nth) {
       const int al = e % RA, a = (e / RA) % na, be = (e / (RA * na)) % RB;
@@ -221,8 +222,7 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
       }
     }
     const int mstep = na * RA;
-    const int stride = g.maxTA * g.maxRA * g.maxRA + g.maxTB * g.maxRB * g.maxRB;
-    float* stg[2] = {As, As + stride};
+    float* stg[2] = {As, As + szS};
     int k = 0, i = 0, cur = 0;
     stage(0, 0, stg[0]);
     float acc[kGTMaxBlk][4][4];
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
         g.out[(long long)(a0 + a) * g.B.batch + (b0 + b)] = v;
       } else {
         const int S = g.gstart[grp + 1] - g.gstart[grp];
-        const int la = a0 + a - g.gstart[grp], lb = b0 + b - g.gstart[grp];
+        const int la = g.perm[a0 + a], lb = g.perm[b0 + b];
         float* o = g.gout + g.gout_off[grp];
         o[(long long)la * S + lb] = v;
         if (sym) o[(long long)lb * S + la] = v;
@@ -380,6 +380,46 @@ void plan_gram_tile(int RA, int RB, int batchA, int batchB, int* TA, int* TB, in
       }
     }
   }
+}
+
+// Persistent launch over a work list of tiles of ragged objects (one CTA per SM).
+t3f_status launch_gram_tile_table(const void* cores, int dtype, int dmax, const long long* off, const int* rk,
+                                  const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
+                                  const int* gd, float* out, const long long* gout_off, const int* perm, size_t smem,
+                                  cudaStream_t s) {
+  GramTileArgs g;
+  memset(&g, 0, sizeof(g));
+  g.mode = 1;
+  g.dtype = dtype;
+  g.tab.off = off;
+  g.tab.rk = rk;
+  g.tab.d = dmax;
+  g.gcores = cores;
+  g.nmodes = nmodes;
+  g.items = items;
+  g.nitems = nitems;
+  g.head = head;
+  g.gstart = gstart;
+  g.gd = gd;
+  g.gout = out;
+  g.gout_off = gout_off;
+  g.perm = perm;
+  if (smem > 227 * 1024) return T3F_ERR_UNSUPPORTED;
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = nitems < sms ? (nitems > 0 ? nitems : 1) : sms;
+  if (dtype == T3F_F32) {
+    auto kern = k_gram_tile<float>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<grid, 512, smem, s>>>(g);
+  } else {
+    auto kern = k_gram_tile<__nv_bfloat16>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<grid, 512, smem, s>>>(g);
+  }
+  return launch_status();
 }
 
 bool gram_tile_supported(const TTV& A, const TTV& B) {

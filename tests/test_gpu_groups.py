@@ -1,0 +1,130 @@
+"""Grouped Gram matrices over ragged collections (uneven d, n and r per object) against the
+FP64 oracle: forward, FP64 norms, adjoint, BF16 storage, the tile autotuner and CUDA-graph
+replay of the prepared persistent launch."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth as S
+from tests._util import TOL, rel_err, rel_err_cores, round32, round_bf16
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def ragged_case(seed=400):
+    rng = np.random.default_rng(seed)
+    groups = []
+    for d, n, S_, rlo, rhi in ((4, [3, 2, 4, 3], 9, 1, 12), (3, [5, 4, 2], 6, 2, 40), (5, [2, 3, 2, 2, 3], 5, 3, 64)):
+        objs = []
+        for _ in range(S_):
+            r = int(rng.integers(rlo, rhi + 1))
+            ranks = [1] + [r] * (d - 1) + [1]
+            objs.append([c[0] for c in S.random_tt(rng, 1, n, ranks, 1.0 / np.sqrt(r))])
+        groups.append(objs)
+    gstart = [0]
+    for objs in groups:
+        gstart.append(gstart[-1] + len(objs))
+    return [o for objs in groups for o in objs], gstart
+
+
+def as_f32(objs):
+    return [round32(o) for o in objs]
+
+
+def oracle_groups(objs, gstart):
+    out = []
+    for g in range(len(gstart) - 1):
+        grp = objs[gstart[g]:gstart[g + 1]]
+        out.append(O.gram(grp, grp).ravel())
+    return np.concatenate(out)
+
+
+def test_gram_groups_forward_norms_backward(lib):
+    objs, gstart = ragged_case()
+    objs = as_f32(objs)
+    X = lib.RaggedTT.from_objects([[np.asarray(c, np.float32) for c in o] for o in objs])
+    ws = lib.gram_groups_prepare(X, gstart)
+    G, nrm = lib.gram_groups(X, gstart, ws)
+    ref = oracle_groups(objs, gstart)
+    assert rel_err(G.cpu().numpy(), ref) < TOL["fp32"]
+    assert rel_err(nrm.cpu().numpy(), [O.norm(o) for o in objs]) < TOL["fp32"]
+    rng = np.random.default_rng(401)
+    dout = rng.normal(size=G.numel()).astype(np.float32)
+    dX = lib.gram_groups_backward(X, gstart, ws, torch.tensor(dout, device="cuda"))
+    off = 0
+    for g in range(len(gstart) - 1):
+        grp = objs[gstart[g]:gstart[g + 1]]
+        Sg = len(grp)
+        dG = dout[off:off + Sg * Sg].reshape(Sg, Sg).astype(np.float64)
+        off += Sg * Sg
+        dA, dB = O.gram_vjp(grp, grp, dG)
+        for j in range(Sg):
+            o = gstart[g] + j
+            got = [c.double().cpu().numpy() for c in
+                   lib.RaggedTT(dX, X.dims, X.modes, X.ranks, X.offsets).object_cores(o)]
+            want = [a + b for a, b in zip(dA[j], dB[j])]
+            assert rel_err_cores(got, want) < TOL["fp32"], (g, j)
+
+
+def test_gram_groups_bf16_storage(lib):
+    objs, gstart = ragged_case(402)
+    objs_b = [round_bf16(o) for o in objs]
+    X = lib.RaggedTT.from_objects([[torch.tensor(np.asarray(c)) for c in o] for o in objs_b], dtype=torch.bfloat16)
+    ws = lib.gram_groups_prepare(X, gstart)
+    G, nrm = lib.gram_groups(X, gstart, ws)
+    assert rel_err(G.cpu().numpy(), oracle_groups(objs_b, gstart)) < TOL["bf16"]
+    assert rel_err(nrm.cpu().numpy(), [O.norm(o) for o in objs_b]) < TOL["bf16"]
+    # the arithmetic is FP32 on the rounded inputs: far inside the BF16 tolerance
+    assert rel_err(G.cpu().numpy(), oracle_groups(objs_b, gstart)) < 1e-5
+
+
+def test_gram_groups_autotune_and_graph_replay(lib):
+    objs, gstart = ragged_case(403)
+    objs = as_f32(objs)
+    X = lib.RaggedTT.from_objects([[np.asarray(c, np.float32) for c in o] for o in objs])
+    tiles, _ = lib.autotune_gram_groups(X, gstart, candidates=(1, 2, 4, 8), reps=1)
+    assert len(tiles) == 4 and all(1 <= t <= 16 for t in tiles)
+    ws = lib.gram_groups_prepare(X, gstart, tiles)
+    G0, n0 = lib.gram_groups(X, gstart, ws, tiles)
+    dout = torch.randn(G0.numel(), device="cuda")
+    d0 = lib.gram_groups_backward(X, gstart, ws, dout, tiles)
+    G, nrm, dX = torch.empty_like(G0), torch.empty_like(n0), torch.empty_like(d0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        lib.gram_groups(X, gstart, ws, tiles, out=G, norms=nrm)  # warm-up on the capture stream
+        lib.gram_groups_backward(X, gstart, ws, dout, tiles, dcores=dX)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        lib.gram_groups(X, gstart, ws, tiles, out=G, norms=nrm)
+        lib.gram_groups_backward(X, gstart, ws, dout, tiles, dcores=dX)
+    G.zero_()
+    dX.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert rel_err(G.cpu().numpy(), G0.cpu().numpy()) < 1e-6
+    assert rel_err(dX.cpu().numpy(), d0.cpu().numpy()) < 1e-5
+    assert rel_err(G.cpu().numpy(), oracle_groups(objs, gstart)) < TOL["fp32"]
+
+
+def test_gram_groups_config4_sampled(lib):
+    cfg = S.config4()
+    objs, gstart = [], [0]
+    for grp in cfg.groups:
+        objs += [round32(o) for o in grp.cores]
+        gstart.append(len(objs))
+    X = lib.RaggedTT.from_objects([[np.asarray(c, np.float32) for c in o] for o in objs])
+    ws = lib.gram_groups_prepare(X, gstart)
+    G, nrm = lib.gram_groups(X, gstart, ws)
+    G = G.cpu().numpy()
+    rng = np.random.default_rng(404)
+    got, want, off = [], [], 0
+    for g in range(len(gstart) - 1):
+        Sg = gstart[g + 1] - gstart[g]
+        for a, b in [(0, 0), (Sg - 1, Sg - 1)] + [tuple(rng.integers(0, Sg, 2)) for _ in range(4)]:
+            got.append(G[off + a * Sg + b])
+            want.append(O.dot(objs[gstart[g] + a], objs[gstart[g] + b]))
+        off += Sg * Sg
+    assert rel_err(got, want) < TOL["fp32"]
