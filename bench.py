@@ -7,6 +7,9 @@ One step = one pass of every hot-path operation over its synthetic workload:
   matvec       100 TT-matrices (4x4 modes, r=10) zip 100 TT-vectors (r=10), fwd + adjoint
   psum         FP64 orthogonalisation of X (d=20, n=16, r=32) + project_sum of 1000 rank-8
                TTs and the adjoint of ||project_sum||^2
+  uneven       512 ragged TTs in 8 groups of 64 (d in [4,16], n in [2,16], r in [2,64]): all
+               pairwise inner products within groups + FP64 norms + adjoint, one persistent
+               work-queue launch with autotuned rank-bucket tiles, replayed as a CUDA graph
 value = algorithmic FLOPs of the step / device time of the step (GFLOP/s, FP32).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -35,7 +38,8 @@ import synth as S  # noqa: E402
 
 METRIC = "TT-sweep GFLOP/s and % roofline (Gram, gather fwd+bwd, project_sum) vs plain FP32"
 WORKLOAD = ("t3f-hot-path: completion(N=1e6,d=10,n=10,r=8)+rgrad + gram(100x100,d=10,n=10,r=10)"
-            "+bwd+norm + matvec(100,d=10,4x4,r=10)+bwd + orth+project_sum(1000,d=20,n=16,rX=32,rZ=8)+bwd")
+            "+bwd+norm + matvec(100,d=10,4x4,r=10)+bwd + orth+project_sum(1000,d=20,n=16,rX=32,rZ=8)+bwd"
+            " + uneven(8x64 ragged TTs, d 4-16, n 2-16, r 2-64: grouped gram+norms+bwd, graph replay)")
 L2_BYTES = 129 * 1024 * 1024
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
@@ -176,6 +180,18 @@ class Workload:
         dC = np.concatenate([rng.normal(size=(100, rc[k], 4, rc[k + 1])).astype(np.float32).ravel() for k in range(10)])
         host["dC"] = dC
         self.meta["dC"] = ([4] * 10, rc, 100, None)
+        # uneven batches: 8 groups of 64 ragged TTs, stored back to back
+        c4 = S.config4(seed=5 + seed_offset)
+        objs = [[np.asarray(c, np.float32) for c in o] for grp in c4.groups for o in grp.cores]
+        self.gstart = [0]
+        for grp in c4.groups:
+            self.gstart.append(self.gstart[-1] + len(grp.cores))
+        r4 = t3f.RaggedTT.from_objects(objs, device="cpu")
+        host["X4"] = r4.data.numpy()
+        self.r4meta = (r4.dims, r4.modes, r4.ranks, r4.offsets)
+        self.shapes["c4"] = c4
+        ntot = sum((self.gstart[g + 1] - self.gstart[g]) ** 2 for g in range(len(self.gstart) - 1))
+        host["dG4"] = rng.normal(size=ntot).astype(np.float32)
         self.host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
         self.h2d_bytes = sum(v.numel() * v.element_size() for v in self.host.values())
         self.devbuf = {k: torch.empty_like(v, device=dev) for k, v in self.host.items()}
@@ -185,6 +201,32 @@ class Workload:
     def upload(self, stream):
         for k, v in self.host.items():
             self.devbuf[k].copy_(v, non_blocking=True)
+
+    def ragged(self):
+        return self.t3f.RaggedTT(self.devbuf["X4"], *self.r4meta)
+
+    def prepare_uneven(self):
+        """Autotune the rank-bucket tiles, prepare the work list and capture the grouped
+        forward + adjoint in a CUDA graph (all outside the timed region)."""
+        t3f, torch = self.t3f, self.torch
+        X4 = self.ragged()
+        self.tiles4, _ = t3f.autotune_gram_groups(X4, self.gstart, reps=2)
+        self.ws4 = t3f.gram_groups_prepare(X4, self.gstart, self.tiles4)
+        total = self.devbuf["dG4"].numel()
+        self.G4 = torch.empty(total, dtype=torch.float32, device=self.dev)
+        self.n4 = torch.empty(X4.count, dtype=torch.float64, device=self.dev)
+        self.dX4 = torch.empty(X4.data.numel(), dtype=torch.float32, device=self.dev)
+        side = torch.cuda.Stream(self.dev)
+        side.wait_stream(torch.cuda.current_stream(self.dev))
+        with torch.cuda.stream(side):
+            t3f.gram_groups(X4, self.gstart, self.ws4, self.tiles4, out=self.G4, norms=self.n4)
+            t3f.gram_groups_backward(X4, self.gstart, self.ws4, self.devbuf["dG4"], self.tiles4, dcores=self.dX4)
+        torch.cuda.current_stream(self.dev).wait_stream(side)
+        self.graph4 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph4):
+            t3f.gram_groups(X4, self.gstart, self.ws4, self.tiles4, out=self.G4, norms=self.n4)
+            t3f.gram_groups_backward(X4, self.gstart, self.ws4, self.devbuf["dG4"], self.tiles4, dcores=self.dX4)
+        torch.cuda.synchronize(self.dev)
 
     def tt(self, key):
         n, r, b, m = self.meta[key]
@@ -212,7 +254,18 @@ class Workload:
             "orth5": f_orth(n16, S.tt_ranks(20, 32)),
             "psum": f_psum_fwd(n16, ru5, rz5, 1000),
             "psum_bwd": f_psum_bwd(n16, ru5, rz5, 1000),
+            "uneven": self.uneven_flops(),
         }
+
+    def uneven_flops(self):
+        """Unique pairs (a <= b) of every group: left sweep + adjoint of each pair."""
+        dims, modes, ranks, _ = self.r4meta
+        tot = 0.0
+        for g in range(len(self.gstart) - 1):
+            for a in range(self.gstart[g], self.gstart[g + 1]):
+                for b in range(a, self.gstart[g + 1]):
+                    tot += f_left_sweep(modes[a], ranks[a], ranks[b]) + f_gram_bwd(modes[a], ranks[a], ranks[b])
+        return tot
 
 
 def run_step(w, timers=None, stream=None):
@@ -249,8 +302,9 @@ def run_step(w, timers=None, stream=None):
     dU5 = timed("psum", lambda: t3f.project_sum(U5, V5, Z5, w.devbuf["c5"]))
     # adjoint of 1/2 ||project_sum||^2: the cotangent of the coordinates is dU5 itself
     dZ, dc = timed("psum_bwd", lambda: t3f.project_sum_backward(U5, V5, Z5, w.devbuf["c5"], dU5))
+    timed("uneven", lambda: w.graph4.replay())
     out.update(loss=loss, dX=dX.data, dU2=dU2.data, G=G, dA=dA.data, dB=dB.data, norm=nrm,
-               dAm=dAm.data, dxv=dxv.data, dU5=dU5.data, dc=dc)
+               dAm=dAm.data, dxv=dxv.data, dU5=dU5.data, dc=dc, G4=w.G4, n4=w.n4, dX4=w.dX4)
     out["_bulk"] = (C, dZ)  # stay on the device
     return out
 
@@ -420,6 +474,7 @@ def gpu_arm(args):
             dist.barrier()
 
     w = Workload(t3f, torch, dev, seed_offset=rank)
+    w.prepare_uneven()
     flops = w.flops()
     step_flops = sum(flops.values())
     stream = torch.cuda.current_stream(dev)

@@ -196,10 +196,14 @@ static void plan_gram_bwd(const TTV& A, const TTV& B, int* TA, int* TB, size_t* 
     }
 }
 
-size_t ws_gram_bwd(const TTV& A, const TTV& B) {
+static size_t ws_gram_bwd_generic(const TTV& A, const TTV& B) {
   long long ioff[T3F_MAX_D + 1];
   const long long n = partial_offsets(A, B, (long long)A.batch * B.batch, ioff);
   return kWsHeader + align256(sizeof(float) * n);
+}
+
+size_t ws_gram_bwd(const TTV& A, const TTV& B) {
+  return gram_tile_bwd_supported(A, B) ? ws_gram_tile_bwd(A, B) : ws_gram_bwd_generic(A, B);
 }
 
 size_t ws_norm(const TTV& A) { return kWsHeader + align256(sizeof(float) * A.batch); }
@@ -214,7 +218,7 @@ __global__ void k_sqrt64(const float* in, double* out, int n) {
 // scatters with atomics.
 t3f_status gram_bwd_accumulate(const TTV& va, const TTV& vb, const float* dG, float* dA, float* dB, void* ws,
                                size_t ws_bytes, cudaStream_t s) {
-  T3F_CHECK(check_ws(ws, ws_bytes, ws_gram_bwd(va, vb)));
+  T3F_CHECK(check_ws(ws, ws_bytes, ws_gram_bwd_generic(va, vb)));
   GramBwdArgs args;
   memset(&args, 0, sizeof(args));
   args.dA = dA;
@@ -307,6 +311,7 @@ extern "C" t3f_status t3f_gram_backward(const t3f_tt* A, const t3f_tt* B, const 
   if (args.dB && cudaMemsetAsync(args.dB, 0, sizeof(float) * t3f_packed_size(dB), s) != cudaSuccess)
     return T3F_ERR_CUDA;
   if (!args.dA && !args.dB) return T3F_OK;
+  if (gram_tile_bwd_supported(va, vb)) return run_gram_tile_bwd(va, vb, dG, args.dA, args.dB, ws, ws_bytes, s);
   return gram_bwd_accumulate(va, vb, dG, args.dA, args.dB, ws, ws_bytes, s);
 }
 

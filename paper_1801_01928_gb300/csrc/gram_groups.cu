@@ -4,16 +4,14 @@
 // Planning (host, t3f_gram_groups_prepare): the objects of every group are ordered by rank
 // and split into rank buckets {<=8, <=16, <=32, <=64}; the upper triangle of each group's
 // pairs is cut into tiles whose side depends on the buckets (tile table), the tiles are
-// sorted by cost, largest first, and the work list plus per-object tables are copied into
+// sorted by cost, largest first, and the work lists plus per-object tables are copied into
 // the workspace once.
 // Forward (t3f_gram_groups): one persistent launch of the tiled sweep kernel whose CTAs
 // take tiles from the work list through an atomic counter, then the FP64 norms.
-// Adjoint (t3f_gram_groups_backward): per group and bucket pair (p <= q) the objects are
-// packed into zero-padded uniform batches (padding leaves every inner product and the
-// gradient on the original entries unchanged), the symmetrised cotangent block is gathered,
-// and the uniform adjoint kernels accumulate into padded gradients that are unpacked at the
-// end. Every step is an asynchronous launch, so the whole sequence can be captured in a
-// CUDA graph after one prepare call.
+// Adjoint (t3f_gram_groups_backward): one persistent launch of the tiled adjoint kernel over
+// a second work list of smaller tiles (the adjoint keeps seven partial tiles in shared
+// memory); off-diagonal tiles use the symmetrised cotangent g_ab + g_ba. Both calls only
+// enqueue memsets and kernels, so they can be captured in a CUDA graph after one prepare.
 #include <algorithm>
 #include <math.h>
 #include <vector>
@@ -28,15 +26,28 @@ t3f_status launch_gram_tile_table(const void* cores, int dtype, int dmax, const 
                                   const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
                                   const int* gd, float* out, const long long* gout_off, const int* perm, size_t smem,
                                   cudaStream_t s);
-t3f_status gram_bwd_accumulate(const TTV& A, const TTV& B, const float* dG, float* dA, float* dB, void* ws,
-                               size_t ws_bytes, cudaStream_t s);
-size_t ws_gram_bwd(const TTV& A, const TTV& B);
+size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB);
+t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, const long long* off, const int* rk,
+                                      const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
+                                      const int* gd, const int* perm, const float* dout, const long long* gout_off,
+                                      float* dX, float* scratch, long long scratch_stride, size_t smem, int grid,
+                                      cudaStream_t s);
 
 namespace {
 
 constexpr int kBuckets = 4;
 const int kBucketMax[kBuckets] = {8, 16, 32, 64};
 const int kDefaultTiles[kBuckets] = {10, 6, 3, 1};
+
+int sm_count_gg() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
 
 struct Range {
   int begin, end, R;  // sorted positions [begin, end), padded inner rank
@@ -46,7 +57,12 @@ struct Plan {
   int count = 0, ngroups = 0, dmax = 0, nitems = 0;
   std::vector<int> sorted;   // sorted position -> object
   std::vector<int> perm;     // sorted position -> local index within the group
-  std::vector<int> items;    // 8 ints per item
+  std::vector<int> items;    // 8 ints per item (forward tiles)
+  std::vector<int> bitems;   // 8 ints per item (adjoint tiles)
+  int nbitems = 0;
+  size_t bsmem = 0;
+  long long bstride = 0;     // scratch floats per CTA of the adjoint
+  int bgrid = 0;
   std::vector<long long> objoff;  // [pos][dmax]
   std::vector<int> objrk;    // [pos][dmax + 1]
   std::vector<int> nmodes;   // [group][dmax]
@@ -54,11 +70,9 @@ struct Plan {
   std::vector<int> gs;       // [group + 1]
   std::vector<long long> gout;  // [group]
   std::vector<Range> br;     // [group][bucket]
-  std::vector<long long> padoff;  // [group][bucket] float offset of the padded batch
   size_t smem = 0;
   // workspace layout (bytes)
-  size_t o_items, o_off, o_rk, o_nm, o_gs, o_gd, o_go, o_perm, o_pad, o_padg, o_dg, o_bws, total;
-  size_t pad_floats = 0, dg_floats = 0, bws_bytes = 0;
+  size_t o_items, o_bitems, o_off, o_rk, o_nm, o_gs, o_gd, o_go, o_perm, o_scr, total;
 };
 
 int bucket_of(int r) {
@@ -68,29 +82,6 @@ int bucket_of(int r) {
 }
 
 inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// Uniform descriptor of the padded batch of (group g, bucket b).
-TTV padded_view(const Plan& P, int g, int b, void* base) {
-  TTV v;
-  memset(&v, 0, sizeof(v));
-  const Range& r = P.br[g * kBuckets + b];
-  v.d = P.gd[g];
-  v.batch = r.end - r.begin;
-  v.dtype = T3F_F32;
-  v.p = base;
-  long long off = 0;
-  for (int k = 0; k <= v.d; ++k) v.r[k] = (k == 0 || k == v.d) ? 1 : r.R;
-  for (int k = 0; k < v.d; ++k) {
-    v.n[k] = P.nmodes[g * P.dmax + k];
-    v.m[k] = 1;
-    v.osz[k] = (long long)v.r[k] * v.n[k] * v.r[k + 1];
-    v.off[k] = off;
-    off += v.osz[k] * v.batch;
-    v.nmax = std::max(v.nmax, v.n[k]);
-  }
-  v.rmax = v.d > 1 ? r.R : 1;
-  return v;
-}
 
 t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, const int* tiles, Plan* P) {
   if (!X || !X->d || !X->n || !X->ranks || !X->obj_off || !X->cores) return T3F_ERR_ARG;
@@ -183,84 +174,80 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
     }
     for (int k = 0; k <= d; ++k) P->objrk[(size_t)pos * (dmax + 1) + k] = X->ranks[roff[o] + k];
   }
-  // tiles of the upper triangle of every group, cut per bucket pair
-  struct It {
-    double cost;
-    int v[8];
-  };
-  std::vector<It> its;
-  size_t smem = 0;
-  for (int g = 0; g < ngroups; ++g) {
-    double slices = 0;
-    for (int k = 0; k < P->gd[g]; ++k) slices += P->nmodes[(size_t)g * dmax + k];
-    for (int p = 0; p < kBuckets; ++p)
-      for (int q = p; q < kBuckets; ++q) {
-        const Range& A = P->br[(size_t)g * kBuckets + p];
-        const Range& B = P->br[(size_t)g * kBuckets + q];
-        if (A.end == A.begin || B.end == B.begin) continue;
-        for (int a0 = A.begin; a0 < A.end; a0 += tl[p]) {
-          const int na = std::min(tl[p], A.end - a0);
-          int RA = 4;
-          for (int x = a0; x < a0 + na; ++x) RA = std::max(RA, (rmax[P->sorted[x]] + 3) & ~3);
-          for (int b0 = (p == q ? a0 : B.begin); b0 < B.end; b0 += tl[q]) {
-            const int nb = std::min(tl[q], B.end - b0);
-            int RB = 4;
-            for (int x = b0; x < b0 + nb; ++x) RB = std::max(RB, (rmax[P->sorted[x]] + 3) & ~3);
-            // a tile must fit one CTA of 512 threads: 2 blocks and 16 staged values each
-            if (na * (RA / 4) * nb * (RB / 4) > 1024 || na * RA * RA + nb * RB * RB > 512 * 16)
-              return T3F_ERR_UNSUPPORTED;
-            It it;
-            it.cost = (double)na * nb * RA * RB * (RA + RB) * slices;
-            it.v[0] = g;
-            it.v[1] = a0;
-            it.v[2] = na;
-            it.v[3] = b0;
-            it.v[4] = nb;
-            it.v[5] = RA;
-            it.v[6] = RB;
-            it.v[7] = (p == q && a0 == b0) ? 0 : 1;
-            its.push_back(it);
-            smem = std::max(smem, gram_tile_smem(na, nb, RA, RB));
+  // tiles of the upper triangle of every group, cut per bucket pair; `fits` bounds a tile
+  auto make_items = [&](const int* side, bool bwd, std::vector<int>* out, size_t* smem_out,
+                        long long* pmax_out) -> t3f_status {
+    struct It {
+      double cost;
+      int v[8];
+    };
+    std::vector<It> its;
+    size_t smem = 0;
+    long long pmax = 0;
+    for (int g = 0; g < ngroups; ++g) {
+      double slices = 0;
+      for (int k = 0; k < P->gd[g]; ++k) slices += P->nmodes[(size_t)g * dmax + k];
+      for (int p = 0; p < kBuckets; ++p)
+        for (int q = p; q < kBuckets; ++q) {
+          const Range& A = P->br[(size_t)g * kBuckets + p];
+          const Range& B = P->br[(size_t)g * kBuckets + q];
+          if (A.end == A.begin || B.end == B.begin) continue;
+          for (int a0 = A.begin; a0 < A.end; a0 += side[p]) {
+            const int na = std::min(side[p], A.end - a0);
+            int RA = 4;
+            for (int x = a0; x < a0 + na; ++x) RA = std::max(RA, (rmax[P->sorted[x]] + 3) & ~3);
+            for (int b0 = (p == q ? a0 : B.begin); b0 < B.end; b0 += side[q]) {
+              const int nb = std::min(side[q], B.end - b0);
+              int RB = 4;
+              for (int x = b0; x < b0 + nb; ++x) RB = std::max(RB, (rmax[P->sorted[x]] + 3) & ~3);
+              // a tile must fit one CTA of 512 threads: 2 blocks each, staging bounds
+              if (na * (RA / 4) * nb * (RB / 4) > 1024) return T3F_ERR_UNSUPPORTED;
+              const size_t sm = bwd ? gram_tile_bwd_smem(na, nb, RA, RB) : gram_tile_smem(na, nb, RA, RB);
+              if (sm > 200 * 1024) return T3F_ERR_UNSUPPORTED;
+              if (!bwd && na * RA * RA + nb * RB * RB > 512 * 16) return T3F_ERR_UNSUPPORTED;
+              It it;
+              it.cost = (double)na * nb * RA * RB * (RA + RB) * slices;
+              it.v[0] = g;
+              it.v[1] = a0;
+              it.v[2] = na;
+              it.v[3] = b0;
+              it.v[4] = nb;
+              it.v[5] = RA;
+              it.v[6] = RB;
+              it.v[7] = (p == q && a0 == b0) ? 0 : 1;
+              its.push_back(it);
+              smem = std::max(smem, sm);
+              pmax = std::max(pmax, (long long)na * nb * RA * RB);
+            }
           }
         }
-      }
-  }
-  std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
-  P->nitems = (int)its.size();
-  P->items.resize((size_t)P->nitems * 8);
-  for (int w = 0; w < P->nitems; ++w)
-    for (int q = 0; q < 8; ++q) P->items[(size_t)w * 8 + q] = its[w].v[q];
-  P->smem = smem;
-  // padded batches of the adjoint (one per group and non-empty bucket)
-  P->padoff.assign((size_t)ngroups * kBuckets, -1);
-  size_t pf = 0;
-  size_t bws = 0;
-  for (int g = 0; g < ngroups; ++g)
-    for (int b = 0; b < kBuckets; ++b) {
-      const Range& r = P->br[(size_t)g * kBuckets + b];
-      if (r.end == r.begin) continue;
-      P->padoff[(size_t)g * kBuckets + b] = (long long)pf;
-      TTV v = padded_view(*P, g, b, nullptr);
-      size_t sz = 0;
-      for (int k = 0; k < v.d; ++k) sz += (size_t)v.osz[k] * v.batch;
-      pf += (sz + 63) & ~size_t(63);
     }
-  P->pad_floats = pf;
-  size_t dgf = 0;
-  for (int g = 0; g < ngroups; ++g)
-    for (int p = 0; p < kBuckets; ++p)
-      for (int q = p; q < kBuckets; ++q) {
-        const Range& A = P->br[(size_t)g * kBuckets + p];
-        const Range& B = P->br[(size_t)g * kBuckets + q];
-        if (A.end == A.begin || B.end == B.begin) continue;
-        dgf = std::max(dgf, (size_t)(A.end - A.begin) * (B.end - B.begin));
-        TTV va = padded_view(*P, g, p, nullptr), vb = padded_view(*P, g, q, nullptr);
-        bws = std::max(bws, ws_gram_bwd(va, vb));
-      }
-  P->dg_floats = dgf;
-  P->bws_bytes = bws;
+    std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+    out->resize(its.size() * 8);
+    for (size_t w = 0; w < its.size(); ++w)
+      for (int q = 0; q < 8; ++q) (*out)[w * 8 + q] = its[w].v[q];
+    *smem_out = smem;
+    *pmax_out = pmax;
+    return T3F_OK;
+  };
+  size_t smem = 0;
+  long long pmax = 0;
+  T3F_CHECK(make_items(tl, false, &P->items, &smem, &pmax));
+  P->nitems = (int)(P->items.size() / 8);
+  // adjoint tiles: half the side (the adjoint holds seven partial tiles per pair)
+  int tlb[kBuckets];
+  for (int b = 0; b < kBuckets; ++b) tlb[b] = std::max(1, tl[b] / 2);
+  size_t bsmem = 0;
+  long long bpmax = 0;
+  T3F_CHECK(make_items(tlb, true, &P->bitems, &bsmem, &bpmax));
+  P->nbitems = (int)(P->bitems.size() / 8);
+  P->bsmem = bsmem;
+  P->bstride = (long long)(dmax + 1) * bpmax;
+  P->bgrid = std::max(1, std::min(P->nbitems, sm_count_gg()));
+  P->smem = smem;
   size_t o = kWsHeader;
   P->o_items = o; o += a256(sizeof(int) * P->items.size());
+  P->o_bitems = o; o += a256(sizeof(int) * P->bitems.size());
   P->o_off = o; o += a256(sizeof(long long) * P->objoff.size());
   P->o_rk = o; o += a256(sizeof(int) * P->objrk.size());
   P->o_nm = o; o += a256(sizeof(int) * P->nmodes.size());
@@ -268,10 +255,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
   P->o_gd = o; o += a256(sizeof(int) * P->gd.size());
   P->o_go = o; o += a256(sizeof(long long) * P->gout.size());
   P->o_perm = o; o += a256(sizeof(int) * P->perm.size());
-  P->o_pad = o; o += a256(sizeof(float) * pf);
-  P->o_padg = o; o += a256(sizeof(float) * pf);
-  P->o_dg = o; o += a256(sizeof(float) * dgf);
-  P->o_bws = o; o += a256(bws);
+  P->o_scr = o; o += a256(sizeof(float) * (size_t)P->bstride * P->bgrid);
   P->total = o;
   return T3F_OK;
 }
@@ -289,54 +273,6 @@ __global__ void k_group_norms(const float* out, const long long* gout_off, const
   }
 }
 
-struct PackArgs {
-  TTV P;                 // padded uniform batch (F32)
-  const void* cores;     // ragged cores (F32 or BF16), or F32 gradient target when unpacking
-  const long long* off;  // [pos][dmax]
-  const int* rk;         // [pos][dmax + 1]
-  int dmax, pos0, dtype, unpack;
-  float* pad;
-  float* target;         // unpack: ragged F32 gradient
-};
-
-__global__ void k_pack(const __grid_constant__ PackArgs a) {
-  const TTV& P = a.P;
-  for (int k = 0; k < P.d; ++k) {
-    const long long tot = P.osz[k] * P.batch;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-      const int t = (int)(e / P.osz[k]);
-      const long long q = e % P.osz[k];
-      const int r1p = P.r[k + 1], np = P.n[k];
-      const int be = (int)(q % r1p), i = (int)((q / r1p) % np), al = (int)(q / ((long long)r1p * np));
-      const int pos = a.pos0 + t;
-      const int r0 = a.rk[(long long)pos * (a.dmax + 1) + k], r1 = a.rk[(long long)pos * (a.dmax + 1) + k + 1];
-      const bool in = al < r0 && be < r1;
-      const long long src = a.off[(long long)pos * a.dmax + k] + ((long long)al * np + i) * r1 + be;
-      float* pe = a.pad + P.off[k] + e;
-      if (!a.unpack) {
-        float v = 0.0f;
-        if (in) v = a.dtype == T3F_F32 ? static_cast<const float*>(a.cores)[src]
-                                       : __bfloat162float(static_cast<const __nv_bfloat16*>(a.cores)[src]);
-        *pe = v;
-      } else if (in) {
-        a.target[src] = *pe;
-      }
-    }
-  }
-}
-
-// dG'[x][y] = dout[ga(x)][gb(y)] (+ dout[gb(y)][ga(x)] for p < q), local indices via perm
-__global__ void k_gather_dg(const float* dout, long long goff, int S, const int* perm, int a0, int na, int b0, int nb,
-                            int symm, float* dg) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < na * nb; e += gridDim.x * blockDim.x) {
-    const int x = e / nb, y = e % nb;
-    const int la = perm[a0 + x], lb = perm[b0 + y];
-    float v = dout[goff + (long long)la * S + lb];
-    if (symm) v += dout[goff + (long long)lb * S + la];
-    dg[e] = v;
-  }
-}
-
 }  // namespace
 
 t3f_status gg_tables_upload(const Plan& P, char* w, cudaStream_t s) {
@@ -345,6 +281,7 @@ t3f_status gg_tables_upload(const Plan& P, char* w, cudaStream_t s) {
     const void* src;
     size_t bytes;
   } cps[] = {{P.o_items, P.items.data(), sizeof(int) * P.items.size()},
+             {P.o_bitems, P.bitems.data(), sizeof(int) * P.bitems.size()},
              {P.o_off, P.objoff.data(), sizeof(long long) * P.objoff.size()},
              {P.o_rk, P.objrk.data(), sizeof(int) * P.objrk.size()},
              {P.o_nm, P.nmodes.data(), sizeof(int) * P.nmodes.size()},
@@ -411,65 +348,25 @@ extern "C" t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t n
   if (!dout || !dcores) return T3F_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   char* w = static_cast<char*>(ws);
-  float* pad = reinterpret_cast<float*>(w + P.o_pad);
-  float* padg = reinterpret_cast<float*>(w + P.o_padg);
-  float* dg = reinterpret_cast<float*>(w + P.o_dg);
-  const long long* off = reinterpret_cast<const long long*>(w + P.o_off);
-  const int* rk = reinterpret_cast<const int*>(w + P.o_rk);
-  const int* perm = reinterpret_cast<const int*>(w + P.o_perm);
-  if (cudaMemsetAsync(padg, 0, sizeof(float) * P.pad_floats, s) != cudaSuccess) return T3F_ERR_CUDA;
-  // pack every (group, bucket) into its padded batch
-  for (int g = 0; g < ngroups; ++g)
-    for (int b = 0; b < kBuckets; ++b) {
-      const long long po = P.padoff[(size_t)g * kBuckets + b];
-      if (po < 0) continue;
-      PackArgs pa;
-      memset(&pa, 0, sizeof(pa));
-      pa.P = padded_view(P, g, b, pad + po);
-      pa.cores = X->cores;
-      pa.off = off;
-      pa.rk = rk;
-      pa.dmax = P.dmax;
-      pa.pos0 = P.br[(size_t)g * kBuckets + b].begin;
-      pa.dtype = X->dtype;
-      pa.pad = pad + po;
-      k_pack<<<128, 256, 0, s>>>(pa);
-      T3F_CHECK(launch_status());
+  long long nel = 0;  // elements of the ragged cores
+  {
+    long long no = 0, ro = 0;
+    for (int o = 0; o < X->count; ++o) {
+      long long e = 0;
+      for (int k = 0; k < X->d[o]; ++k) e += (long long)X->ranks[ro + k] * X->n[no + k] * X->ranks[ro + k + 1];
+      nel = std::max(nel, X->obj_off[o] + e);
+      no += X->d[o];
+      ro += X->d[o] + 1;
     }
-  // adjoint of every bucket pair p <= q with the symmetrised cotangent block
-  for (int g = 0; g < ngroups; ++g) {
-    const int S = gstart[g + 1] - gstart[g];
-    for (int p = 0; p < kBuckets; ++p)
-      for (int q = p; q < kBuckets; ++q) {
-        const long long pp = P.padoff[(size_t)g * kBuckets + p], pq = P.padoff[(size_t)g * kBuckets + q];
-        if (pp < 0 || pq < 0) continue;
-        const Range& A = P.br[(size_t)g * kBuckets + p];
-        const Range& B = P.br[(size_t)g * kBuckets + q];
-        const int na = A.end - A.begin, nb = B.end - B.begin;
-        k_gather_dg<<<(na * nb + 255) / 256, 256, 0, s>>>(dout, P.gout[g], S, perm, A.begin, na, B.begin, nb,
-                                                          p != q ? 1 : 0, dg);
-        T3F_CHECK(launch_status());
-        TTV va = padded_view(P, g, p, pad + pp), vb = padded_view(P, g, q, pad + pq);
-        T3F_CHECK(gram_bwd_accumulate(va, vb, dg, padg + pp, padg + pq, w + P.o_bws, P.bws_bytes, s));
-      }
   }
-  // unpack the padded gradients onto the ragged layout
-  for (int g = 0; g < ngroups; ++g)
-    for (int b = 0; b < kBuckets; ++b) {
-      const long long po = P.padoff[(size_t)g * kBuckets + b];
-      if (po < 0) continue;
-      PackArgs pa;
-      memset(&pa, 0, sizeof(pa));
-      pa.P = padded_view(P, g, b, padg + po);
-      pa.off = off;
-      pa.rk = rk;
-      pa.dmax = P.dmax;
-      pa.pos0 = P.br[(size_t)g * kBuckets + b].begin;
-      pa.unpack = 1;
-      pa.pad = padg + po;
-      pa.target = dcores;
-      k_pack<<<128, 256, 0, s>>>(pa);
-      T3F_CHECK(launch_status());
-    }
-  return T3F_OK;
+  if (cudaMemsetAsync(dcores, 0, sizeof(float) * nel, s) != cudaSuccess) return T3F_ERR_CUDA;
+  int* head = reinterpret_cast<int*>(w + 2 * sizeof(int));  // third word of the header
+  if (cudaMemsetAsync(head, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
+  return launch_gram_tile_bwd_table(
+      X->cores, X->dtype, P.dmax, reinterpret_cast<const long long*>(w + P.o_off),
+      reinterpret_cast<const int*>(w + P.o_rk), reinterpret_cast<const int*>(w + P.o_nm),
+      reinterpret_cast<const int*>(w + P.o_bitems), P.nbitems, head, reinterpret_cast<const int*>(w + P.o_gs),
+      reinterpret_cast<const int*>(w + P.o_gd), reinterpret_cast<const int*>(w + P.o_perm), dout,
+      reinterpret_cast<const long long*>(w + P.o_go), dcores, reinterpret_cast<float*>(w + P.o_scr), P.bstride,
+      P.bsmem, P.bgrid, s);
 }

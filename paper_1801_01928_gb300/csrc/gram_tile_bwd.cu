@@ -1,0 +1,542 @@
+// Tiled adjoint of the Gram sweep (cotangent of sum_ab g_ab <A_a, B_b>).
+//
+// For a pair (a, b) with left partials M_k and right partials R_{k+1} (interfaces k, k+1):
+//   dA_a^k[:, i, :] += g_ab M_k B_b^k[:, i, :] R_{k+1}^T,   dB_b^k[:, i, :] += g_ab M_k^T A_a^k[:, i, :] R_{k+1},
+//   R_k = sum_i A_a^k[:, i, :] R_{k+1} B_b^k[:, i, :]^T.
+// A CTA owns a tile of na x nb pairs. It first runs the left sweep of its pairs (as the
+// forward kernel) and keeps M at every interface in a per-CTA scratch area, then runs the
+// right sweep; per mode slice five register-blocked products (4 x 4 blocks) run on shared
+// memory:
+//   X  = A_i R          Y' = g B_i R^T        R' += X B_i^T
+//   dA_a,i = sum_b M Y'   (K = the tile's (b, beta))      dB_b,i = sum_a (g M)^T X   (K = (a, alpha))
+// dA / dB of a slice are added to the global gradients with atomics (other tiles share the
+// objects). Ranks are zero-padded to multiples of 4; the same kernel takes tiles from the
+// block index (uniform batches) or from a work list (grouped ragged collections).
+#include "t3f_internal.cuh"
+
+namespace t3f {
+
+struct GramBwdTileArgs {
+  TTV A, B;              // uniform mode
+  int TA, TB, RA, RB;
+  const float* dG;       // uniform: [bA][bB]
+  float* dA;             // uniform: packed like A
+  float* dB;             // uniform: packed like B
+  // table mode
+  const long long* off;
+  const int* rk;
+  int dmax;
+  const void* gcores;
+  const int* nmodes;
+  const int* items;      // [item][8]: group, a0, na, b0, nb, RA, RB, sym
+  int nitems;
+  int* head;
+  const int* gd;
+  const int* perm;
+  const float* dout;     // [group][S][S]
+  const long long* gout_off;
+  const int* gstart;
+  float* dX;             // gradient with the layout of the ragged cores
+  // common
+  float* scratch;        // per CTA: (dmax + 1) interfaces of the tile's partials
+  long long scratch_stride;
+  int mode, dtype;
+};
+
+__device__ __forceinline__ void fma44b(float (&acc)[4][4], const float4 a, const float4 b) {
+  const float av[4] = {a.x, a.y, a.z, a.w};
+  const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+}
+
+template <typename ST>
+__global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ GramBwdTileArgs g) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int s_item[8];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  float* scr = g.scratch + (long long)blockIdx.x * g.scratch_stride;
+  for (int it = 0;; ++it) {
+    int grp = 0, a0, na, b0, nb, RA, RB, sym = 0, d;
+    if (g.mode == 0) {
+      if (it > 0) break;
+      const int ntb = (g.B.batch + g.TB - 1) / g.TB;
+      a0 = (blockIdx.x / ntb) * g.TA;
+      b0 = (blockIdx.x % ntb) * g.TB;
+      na = min(g.TA, g.A.batch - a0);
+      nb = min(g.TB, g.B.batch - b0);
+      RA = g.RA;
+      RB = g.RB;
+      d = g.A.d;
+    } else {
+      __syncthreads();
+      if (tid == 0) {
+        const int w = atomicAdd(g.head, 1);
+        s_item[7] = w;
+        if (w < g.nitems)
+          for (int q = 0; q < 7; ++q) s_item[q] = g.items[w * 8 + q];
+      }
+      __syncthreads();
+      if (s_item[7] >= g.nitems) break;
+      grp = s_item[0];
+      a0 = s_item[1];
+      na = s_item[2];
+      b0 = s_item[3];
+      nb = s_item[4];
+      RA = s_item[5];
+      RB = s_item[6];
+      sym = g.items[s_item[7] * 8 + 7];
+      d = g.gd[grp];
+    }
+    const int P = na * nb, PS = RA * RB, QA = RA / 4, QB = RB / 4;
+    // shared memory of this tile
+    float* Rm = sm;                      // [p][RA][RB]  R (rows alpha')
+    float* RT = Rm + P * PS;             // [p][RB][RA]  R^T
+    float* Mm = RT + P * PS;             // [a][al][b][be] g * M   (K rows (a, al) for dB)
+    float* MT = Mm + P * PS;             // [b][be][a][al] M       (K rows (b, be) for dA)
+    float* Xm = MT + P * PS;             // [a][al][b][bp] X       (K rows (a, al) for dB)
+    float* XT = Xm + P * PS;             // [p][bp][al]    X^T     (K rows bp for R')
+    float* Ym = XT + P * PS;             // [b][be][a][ap] g Y     (K rows (b, be) for dA)
+    float* Sg = Ym + P * PS;             // staging: [2][AT (na RA RA) + BT (nb RB RB)]
+    const int szA = na * RA * RA, szS = szA + nb * RB * RB;
+    float* gsm = Sg + 2 * szS;           // [P] cotangents of the tile's pairs
+    // per-object access
+    auto objX = [&](int side, int t, int k, long long* base, int* r0, int* r1, int* n) {
+      if (g.mode == 0) {
+        const TTV& V = side == 0 ? g.A : g.B;
+        *base = core_base(V, k, (side == 0 ? a0 : b0) + t);
+        *r0 = V.r[k];
+        *r1 = V.r[k + 1];
+        *n = V.n[k];
+      } else {
+        const int o = (side == 0 ? a0 : b0) + t;
+        *base = g.off[(long long)o * g.dmax + k];
+        *r0 = g.rk[(long long)o * (g.dmax + 1) + k];
+        *r1 = g.rk[(long long)o * (g.dmax + 1) + k + 1];
+        *n = g.nmodes[grp * g.dmax + k];
+      }
+    };
+    const void* Ap = g.mode == 0 ? g.A.p : g.gcores;
+    const void* Bp = g.mode == 0 ? g.B.p : g.gcores;
+    // cotangents of the pairs (table mode: symmetrised for off-diagonal tiles)
+    for (int p = tid; p < P; p += nth) {
+      const int a = p / nb, b = p % nb;
+      float v;
+      if (g.mode == 0) {
+        v = g.dG[(long long)(a0 + a) * g.B.batch + (b0 + b)];
+      } else {
+        const int S = g.gstart[grp + 1] - g.gstart[grp];
+        const int la = g.perm[a0 + a], lb = g.perm[b0 + b];
+        const float* o = g.dout + g.gout_off[grp];
+        v = o[(long long)la * S + lb];
+        if (sym) v += o[(long long)lb * S + la];
+      }
+      gsm[p] = v;
+    }
+    // stage slice i of core k: trans = 0 -> [t][row][col], trans = 1 -> [t][col][row]
+    auto stage = [&](int k, int i, float* buf, int trans) {
+      int rA0, rA1, nA, rB0, rB1, nB;
+      long long bb;
+      objX(0, 0, k, &bb, &rA0, &rA1, &nA);
+      objX(1, 0, k, &bb, &rB0, &rB1, &nB);
+      for (int e = tid; e < szS; e += nth) {
+        const int side = e < szA ? 0 : 1;
+        const int R = side == 0 ? RA : RB;
+        const int e2 = side == 0 ? e : e - szA;
+        const int t = e2 / (R * R), q = e2 % (R * R);
+        const int u = q / R, v = q % R;
+        const int row = trans ? v : u, col = trans ? u : v;
+        long long base;
+        int r0, r1, n;
+        objX(side, t, k, &base, &r0, &r1, &n);
+        const bool ok = row < r0 && col < r1 && i < n;
+        const long long idx = ok ? base + ((long long)row * n + i) * r1 + col : base;
+        const void* src = side == 0 ? Ap : Bp;
+        if (sizeof(ST) == 4) {
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(buf + e);
+          const float* gp = static_cast<const float*>(src) + idx;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gp), "r"(ok ? 4 : 0));
+        } else {
+          buf[e] = ok ? ldf<ST>(static_cast<const ST*>(src), idx) : 0.0f;
+        }
+      }
+      if (sizeof(ST) == 4) asm volatile("cp.async.commit_group;\n" ::);
+    };
+    auto nmode = [&](int k) {
+      long long bb;
+      int r0, r1, n;
+      objX(0, 0, k, &bb, &r0, &r1, &n);
+      return n;
+    };
+    // ---------------- left sweep: M at every interface into the CTA scratch ------------
+    // scratch layout per interface j: [a][al][b][be]
+    for (int e = tid; e < P * PS; e += nth) {
+      const int be = e % RB, b = (e / RB) % nb, al = (e / (RB * nb)) % RA;
+      Rm[e] = (al == 0 && be == 0) ? 1.0f : 0.0f;  // Rm holds M during the left sweep
+      scr[e] = Rm[e];
+      (void)b;
+    }
+    {
+      int k = 0, i = 0, cur = 0;
+      stage(0, 0, Sg, 0);
+      float acc[2][4][4];
+      const int nblk = na * QA * nb * QB;
+      while (k < d) {
+        const int nk = nmode(k);
+        if (i == 0) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) acc[q][x][y] = 0.0f;
+        }
+        int k2 = k, i2 = i + 1;
+        if (i2 >= nk) {
+          k2 = k + 1;
+          i2 = 0;
+        }
+        if (k2 < d) {
+          stage(k2, i2, Sg + (cur ^ 1) * szS, 0);
+          if (sizeof(ST) == 4) asm volatile("cp.async.wait_group 1;\n" ::);
+        } else if (sizeof(ST) == 4) {
+          asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+        __syncthreads();
+        const float* As = Sg + cur * szS;  // [a][al][ap]
+        const float* Bs = As + szA;        // [b][be][bp]
+        // T[a][al][b][bp] = sum_be M[a][al][b][be] B[b][be][bp]  (T in RT's storage)
+        for (int blk = tid; blk < nblk; blk += nth) {
+          const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+          float t4[4][4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
+          for (int be = 0; be < RB; ++be) {
+            float4 mv;
+            mv.x = Rm[(((size_t)a * RA + 4 * qa + 0) * nb + b) * RB + be];
+            mv.y = Rm[(((size_t)a * RA + 4 * qa + 1) * nb + b) * RB + be];
+            mv.z = Rm[(((size_t)a * RA + 4 * qa + 2) * nb + b) * RB + be];
+            mv.w = Rm[(((size_t)a * RA + 4 * qa + 3) * nb + b) * RB + be];
+            fma44b(t4, mv, *reinterpret_cast<const float4*>(Bs + ((size_t)b * RB + be) * RB + 4 * qb));
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+            *reinterpret_cast<float4*>(RT + (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb) =
+                make_float4(t4[x][0], t4[x][1], t4[x][2], t4[x][3]);
+        }
+        __syncthreads();
+        // M'[a][ap][b][bp] += sum_al A[a][al][ap] T[a][al][b][bp]
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int blk = tid + q * nth;
+          if (blk < nblk) {
+            const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+            for (int al = 0; al < RA; ++al)
+              fma44b(acc[q], *reinterpret_cast<const float4*>(As + ((size_t)a * RA + al) * RA + 4 * qa),
+                     *reinterpret_cast<const float4*>(RT + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb));
+          }
+        }
+        __syncthreads();
+        cur ^= 1;
+        if (++i >= nk) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int blk = tid + q * nth;
+            if (blk < nblk) {
+              const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+#pragma unroll
+              for (int x = 0; x < 4; ++x) {
+                const size_t o = (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb;
+                const float4 v = make_float4(acc[q][x][0], acc[q][x][1], acc[q][x][2], acc[q][x][3]);
+                *reinterpret_cast<float4*>(Rm + o) = v;
+                *reinterpret_cast<float4*>(scr + (size_t)(k + 1) * P * PS + o) = v;
+              }
+            }
+          }
+          __syncthreads();
+          i = 0;
+          ++k;
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- right sweep with the gradient products ---------------------------
+    // R at interface d = 1
+    for (int e = tid; e < P * PS; e += nth) {
+      const int q = e % PS;
+      Rm[e] = q == 0 ? 1.0f : 0.0f;
+      RT[e] = q == 0 ? 1.0f : 0.0f;
+    }
+    for (int k = d - 1; k >= 0; --k) {
+      const int nk = nmode(k);
+      // M at interface k: Mm = g M in [a][al][b][be], MT = M in [b][be][a][al]
+      for (int e = tid; e < P * PS; e += nth) {
+        const int be = e % RB, b = (e / RB) % nb, al = (e / (RB * nb)) % RA, a = e / (RB * nb * RA);
+        const float v = scr[(size_t)k * P * PS + e];
+        Mm[e] = gsm[a * nb + b] * v;
+        MT[(((size_t)b * RB + be) * na + a) * RA + al] = v;
+      }
+      float racc[2][4][4];
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) racc[q][x][y] = 0.0f;
+      int cur = 0;
+      stage(k, 0, Sg, 1);
+      for (int i = 0; i < nk; ++i) {
+        if (i + 1 < nk) {
+          stage(k, i + 1, Sg + (cur ^ 1) * szS, 1);
+          if (sizeof(ST) == 4) asm volatile("cp.async.wait_group 1;\n" ::);
+        } else if (sizeof(ST) == 4) {
+          asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+        __syncthreads();
+        const float* AT = Sg + cur * szS;  // [a][ap][al]  (A_i transposed)
+        const float* BT = AT + szA;        // [b][bp][be]  (B_i transposed)
+        // (1) X[a][al][b][bp] = sum_ap A[al][ap] R[ap][bp]; Y'[b][be][a][ap] = g sum_bp B[be][bp] R[ap][bp]
+        const int nx = na * QA * nb * QB, ny = nb * QB * na * QA;
+        for (int blk = tid; blk < nx + ny; blk += nth) {
+          float t4[4][4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
+          if (blk < nx) {
+            const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+            const float* rr = Rm + (size_t)(a * nb + b) * PS + 4 * qb;  // + ap * RB
+            const float* at = AT + (size_t)a * RA * RA + 4 * qa;        // + ap * RA
+            for (int ap = 0; ap < RA; ++ap)
+              fma44b(t4, *reinterpret_cast<const float4*>(at + ap * RA), *reinterpret_cast<const float4*>(rr + ap * RB));
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              const int al = 4 * qa + x;
+              *reinterpret_cast<float4*>(Xm + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb) =
+                  make_float4(t4[x][0], t4[x][1], t4[x][2], t4[x][3]);
+#pragma unroll
+              for (int y = 0; y < 4; ++y) XT[((size_t)(a * nb + b) * RB + 4 * qb + y) * RA + al] = t4[x][y];
+            }
+          } else {
+            const int bl = blk - nx;
+            const int qa = bl % QA, a = (bl / QA) % na, qb = (bl / (QA * na)) % QB, b = bl / (QA * na * QB);
+            const float* rt = RT + (size_t)(a * nb + b) * PS + 4 * qa;  // + bp * RA
+            const float* bt = BT + (size_t)b * RB * RB + 4 * qb;        // + bp * RB
+            for (int bp = 0; bp < RB; ++bp)
+              fma44b(t4, *reinterpret_cast<const float4*>(bt + bp * RB), *reinterpret_cast<const float4*>(rt + bp * RA));
+            const float gg = gsm[a * nb + b];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+              *reinterpret_cast<float4*>(Ym + (((size_t)b * RB + 4 * qb + x) * na + a) * RA + 4 * qa) =
+                  make_float4(gg * t4[x][0], gg * t4[x][1], gg * t4[x][2], gg * t4[x][3]);
+          }
+        }
+        __syncthreads();
+        // (2) R'[a][al][b][be] += sum_bp X[al][bp] B[be][bp]
+        const int nr = na * QA * nb * QB;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int blk = tid + q * nth;
+          if (blk < nr) {
+            const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+            const float* xt = XT + (size_t)(a * nb + b) * PS + 4 * qa;  // + bp * RA
+            const float* bt = BT + (size_t)b * RB * RB + 4 * qb;        // + bp * RB
+            for (int bp = 0; bp < RB; ++bp)
+              fma44b(racc[q], *reinterpret_cast<const float4*>(xt + bp * RA), *reinterpret_cast<const float4*>(bt + bp * RB));
+          }
+        }
+        // (3) dA_a,i[al][ap] = sum_{b,be} M[al][be] Y'[be][ap];  dB_b,i[be][bp] = sum_{a,al} gM[al][be] X[al][bp]
+        const int nda = na * QA * QA, ndb = nb * QB * QB;
+        for (int blk = tid; blk < nda + ndb; blk += nth) {
+          float t4[4][4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
+          if (blk < nda) {
+            const int qp = blk % QA, qa = (blk / QA) % QA, a = blk / (QA * QA);
+            for (int b = 0; b < nb; ++b)
+              for (int be = 0; be < RB; ++be)
+                fma44b(t4, *reinterpret_cast<const float4*>(MT + (((size_t)b * RB + be) * na + a) * RA + 4 * qa),
+                       *reinterpret_cast<const float4*>(Ym + (((size_t)b * RB + be) * na + a) * RA + 4 * qp));
+            long long base;
+            int r0, r1, n;
+            objX(0, a, k, &base, &r0, &r1, &n);
+            float* dst = g.mode == 0 ? g.dA : g.dX;
+            if (dst)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) {
+                const int al = 4 * qa + x, ap = 4 * qp + y;
+                if (al < r0 && ap < r1 && t4[x][y] != 0.0f) atomicAdd(dst + base + ((long long)al * n + i) * r1 + ap, t4[x][y]);
+              }
+          } else {
+            const int bl = blk - nda;
+            const int qp = bl % QB, qb = (bl / QB) % QB, b = bl / (QB * QB);
+            for (int a = 0; a < na; ++a)
+              for (int al = 0; al < RA; ++al)
+                fma44b(t4, *reinterpret_cast<const float4*>(Mm + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb),
+                       *reinterpret_cast<const float4*>(Xm + (((size_t)a * RA + al) * nb + b) * RB + 4 * qp));
+            long long base;
+            int r0, r1, n;
+            objX(1, b, k, &base, &r0, &r1, &n);
+            float* dst = g.mode == 0 ? g.dB : g.dX;
+            if (dst)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) {
+                const int be = 4 * qb + x, bp = 4 * qp + y;
+                if (be < r0 && bp < r1 && t4[x][y] != 0.0f) atomicAdd(dst + base + ((long long)be * n + i) * r1 + bp, t4[x][y]);
+              }
+          }
+        }
+        __syncthreads();
+        cur ^= 1;
+      }
+      // R at interface k
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int blk = tid + q * nth;
+        if (blk < na * QA * nb * QB) {
+          const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            *reinterpret_cast<float4*>(Rm + (size_t)(a * nb + b) * PS + (4 * qa + x) * RB + 4 * qb) =
+                make_float4(racc[q][x][0], racc[q][x][1], racc[q][x][2], racc[q][x][3]);
+#pragma unroll
+            for (int y = 0; y < 4; ++y) RT[(size_t)(a * nb + b) * PS + (4 * qb + y) * RA + 4 * qa + x] = racc[q][x][y];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+
+static int pad4b(int r) { return (r + 3) & ~3; }
+
+size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB) {
+  const size_t P = (size_t)na * nb, PS = (size_t)RA * RB;
+  const size_t szS = (size_t)na * RA * RA + (size_t)nb * RB * RB;
+  return sizeof(float) * (7 * P * PS + 2 * szS + P);
+}
+
+// Largest balanced tile whose buffers fit one CTA (512 threads, 2 blocks per thread).
+void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB) {
+  *TA = 1;
+  *TB = 1;
+  double best = 1e300;
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int ta = 1; ta <= 16 && ta <= batchA; ++ta)
+    for (int tb = 1; tb <= 16 && tb <= batchB; ++tb) {
+      if (ta * (RA / 4) * tb * (RB / 4) > 1024) continue;
+      if (gram_tile_bwd_smem(ta, tb, RA, RB) > 200 * 1024) continue;
+      const long long tiles = (long long)((batchA + ta - 1) / ta) * ((batchB + tb - 1) / tb);
+      const long long per_sm = (tiles + sms - 1) / sms;
+      const double work = (double)per_sm * ta * tb * (1.0 + 0.5 / ta + 0.5 / tb);
+      if (work < best - 1e-9) {
+        best = work;
+        *TA = ta;
+        *TB = tb;
+      }
+    }
+}
+
+bool gram_tile_bwd_supported(const TTV& A, const TTV& B) {
+  const int RA = pad4b(A.rmax), RB = pad4b(B.rmax);
+  return RA <= 64 && RB <= 64 && gram_tile_bwd_smem(1, 1, RA, RB) <= 200 * 1024 && A.d <= T3F_MAX_D;
+}
+
+size_t ws_gram_tile_bwd(const TTV& A, const TTV& B) {
+  const int RA = pad4b(A.rmax), RB = pad4b(B.rmax);
+  int ta, tb;
+  plan_gram_tile_bwd(RA, RB, A.batch, B.batch, &ta, &tb);
+  const long long tiles = (long long)((A.batch + ta - 1) / ta) * ((B.batch + tb - 1) / tb);
+  const long long stride = (long long)(A.d + 1) * ta * tb * RA * RB;
+  return kWsHeader + align256(sizeof(float) * stride * tiles);
+}
+
+t3f_status run_gram_tile_bwd(const TTV& A, const TTV& B, const float* dG, float* dA, float* dB, void* ws,
+                             size_t ws_bytes, cudaStream_t s) {
+  T3F_CHECK(check_ws(ws, ws_bytes, ws_gram_tile_bwd(A, B)));
+  GramBwdTileArgs g;
+  memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.B = B;
+  g.RA = pad4b(A.rmax);
+  g.RB = pad4b(B.rmax);
+  plan_gram_tile_bwd(g.RA, g.RB, A.batch, B.batch, &g.TA, &g.TB);
+  g.dG = dG;
+  g.dA = dA;
+  g.dB = dB;
+  g.mode = 0;
+  g.dtype = A.dtype;
+  g.scratch = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeader);
+  g.scratch_stride = (long long)(A.d + 1) * g.TA * g.TB * g.RA * g.RB;
+  const size_t smem = gram_tile_bwd_smem(g.TA, g.TB, g.RA, g.RB);
+  const long long grid = (long long)((A.batch + g.TA - 1) / g.TA) * ((B.batch + g.TB - 1) / g.TB);
+  if (A.dtype == T3F_F32) {
+    auto kern = k_gram_tile_bwd<float>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<(unsigned)grid, 512, smem, s>>>(g);
+  } else {
+    auto kern = k_gram_tile_bwd<__nv_bfloat16>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<(unsigned)grid, 512, smem, s>>>(g);
+  }
+  return launch_status();
+}
+
+// Persistent adjoint over a work list of ragged tiles (grouped Gram matrices).
+t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, const long long* off, const int* rk,
+                                      const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
+                                      const int* gd, const int* perm, const float* dout, const long long* gout_off,
+                                      float* dX, float* scratch, long long scratch_stride, size_t smem, int grid,
+                                      cudaStream_t s) {
+  GramBwdTileArgs g;
+  memset(&g, 0, sizeof(g));
+  g.mode = 1;
+  g.dtype = dtype;
+  g.off = off;
+  g.rk = rk;
+  g.dmax = dmax;
+  g.gcores = cores;
+  g.nmodes = nmodes;
+  g.items = items;
+  g.nitems = nitems;
+  g.head = head;
+  g.gstart = gstart;
+  g.gd = gd;
+  g.perm = perm;
+  g.dout = dout;
+  g.gout_off = gout_off;
+  g.dX = dX;
+  g.scratch = scratch;
+  g.scratch_stride = scratch_stride;
+  if (smem > 227 * 1024) return T3F_ERR_UNSUPPORTED;
+  if (dtype == T3F_F32) {
+    auto kern = k_gram_tile_bwd<float>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<grid, 512, smem, s>>>(g);
+  } else {
+    auto kern = k_gram_tile_bwd<__nv_bfloat16>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<grid, 512, smem, s>>>(g);
+  }
+  return launch_status();
+}
+
+}  // namespace t3f

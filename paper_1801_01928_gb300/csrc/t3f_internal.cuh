@@ -86,6 +86,12 @@ t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V,
 bool gram_tile_supported(const TTV& A, const TTV& B);
 t3f_status run_gram_tile(const TTV& A, const TTV& B, float* out, cudaStream_t s);
 
+// Tiled Gram adjoint (gram_tile_bwd.cu).
+bool gram_tile_bwd_supported(const TTV& A, const TTV& B);
+size_t ws_gram_tile_bwd(const TTV& A, const TTV& B);
+t3f_status run_gram_tile_bwd(const TTV& A, const TTV& B, const float* dG, float* dA, float* dB, void* ws,
+                             size_t ws_bytes, cudaStream_t s);
+
 // Workspace sizes (bytes, header included) of the operations.
 size_t ws_gram_bwd(const TTV& A, const TTV& B);
 size_t ws_norm(const TTV& A);
