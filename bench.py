@@ -222,11 +222,40 @@ class Workload:
             t3f.gram_groups(X4, self.gstart, self.ws4, self.tiles4, out=self.G4, norms=self.n4)
             t3f.gram_groups_backward(X4, self.gstart, self.ws4, self.devbuf["dG4"], self.tiles4, dcores=self.dX4)
         torch.cuda.current_stream(self.dev).wait_stream(side)
-        self.graph4 = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph4):
+        self.graph4f = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph4f):
             t3f.gram_groups(X4, self.gstart, self.ws4, self.tiles4, out=self.G4, norms=self.n4)
+        self.graph4b = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph4b):
             t3f.gram_groups_backward(X4, self.gstart, self.ws4, self.devbuf["dG4"], self.tiles4, dcores=self.dX4)
         torch.cuda.synchronize(self.dev)
+
+    def plain_uneven(self):
+        """The single-shape FP32 comparator for the uneven batch: every group zero-padded to
+        its largest rank (inner products unchanged) and run as one uniform Gram + adjoint
+        launch sequence per group, without the work queue or graph."""
+        t3f, torch = self.t3f, self.torch
+        dims, modes, ranks, _ = self.r4meta
+        rg = self.t3f.RaggedTT(self.host["X4"], dims, modes, ranks, self.r4meta[3])
+        groups, off = [], 0
+        for g in range(len(self.gstart) - 1):
+            objs = list(range(self.gstart[g], self.gstart[g + 1]))
+            d, n = dims[objs[0]], modes[objs[0]]
+            R = max(max(ranks[o][1:-1], default=1) for o in objs)
+            rk = [1] + [R] * (d - 1) + [1]
+            cores = []
+            for k in range(d):
+                blk = np.zeros((len(objs), rk[k], n[k], rk[k + 1]), np.float32)
+                for j, o in enumerate(objs):
+                    c = rg.object_cores(o)[k].numpy()
+                    blk[j, :c.shape[0], :, :c.shape[2]] = c
+                cores.append(blk)
+            A = t3f.TT.from_cores(cores, device=self.dev)
+            S_ = len(objs)
+            dG = self.devbuf["dG4"][off:off + S_ * S_].view(S_, S_)
+            off += S_ * S_
+            groups.append((A, dG))
+        return groups
 
     def tt(self, key):
         n, r, b, m = self.meta[key]
@@ -254,17 +283,19 @@ class Workload:
             "orth5": f_orth(n16, S.tt_ranks(20, 32)),
             "psum": f_psum_fwd(n16, ru5, rz5, 1000),
             "psum_bwd": f_psum_bwd(n16, ru5, rz5, 1000),
-            "uneven": self.uneven_flops(),
+            "uneven": self.uneven_flops(False),
+            "uneven_bwd": self.uneven_flops(True),
         }
 
-    def uneven_flops(self):
-        """Unique pairs (a <= b) of every group: left sweep + adjoint of each pair."""
+    def uneven_flops(self, bwd):
+        """Unique pairs (a <= b) of every group: the left sweep (forward) or the adjoint."""
         dims, modes, ranks, _ = self.r4meta
         tot = 0.0
         for g in range(len(self.gstart) - 1):
             for a in range(self.gstart[g], self.gstart[g + 1]):
                 for b in range(a, self.gstart[g + 1]):
-                    tot += f_left_sweep(modes[a], ranks[a], ranks[b]) + f_gram_bwd(modes[a], ranks[a], ranks[b])
+                    f = f_gram_bwd if bwd else f_left_sweep
+                    tot += f(modes[a], ranks[a], ranks[b])
         return tot
 
 
@@ -302,7 +333,8 @@ def run_step(w, timers=None, stream=None):
     dU5 = timed("psum", lambda: t3f.project_sum(U5, V5, Z5, w.devbuf["c5"]))
     # adjoint of 1/2 ||project_sum||^2: the cotangent of the coordinates is dU5 itself
     dZ, dc = timed("psum_bwd", lambda: t3f.project_sum_backward(U5, V5, Z5, w.devbuf["c5"], dU5))
-    timed("uneven", lambda: w.graph4.replay())
+    timed("uneven", lambda: w.graph4f.replay())
+    timed("uneven_bwd", lambda: w.graph4b.replay())
     out.update(loss=loss, dX=dX.data, dU2=dU2.data, G=G, dA=dA.data, dB=dB.data, norm=nrm,
                dAm=dAm.data, dxv=dxv.data, dU5=dU5.data, dc=dc, G4=w.G4, n4=w.n4, dX4=w.dX4)
     out["_bulk"] = (C, dZ)  # stay on the device
@@ -566,6 +598,31 @@ def gpu_arm(args):
         "clocks": clk.summary(),
         "ops": per_op,
     }
+    # single-shape FP32 comparator for the uneven batch (outside the timed step)
+    if not args.no_comparator:
+        groups = w.plain_uneven()
+        def plain():
+            for A, dG in groups:
+                t3f.gram(A, A)
+                t3f.gram_backward(A, A, dG)
+        plain()
+        torch.cuda.synchronize(dev)
+        reps = 2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            plain()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        pm = e0.elapsed_time(e1) / reps
+        um = op_ms["uneven"] + op_ms["uneven_bwd"]
+        uf = flops["uneven"] + flops["uneven_bwd"]
+        line["comparators"] = {"uneven_plain_fp32": {
+            "what": "per-group uniform Gram + adjoint launches, ranks zero-padded to the group maximum",
+            "ms": round(pm, 3), "gflops_same_work": round(uf / (pm * 1e-3) / 1e9, 1),
+            "uneven_ms": round(um, 3), "uneven_speedup": round(pm / um, 2)}}
+        del groups
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f, s, desc, _ = oracle_sample(args.cpu_fraction)
         line["cpu_baseline"] = {"value": round(f / s / 1e9, 4), "unit": "GFLOP/s", "cores": 1,
@@ -585,6 +642,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-fraction", type=float, default=0.15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

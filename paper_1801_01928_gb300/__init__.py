@@ -6,6 +6,7 @@ a hand-written adjoint -- behind the C ABI of include/t3f.h.
 The Python layer is argument marshalling over libt3f.so; import fails loudly at call time if
 the library has not been built (``python -m paper_1801_01928_gb300.build``).
 """
+from . import autograd  # noqa: F401,E402
 from ._binding import (  # noqa: F401
     BF16, DEFAULT_TILES, EXPORTS, F32, F64, LIB_PATH, RaggedTT, T3FError, TT, autotune_gram_groups,
     device_status, gather, gather_backward, gram_groups, gram_groups_backward, gram_groups_prepare,
