@@ -578,7 +578,7 @@ def gpu_arm(args):
     if os.path.exists(prof):
         try:
             tj = json.load(open(prof))
-            traffic = tj.get(dom)
+            traffic = tj.get(dom, {}).get("dram_bytes")
         except (OSError, ValueError):
             traffic = None
     line = {

@@ -111,7 +111,13 @@ size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* b, int64_t 
  * G[a * B->batch + b] = <A_a, B_b> = sum over all elements of full(A_a) * full(B_b),
  * computed by the left transfer sweep M_0 = 1, M_k = sum_i A_k[:,i,:]^T M_{k-1} B_k[:,i,:].
  * A, B: TT-vectors with equal d and n_k (else T3F_ERR_SHAPE); F32 or BF16 cores; ranks may
- * differ between A and B. G: device float [A->batch][B->batch]. math: t3f_math.
+ * differ between A and B. G: device float [A->batch][B->batch]. math: t3f_math --
+ *   FP32: CUDA-core FP32 arithmetic throughout.
+ *   TF32 (F32 cores) / BF16 (F32 or BF16 cores): the two products of every sweep step run on
+ *   the tensor cores with operands rounded to TF32 / BF16 (round to nearest) and FP32
+ *   accumulation; ranks <= 64 (zero-padded to 16, 32 or 64), else T3F_ERR_UNSUPPORTED.
+ * ws: t3f_workspace_size(T3F_OP_GRAM) bytes (the error word; may be NULL for FP32). A
+ * tensor-core wait that runs out writes T3F_ERR_TIMEOUT there (see t3f_device_status).
  */
 t3f_status t3f_gram(const t3f_tt* A, const t3f_tt* B, float* G, int32_t math,
                     void* ws, size_t ws_bytes, t3f_stream_t stream);

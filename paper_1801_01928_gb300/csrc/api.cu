@@ -132,7 +132,7 @@ extern "C" size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* 
                       op == T3F_OP_PSUM_BWD;
   if (need_b && (!b || make_view(b, &vb, -1, b->m != nullptr) != T3F_OK)) return 0;
   switch (op) {
-    case T3F_OP_GRAM: return 0;
+    case T3F_OP_GRAM: return kWsHeader;
     case T3F_OP_GRAM_BWD: return ws_gram_bwd(va, vb);
     case T3F_OP_NORM: return ws_norm(va);
     case T3F_OP_GATHER: return ws_gather(va, n_items, false);

@@ -260,9 +260,12 @@ extern "C" t3f_status t3f_gram(const t3f_tt* A, const t3f_tt* B, float* G, int32
   T3F_CHECK(gram_views(A, B, &va, &vb));
   if (!G) return T3F_ERR_ARG;
   if (math != T3F_MATH_FP32 && math != T3F_MATH_TF32 && math != T3F_MATH_BF16) return T3F_ERR_ARG;
-  if (math != T3F_MATH_FP32) return T3F_ERR_UNSUPPORTED;
-  (void)ws;
-  (void)ws_bytes;
+  if (math != T3F_MATH_FP32) {
+    if (!gram_mma_supported(va, vb, math)) return T3F_ERR_UNSUPPORTED;
+    int* err = (ws && ws_bytes >= kWsHeader) ? static_cast<int*>(ws) : nullptr;
+    if (err && cudaMemsetAsync(err, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess) return T3F_ERR_CUDA;
+    return run_gram_mma(va, vb, G, math, err, (cudaStream_t)stream);
+  }
   if (gram_tile_supported(va, vb)) return run_gram_tile(va, vb, G, (cudaStream_t)stream);
   return run_pair_sweep(va, vb, 0, G, nullptr, nullptr, (cudaStream_t)stream);
 }

@@ -86,6 +86,11 @@ t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V,
 bool gram_tile_supported(const TTV& A, const TTV& B);
 t3f_status run_gram_tile(const TTV& A, const TTV& B, float* out, cudaStream_t s);
 
+// Tensor-core Gram sweep (gram_mma.cu): TF32 (F32 cores) or BF16 (F32 or BF16 cores)
+// operands, FP32 accumulation; ranks <= 64.
+bool gram_mma_supported(const TTV& A, const TTV& B, int math);
+t3f_status run_gram_mma(const TTV& A, const TTV& B, float* out, int math, int* err, cudaStream_t s);
+
 // Tiled Gram adjoint (gram_tile_bwd.cu).
 bool gram_tile_bwd_supported(const TTV& A, const TTV& B);
 size_t ws_gram_tile_bwd(const TTV& A, const TTV& B);

@@ -44,7 +44,7 @@ def test_completion_loss_autograd(lib):
     Xo = objects(X)[0]
     ref_loss = O.completion_loss(Xo, idx, y.astype(np.float64))
     _, ref_grad = O.completion_loss_grad(Xo, idx, y.astype(np.float64))
-    assert abs(float(loss) - ref_loss) / abs(ref_loss) < TOL["fp32"]
+    assert abs(float(loss.detach()) - ref_loss) / abs(ref_loss) < TOL["fp32"]
     got = _host_cores(lib, Xt.data.grad, Xt)
     assert rel_err_cores([g[0] for g in got], [3.0 * g for g in ref_grad]) < TOL["fp32"]
     # central differences of the CUDA forward along a random direction
@@ -91,15 +91,17 @@ def test_gram_autograd(lib, same):
     else:
         assert rel_err_cores(_host_cores(lib, At.data.grad, At), batched(dA)) < TOL["fp32"]
         assert rel_err_cores(_host_cores(lib, Bt.data.grad, Bt), batched(dB)) < TOL["fp32"]
-    # the Gram matrix is bilinear: central differences along (DA, DB) are exact up to rounding
+    # full(A) is multilinear in A's cores, so f is a polynomial of degree d (2d for B = A)
+    # along DA: a small step keeps the O(h^2) truncation far below the tolerance
     DA = torch.randn_like(At.data)
     if same:
-        f = lambda d: (AG.gram(lib.TT(d, At.n, At.ranks, At.batch), lib.TT(d, At.n, At.ranks, At.batch)) * W).sum()
-        fd = _fd(f, At.data.detach(), DA, 1e-2)
+        f = lambda d: (AG.gram(lib.TT(d, At.n, At.ranks, At.batch), lib.TT(d, At.n, At.ranks, At.batch)).double()
+                       * W.double()).sum()
+        fd = _fd(f, At.data.detach(), DA, 1e-3)
         ad = float((At.data.grad.double() * DA.double()).sum())
     else:
-        f = lambda d: (AG.gram(lib.TT(d, At.n, At.ranks, At.batch), Bt) * W).sum()
-        fd = _fd(f, At.data.detach(), DA, 1e-2)
+        f = lambda d: (AG.gram(lib.TT(d, At.n, At.ranks, At.batch), Bt).double() * W.double()).sum()
+        fd = _fd(f, At.data.detach(), DA, 1e-3)
         ad = float((At.data.grad.double() * DA.double()).sum())
     assert abs(fd - ad) / abs(ad) < 1e-3
 
@@ -124,9 +126,10 @@ def test_project_sum_autograd(lib):
                                [x.double().cpu().numpy()[0] for x in rb.cores()])
     assert rel_err_cores(_host_cores(lib, Zt.data.grad, Zt), batched(rZ)) < TOL["fp32"]
     assert rel_err(ct.grad.cpu().numpy(), rc) < TOL["fp32"]
-    # project_sum is linear in each Z_j and bilinear in (c, Z): differences along Z are exact
+    # project_sum is linear in each Z_j as a tensor, i.e. multilinear in its cores
     DZ = torch.randn_like(Zt.data)
-    f = lambda d: (AG.project_sum(U, V, lib.TT(d, Zt.n, Zt.ranks, Zt.batch), ct.detach()).data * Rbar).sum()
-    fd = _fd(f, Zt.data.detach(), DZ, 1e-2)
+    f = lambda d: (AG.project_sum(U, V, lib.TT(d, Zt.n, Zt.ranks, Zt.batch), ct.detach()).data.double()
+                   * Rbar.double()).sum()
+    fd = _fd(f, Zt.data.detach(), DZ, 1e-3)
     ad = float((Zt.data.grad.double() * DZ.double()).sum())
     assert abs(fd - ad) / abs(ad) < 1e-3
