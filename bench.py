@@ -341,6 +341,51 @@ def run_step(w, timers=None, stream=None):
     return out
 
 
+def reduced_precision(w, flops, flush, stream, reps=5):
+    """TF32 / BF16 tensor-core Gram of config 3a and the uneven batch with BF16 cores, each
+    timed with CUDA events (L2 flushed before every repetition) and compared with the FP32
+    result of the same inputs (normwise relative difference)."""
+    t3f, torch = w.t3f, w.torch
+    A3, B3 = w.tt("A3"), w.tt("B3")
+    G32 = t3f.gram(A3, B3).double()
+    X4 = w.ragged()
+    X4b = t3f.RaggedTT(X4.data.to(torch.bfloat16), X4.dims, X4.modes, X4.ranks, X4.offsets)
+    ws4b = t3f.gram_groups_prepare(X4b, w.gstart, w.tiles4)
+    G4_32 = w.G4.double()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    def rel(x, y):
+        return float((x.double() - y).norm() / y.norm())
+
+    out = {}
+    for math_ in ("tf32", "bf16"):
+        ms = timed(lambda: t3f.gram(A3, B3, math=math_))
+        G = t3f.gram(A3, B3, math=math_)
+        out[f"gram_{math_}"] = {"ms": round(ms, 4), "gflops": round(flops["gram"] / (ms * 1e-3) / 1e9, 1),
+                                "diff_vs_fp32": round(rel(G, G32), 6),
+                                "path": "tcgen05 " + math_ + " products, FP32 accumulation in TMEM"}
+    ms = timed(lambda: t3f.gram_groups(X4b, w.gstart, ws4b, w.tiles4))
+    Gb, _ = t3f.gram_groups(X4b, w.gstart, ws4b, w.tiles4)
+    out["uneven_bf16_cores"] = {"ms": round(ms, 4), "gflops": round(flops["uneven"] / (ms * 1e-3) / 1e9, 1),
+                                "diff_vs_fp32": round(rel(Gb, G4_32), 6),
+                                "path": "BF16 cores, FP32 CUDA-core arithmetic (grouped work list)"}
+    return out
+
+
 # ---------------------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------------------
@@ -623,6 +668,8 @@ def gpu_arm(args):
             "ms": round(pm, 3), "gflops_same_work": round(uf / (pm * 1e-3) / 1e9, 1),
             "uneven_ms": round(um, 3), "uneven_speedup": round(pm / um, 2)}}
         del groups
+    # reduced-precision forms of the same work (outside the timed step; FP32 step above)
+    line["reduced_precision"] = reduced_precision(w, flops, flush, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f, s, desc, _ = oracle_sample(args.cpu_fraction)
         line["cpu_baseline"] = {"value": round(f / s / 1e9, 4), "unit": "GFLOP/s", "cores": 1,

@@ -234,9 +234,17 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
   long long pmax = 0;
   T3F_CHECK(make_items(tl, false, &P->items, &smem, &pmax));
   P->nitems = (int)(P->items.size() / 8);
-  // adjoint tiles: half the side (the adjoint holds seven partial tiles per pair)
+  // adjoint tiles: the adjoint holds seven partial tiles per pair, so its side is the largest
+  // one (at most the forward side) whose buffers fit a CTA at the bucket's largest rank;
+  // that keeps most of the 512 threads busy with a 4 x 4 block each
   int tlb[kBuckets];
-  for (int b = 0; b < kBuckets; ++b) tlb[b] = std::max(1, tl[b] / 2);
+  for (int b = 0; b < kBuckets; ++b) {
+    const int R = kBucketMax[b];
+    int side = 1;
+    for (int t = 2; t <= tl[b]; ++t)
+      if ((long long)t * t * (R / 4) * (R / 4) <= 1024 && gram_tile_bwd_smem(t, t, R, R) <= 200 * 1024) side = t;
+    tlb[b] = side;
+  }
   size_t bsmem = 0;
   long long bpmax = 0;
   T3F_CHECK(make_items(tlb, true, &P->bitems, &bsmem, &bpmax));

@@ -24,12 +24,16 @@ namespace {
 constexpr uint32_t kLBO = 144;
 constexpr int kMmaThreads = 256;
 constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kSkew = 64;  // extra bytes between consecutive operands (16-bank shift)
+
+// Slice operands are double-buffered unless that would not fit (TF32 at R = 64).
+__host__ __device__ constexpr int slice_buffers(int kind, int R) { return (kind == 0 && R == 64) ? 1 : 2; }
 
 struct GramMmaArgs {
   TTV A, B;
   float* out;      // [bA][bB]
   int* err;        // device error word (nullable)
-  uint32_t o_mop, o_top, o_as, smem_bytes;  // region offsets (the B slices start at 0)
+  uint32_t smem_bytes;
 };
 
 template <int KIND>
@@ -45,6 +49,14 @@ struct OpT<0> {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
     *reinterpret_cast<uint32_t*>(p) = r;
   }
+  static __device__ __forceinline__ uint32_t cv(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+  }
+  static __device__ __forceinline__ uint4 pack(const float (&v)[4]) {
+    return make_uint4(cv(v[0]), cv(v[1]), cv(v[2]), cv(v[3]));
+  }
 };
 template <>
 struct OpT<1> {
@@ -53,6 +65,13 @@ struct OpT<1> {
   static constexpr int KI = 16;
   static __device__ __forceinline__ void st(char* p, float v) {
     *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+  }
+  static __device__ __forceinline__ uint32_t cv2(float lo, float hi) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&b);
+  }
+  static __device__ __forceinline__ uint4 pack(const float (&v)[8]) {
+    return make_uint4(cv2(v[0], v[1]), cv2(v[2], v[3]), cv2(v[4], v[5]), cv2(v[6], v[7]));
   }
 };
 
@@ -143,27 +162,31 @@ template <int KIND, int R, typename ST>
 __global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant__ GramMmaArgs g) {
   using O = OpT<KIND>;
   constexpr int ES = O::ES;
-  constexpr int T = 16 / ES;
+  constexpr int T = 16 / ES;                                   // elements per 16 bytes
   constexpr int TL = 128 / R;                                  // objects per tile side
+  constexpr int NBUF = slice_buffers(KIND, R);                 // slice double buffering
   constexpr uint32_t SBO = (uint32_t)(R / T) * kLBO;          // every operand has K = R
-  constexpr uint32_t SZ_BIG = 16u * SBO;                       // 128 x R operand (M_b, T_a)
-  constexpr uint32_t SZ_SL = (uint32_t)(R / 8) * SBO;          // R x R operand (slices)
+  constexpr uint32_t SZ_BIG = 16u * SBO + kSkew;               // stride of 128 x R operands (M_b, T_a)
+  constexpr uint32_t SZ_SL = (uint32_t)(R / 8) * SBO + kSkew;  // stride of R x R operands (slices)
   constexpr uint32_t ID = idesc(O::FMT, R);
-  constexpr int PER = TL * R * R / kMmaThreads;               // staged elements per thread and side
-  static_assert(PER * kMmaThreads == TL * R * R, "slice staging must divide evenly");
+  constexpr int KG = R / T;                                    // K groups of T elements
+  constexpr int UPT = TL * R * KG / kMmaThreads;               // staged K runs per thread and side
+  constexpr int USTEP = kMmaThreads / R;
+  static_assert(UPT * kMmaThreads == TL * R * KG && kMmaThreads % R == 0, "slice staging must divide evenly");
 
   extern __shared__ __align__(128) char sm[];
-  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntb = (g.B.batch + TL - 1) / TL;
   const int a0 = (blockIdx.x / ntb) * TL, b0 = (blockIdx.x % ntb) * TL;
   const int na = min(TL, g.A.batch - a0), nb = min(TL, g.B.batch - b0);
-  char* bsl = sm;                 // TL operands B_b,i: rows bp, K = be
-  char* asl = sm + g.o_as;        // TL operands A_a,i: rows ap, K = al
-  char* mop = sm + g.o_mop;       // TL operands M_b: rows (a, al), K = be
-  char* top = sm + g.o_top;       // TL operands T_a: rows (b, bp), K = al
+  // regions: B slices [NBUF][TL], A slices [NBUF][TL], M_b [TL], T_a [TL]
+  char* const bsl = sm;
+  char* const asl = sm + NBUF * TL * SZ_SL;
+  char* const mop = sm + 2 * NBUF * TL * SZ_SL;
+  char* const top = mop + TL * SZ_BIG;
 
   for (uint32_t e = (uint32_t)tid * 16u; e < g.smem_bytes; e += kMmaThreads * 16u)
     *reinterpret_cast<uint4*>(sm + e) = make_uint4(0u, 0u, 0u, 0u);
@@ -171,7 +194,8 @@ __global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant_
   // M_0 = 1 for every pair: element (row a*R, col 0) of every M_b
   if (tid < TL * TL) O::st(mop + (tid / TL) * SZ_BIG + eoff<ES>((tid % TL) * R, 0, SBO), 1.0f);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s_bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s_bar[1])));
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
@@ -183,61 +207,89 @@ __global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant_
   __syncthreads();
   tc_after();
   const uint32_t tmem = s_tmem;
-  const uint32_t bar = su32(&s_bar);
-  uint32_t phase = 0;
-  bool failed = false;  // block-uniform: set when a tensor-core wait ran out
+  const uint32_t bar1 = su32(&s_bar[0]), bar2 = su32(&s_bar[1]);
+  uint32_t ph1 = 0, ph2 = 0;
+  bool pending2 = false;   // an MMA2 batch has been committed and not yet waited for
+  int bad = 0;             // this thread saw a wait run out
+  bool failed = false;     // block-uniform
 
-  // per-thread staging coordinates (identical for both sides): element e = tid + j*256 of
-  // the TL x R x R block is (object o, column-of-K c, row r) = (e / R^2, (e / R) % R, e % R)
   const int q = warp & 3, h = warp >> 2;       // TMEM lane quarter, column half
   const int row = q * 32 + lane;               // TMEM lane = operand row of this thread
+  const int sr = tid % R, su = tid / R;        // staging: operand row, first K-run index
   const int d = g.A.d;
 
-  for (int k = 0; k < d; ++k) {
+  // slice i of core k of both sides -> registers: K run j of this thread covers object
+  // o = (su + j*USTEP) / KG, columns c = ((su + j*USTEP) % KG) * T + t, row sr
+  float pb[UPT][T], pa[UPT][T];
+  auto load_slice = [&](int k, int i) {
     const int rA0 = g.A.r[k], rA1 = g.A.r[k + 1], rB0 = g.B.r[k], rB1 = g.B.r[k + 1], n = g.A.n[k];
-    const long long baseA = g.A.off[k] + (long long)a0 * g.A.osz[k];
-    const long long baseB = g.B.off[k] + (long long)b0 * g.B.osz[k];
-    const long long oszA = g.A.osz[k], oszB = g.B.osz[k];
-    for (int i = 0; i < n; ++i) {
-      // ---- stage the slices B_b,i (row bp, col be) and A_a,i (row ap, col al)
-      float vb[PER], va[PER];
+    const long long bA = g.A.off[k] + (long long)a0 * g.A.osz[k] + (long long)i * rA1 + sr;
+    const long long bB = g.B.off[k] + (long long)b0 * g.B.osz[k] + (long long)i * rB1 + sr;
+    const long long sA = (long long)n * rA1, sB = (long long)n * rB1;
 #pragma unroll
-      for (int j = 0; j < PER; ++j) {
-        const int e = tid + j * kMmaThreads;
-        const int o = e / (R * R), c = (e / R) % R, r = e % R;
-        vb[j] = (o < nb && c < rB0 && r < rB1) ? ldc<ST>(g.B.p, baseB + o * oszB + ((long long)c * n + i) * rB1 + r)
-                                               : 0.0f;
-        va[j] = (o < na && c < rA0 && r < rA1) ? ldc<ST>(g.A.p, baseA + o * oszA + ((long long)c * n + i) * rA1 + r)
-                                               : 0.0f;
-      }
+    for (int j = 0; j < UPT; ++j) {
+      const int w = su + j * USTEP, o = w / KG, c0 = (w % KG) * T;
 #pragma unroll
-      for (int j = 0; j < PER; ++j) {
-        const int e = tid + j * kMmaThreads;
-        const int o = e / (R * R), c = (e / R) % R, r = e % R;
-        const uint32_t off = eoff<ES>(r, c, SBO);
-        O::st(bsl + o * SZ_SL + off, vb[j]);
-        O::st(asl + o * SZ_SL + off, va[j]);
+      for (int t = 0; t < T; ++t) {
+        const int c = c0 + t;
+        pb[j][t] = (o < nb && c < rB0 && sr < rB1) ? ldc<ST>(g.B.p, bB + o * g.B.osz[k] + c * sB) : 0.0f;
+        pa[j][t] = (o < na && c < rA0 && sr < rA1) ? ldc<ST>(g.A.p, bA + o * g.A.osz[k] + c * sA) : 0.0f;
       }
+    }
+  };
+  // registers -> slice buffer s: one 16-byte store per K run (a whole core-matrix row)
+  auto store_slice = [&](int s) {
+#pragma unroll
+    for (int j = 0; j < UPT; ++j) {
+      const int w = su + j * USTEP, o = w / KG, cg = w % KG;
+      const uint32_t off = (uint32_t)(sr >> 3) * SBO + (uint32_t)cg * kLBO + (uint32_t)(sr & 7) * 16u;
+      *reinterpret_cast<uint4*>(bsl + (s * TL + o) * SZ_SL + off) = O::pack(pb[j]);
+      *reinterpret_cast<uint4*>(asl + (s * TL + o) * SZ_SL + off) = O::pack(pa[j]);
+    }
+  };
+
+  int iter = 0;
+  load_slice(0, 0);
+  for (int k = 0; k < d && !failed; ++k) {
+    const int n = g.A.n[k];
+    for (int i = 0; i < n; ++i, ++iter) {
+      const int s = NBUF == 2 ? (iter & 1) : 0;
+      if (NBUF == 1 && pending2) {  // the single slice buffer is still read by MMA2
+        bad |= !mbar_wait(bar2, ph2);
+        ph2 ^= 1u;
+        pending2 = false;
+      }
+      store_slice(s);
       async_fence();
       tc_before();
-      __syncthreads();
-      // ---- MMA1: T for every b
+      if (__syncthreads_or(bad)) { failed = true; break; }
+      // ---- MMA1: T for every b (TMEM columns b*R .. b*R + R - 1)
       if (tid == 0) {
         tc_after();
 #pragma unroll 1
         for (int b = 0; b < TL; ++b) {
-          const uint32_t am = su32(mop + b * SZ_BIG), bm = su32(bsl + b * SZ_SL);
+          const uint32_t am = su32(mop + b * SZ_BIG), bm = su32(bsl + (s * TL + b) * SZ_SL);
 #pragma unroll
           for (int kk = 0; kk < R / O::KI; ++kk)
             mma<KIND>(tmem + (uint32_t)(b * R), sdesc(am + kk * 2 * kLBO, SBO), sdesc(bm + kk * 2 * kLBO, SBO), ID,
                       kk > 0);
         }
-        mma_commit(bar);
+        mma_commit(bar1);
       }
-      failed = __syncthreads_or(!mbar_wait(bar, phase)) != 0;
-      phase ^= 1u;
+      // ---- prefetch the next slice while the products run
+      {
+        int k2 = k, i2 = i + 1;
+        if (i2 == n) { ++k2; i2 = 0; }
+        if (k2 < d) load_slice(k2, i2);
+      }
+      bad |= !mbar_wait(bar1, ph1);
+      ph1 ^= 1u;
+      if (pending2) {  // T_a is still read by the previous MMA2
+        bad |= !mbar_wait(bar2, ph2);
+        ph2 ^= 1u;
+        pending2 = false;
+      }
       tc_after();
-      if (failed) break;
       // ---- epilogue 1: T (rows (a, al), cols (b, bp)) -> T_a[(b, bp), al]
       {
         const int a = row / R, al = row % R;
@@ -253,26 +305,27 @@ __global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant_
       }
       async_fence();
       tc_before();
-      __syncthreads();
-      // ---- MMA2: D_a += T_a A_a,i for every a
+      if (__syncthreads_or(bad)) { failed = true; break; }
+      // ---- MMA2: D_a += T_a A_a,i for every a (TMEM columns 128 + a*R ..)
       if (tid == 0) {
         tc_after();
 #pragma unroll 1
         for (int a = 0; a < TL; ++a) {
-          const uint32_t am = su32(top + a * SZ_BIG), bm = su32(asl + a * SZ_SL);
+          const uint32_t am = su32(top + a * SZ_BIG), bm = su32(asl + (s * TL + a) * SZ_SL);
 #pragma unroll
           for (int kk = 0; kk < R / O::KI; ++kk)
             mma<KIND>(tmem + 128u + (uint32_t)(a * R), sdesc(am + kk * 2 * kLBO, SBO),
                       sdesc(bm + kk * 2 * kLBO, SBO), ID, (i > 0 || kk > 0) ? 1u : 0u);
         }
-        mma_commit(bar);
+        mma_commit(bar2);
       }
-      failed = __syncthreads_or(!mbar_wait(bar, phase)) != 0;
-      phase ^= 1u;
-      tc_after();
-      if (failed) break;
+      pending2 = true;
     }
     if (failed) break;
+    bad |= !mbar_wait(bar2, ph2);
+    ph2 ^= 1u;
+    pending2 = false;
+    tc_after();
     // ---- epilogue 2: D (rows (b, bp), cols (a, ap)) -> M_b[(a, ap), bp], or the Gram entries
     {
       const int b = row / R, bp = row % R;
@@ -297,14 +350,15 @@ __global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant_
     }
     async_fence();
     tc_before();
-    __syncthreads();
+    if (__syncthreads_or(bad)) failed = true;
     tc_after();
   }
   if (failed) {
-    // a product did not signal completion: give it one more bounded wait before the
-    // tensor memory is released, and report the timeout
+    // a product did not signal completion: one more bounded wait for whatever is still
+    // in flight before the tensor memory is released, and report the timeout
     if (tid == 0 && g.err) atomicExch(g.err, (int)T3F_ERR_TIMEOUT);
-    mbar_wait(bar, phase);
+    mbar_wait(bar1, ph1);
+    if (pending2) mbar_wait(bar2, ph2);
   }
   tc_before();
   __syncthreads();
@@ -315,27 +369,22 @@ __global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant_
 
 int pad_pow2_16(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : 64); }
 
-template <int KIND>
-constexpr uint32_t es_of() { return KIND == 0 ? 4u : 2u; }
-
-// Operand regions for rank R, in this order: B slices (TL x R x R), A slices, M (TL x 128 x R),
-// T (TL x 128 x R). The square slice operands come first so that every address a descriptor
-// can form -- under either assignment of the two stride fields -- stays inside the allocation.
-void mma_layout(int kind, int R, uint32_t* o_as, uint32_t* o_mop, uint32_t* o_top, uint32_t* total) {
+// Operand regions for rank R, in this order: B slices [NBUF][TL] (R x R), A slices, M_b [TL]
+// (128 x R), T_a [TL]. The square slice operands come first so that every address a
+// descriptor can form -- under either assignment of its two stride fields -- stays inside
+// the allocation; consecutive operands are kSkew bytes further apart than their size.
+uint32_t mma_smem_bytes(int kind, int R) {
   const uint32_t T = 16u / (kind == 0 ? 4u : 2u);
   const uint32_t sbo = (uint32_t)(R / (int)T) * kLBO;
   const uint32_t TL = 128u / (uint32_t)R;
-  const uint32_t big = TL * 16u * sbo, sl = TL * (uint32_t)(R / 8) * sbo;
-  *o_as = sl;
-  *o_mop = 2u * sl;
-  *o_top = 2u * sl + big;
-  *total = 2u * sl + 2u * big;
+  const uint32_t big = 16u * sbo + kSkew, sl = (uint32_t)(R / 8) * sbo + kSkew;
+  return 2u * (uint32_t)slice_buffers(kind, R) * TL * sl + 2u * TL * big;
 }
 
 template <int KIND, int R, typename ST>
 t3f_status launch_mma(const GramMmaArgs& g0, cudaStream_t s) {
   GramMmaArgs g = g0;
-  mma_layout(KIND, R, &g.o_as, &g.o_mop, &g.o_top, &g.smem_bytes);
+  g.smem_bytes = mma_smem_bytes(KIND, R);
   constexpr int TL = 128 / R;
   const long long grid = (long long)((g.A.batch + TL - 1) / TL) * ((g.B.batch + TL - 1) / TL);
   if (grid <= 0) return T3F_OK;
