@@ -378,11 +378,14 @@ def reduced_precision(w, flops, flush, stream, reps=5):
         out[f"gram_{math_}"] = {"ms": round(ms, 4), "gflops": round(flops["gram"] / (ms * 1e-3) / 1e9, 1),
                                 "diff_vs_fp32": round(rel(G, G32), 6),
                                 "path": "tcgen05 " + math_ + " products, FP32 accumulation in TMEM"}
-    ms = timed(lambda: t3f.gram_groups(X4b, w.gstart, ws4b, w.tiles4))
-    Gb, _ = t3f.gram_groups(X4b, w.gstart, ws4b, w.tiles4)
-    out["uneven_bf16_cores"] = {"ms": round(ms, 4), "gflops": round(flops["uneven"] / (ms * 1e-3) / 1e9, 1),
-                                "diff_vs_fp32": round(rel(Gb, G4_32), 6),
-                                "path": "BF16 cores, FP32 CUDA-core arithmetic (grouped work list)"}
+    for key, X_, ws_, math_, path in (
+            ("uneven_bf16_cores", X4b, ws4b, "fp32", "BF16 cores, FP32 CUDA-core arithmetic (grouped work list)"),
+            ("uneven_tf32", X4, w.ws4, "tf32", "F32 cores; tcgen05 TF32 tiles, FP32 accumulation"),
+            ("uneven_bf16_tc", X4b, ws4b, "bf16", "BF16 cores; tcgen05 BF16 tiles, FP32 accumulation")):
+        ms = timed(lambda: t3f.gram_groups(X_, w.gstart, ws_, w.tiles4, math=math_))
+        Gx, _ = t3f.gram_groups(X_, w.gstart, ws_, w.tiles4, math=math_)
+        out[key] = {"ms": round(ms, 4), "gflops": round(flops["uneven"] / (ms * 1e-3) / 1e9, 1),
+                    "diff_vs_fp32": round(rel(Gx, G4_32), 6), "path": path}
     return out
 
 

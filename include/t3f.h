@@ -283,6 +283,11 @@ typedef struct {
  * <=64}; tiles[b] (host int32[4], NULL = built-in defaults, each in 1..16) is the tile side
  * used for bucket b. The upper triangle of pairs is cut into tiles, sorted by cost and drained
  * by ONE persistent launch.
+ * math (t3f_math): FP32 = CUDA-core FP32 throughout. TF32 (F32 cores) / BF16 (F32 or BF16
+ * cores): every pair runs on the tensor cores (operands rounded to TF32 / BF16, FP32
+ * accumulation) in tiles of (128/RA) x (128/RB) pairs, RA and RB = 16, 16, 32, 64 for the
+ * buckets of the two sides, drained by one persistent launch. A tensor-core wait that runs
+ * out writes T3F_ERR_TIMEOUT into the workspace's error word (t3f_device_status).
  * t3f_gram_groups_prepare writes the work list and object tables into `ws` (host-to-device
  * copies; call it once, outside stream capture). t3f_gram_groups and
  * t3f_gram_groups_backward then only launch kernels (memsets + kernels), so they can be
@@ -295,14 +300,16 @@ t3f_status t3f_gram_groups_prepare(const t3f_tt_ragged* X, int32_t ngroups,
                                    const int32_t* gstart, const int32_t* tiles, void* ws,
                                    size_t ws_bytes, t3f_stream_t stream);
 t3f_status t3f_gram_groups(const t3f_tt_ragged* X, int32_t ngroups, const int32_t* gstart,
-                           const int32_t* tiles, float* out, double* norms, void* ws,
-                           size_t ws_bytes, t3f_stream_t stream);
+                           const int32_t* tiles, int32_t math, float* out, double* norms,
+                           void* ws, size_t ws_bytes, t3f_stream_t stream);
 
 /*
  * Adjoint of t3f_gram_groups: dcores (device float, the layout of X's cores with F32
  * elements) receives the cotangent of sum_g sum_ab dout_g[a][b] <X_a, X_b> for the
- * concatenated per-group cotangents dout (device float, like `out`). Computed per group and
- * pair of rank buckets on zero-padded uniform batches; requires the same prepared `ws`.
+ * concatenated per-group cotangents dout (device float, like `out`). FP32 CUDA-core
+ * arithmetic: one persistent launch of the tiled adjoint over a second work list (tiles sized
+ * per bucket so that the adjoint's seven partial tiles fit one CTA); every off-diagonal tile
+ * uses the symmetrised cotangent dout[a][b] + dout[b][a]. Requires the same prepared `ws`.
  */
 t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t ngroups,
                                     const int32_t* gstart, const int32_t* tiles,

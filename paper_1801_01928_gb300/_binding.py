@@ -335,7 +335,8 @@ _I32P = ctypes.POINTER(ctypes.c_int32)
 _SIGS.update({
     "t3f_gram_groups_workspace_size": (ctypes.c_size_t, [_RP, ctypes.c_int32, _I32P, _I32P]),
     "t3f_gram_groups_prepare": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, _VP, _SZ, _VP]),
-    "t3f_gram_groups": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, _VP, _VP, _VP, _SZ, _VP]),
+    "t3f_gram_groups": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, ctypes.c_int32, _VP, _VP, _VP, _SZ,
+                                         _VP]),
     "t3f_gram_groups_backward": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, _VP, _VP, _VP, _SZ, _VP]),
 })
 EXPORTS = tuple(_SIGS)
@@ -408,14 +409,17 @@ def gram_groups_prepare(X: RaggedTT, gstart, tiles=None) -> torch.Tensor:
     return ws
 
 
-def gram_groups(X: RaggedTT, gstart, ws: torch.Tensor, tiles=None, want_norms=True, out=None, norms=None):
-    """Concatenated per-group Gram matrices (and FP64 norms) from a prepared workspace."""
+def gram_groups(X: RaggedTT, gstart, ws: torch.Tensor, tiles=None, want_norms=True, out=None, norms=None,
+                math: str = "fp32"):
+    """Concatenated per-group Gram matrices (and FP64 norms) from a prepared workspace;
+    math "tf32" / "bf16" puts the pairs of rank > 8 objects on the tensor cores."""
     dev = X.data.device
     total = sum((gstart[g + 1] - gstart[g]) ** 2 for g in range(len(gstart) - 1))
     out = torch.empty(total, dtype=torch.float32, device=dev) if out is None else out
     if want_norms and norms is None:
         norms = torch.empty(X.count, dtype=torch.float64, device=dev)
-    _check(_lib().t3f_gram_groups(ctypes.byref(X.desc()), len(gstart) - 1, _i32(gstart), _tiles_arg(tiles), _ptr(out),
+    _check(_lib().t3f_gram_groups(ctypes.byref(X.desc()), len(gstart) - 1, _i32(gstart), _tiles_arg(tiles),
+                                  MATH[math], _ptr(out),
                                   _ptr(norms) if want_norms else None, _ptr(ws), ws.numel(), _stream(dev)),
            "t3f_gram_groups")
     return out, (norms if want_norms else None)

@@ -33,9 +33,15 @@ t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, co
                                       float* dX, float* scratch, long long scratch_stride, size_t smem, int grid,
                                       cudaStream_t s);
 
+t3f_status launch_gram_mma_list(int math, const void* cores, int dtype, int dmax, const long long* off,
+                                const int* rk, const int* nmodes, const int* items, int nitems, int* head,
+                                const int* gstart, const int* gd, float* gout, const long long* gout_off,
+                                const int* perm, int* err, cudaStream_t s);
+
 namespace {
 
 constexpr int kBuckets = 4;
+constexpr int kMmaR[kBuckets] = {16, 16, 32, 64};  // tensor-core padded rank of each bucket
 const int kBucketMax[kBuckets] = {8, 16, 32, 64};
 const int kDefaultTiles[kBuckets] = {10, 6, 3, 1};
 
@@ -57,7 +63,9 @@ struct Plan {
   int count = 0, ngroups = 0, dmax = 0, nitems = 0;
   std::vector<int> sorted;   // sorted position -> object
   std::vector<int> perm;     // sorted position -> local index within the group
-  std::vector<int> items;    // 8 ints per item (forward tiles)
+  std::vector<int> items;    // 8 ints per item (forward tiles, all bucket pairs)
+  std::vector<int> mitems;   // tensor-core tiles (every bucket pair)
+  int nmitems = 0;
   std::vector<int> bitems;   // 8 ints per item (adjoint tiles)
   int nbitems = 0;
   size_t bsmem = 0;
@@ -72,7 +80,7 @@ struct Plan {
   std::vector<Range> br;     // [group][bucket]
   size_t smem = 0;
   // workspace layout (bytes)
-  size_t o_items, o_bitems, o_off, o_rk, o_nm, o_gs, o_gd, o_go, o_perm, o_scr, total;
+  size_t o_items, o_mitems, o_bitems, o_off, o_rk, o_nm, o_gs, o_gd, o_go, o_perm, o_scr, total;
 };
 
 int bucket_of(int r) {
@@ -234,6 +242,50 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
   long long pmax = 0;
   T3F_CHECK(make_items(tl, false, &P->items, &smem, &pmax));
   P->nitems = (int)(P->items.size() / 8);
+  // tensor-core tiles for every bucket pair p <= q: the a side pads to RA = 16 / 16 / 32 / 64
+  // (bucket p), the b side to RB (bucket q); (128 / RA) x (128 / RB) pairs per tile
+  {
+    struct It {
+      double cost;
+      int v[8];
+    };
+    std::vector<It> its;
+    for (int g = 0; g < ngroups; ++g) {
+      double slices = 0;
+      for (int k = 0; k < P->gd[g]; ++k) slices += P->nmodes[(size_t)g * dmax + k];
+      for (int p = 0; p < kBuckets; ++p)
+        for (int q = p; q < kBuckets; ++q) {
+          const Range& A = P->br[(size_t)g * kBuckets + p];
+          const Range& B = P->br[(size_t)g * kBuckets + q];
+          if (A.end == A.begin || B.end == B.begin) continue;
+          const int RA = kMmaR[p], RB = kMmaR[q], TA = 128 / RA, TB = 128 / RB;
+          for (int a0 = A.begin; a0 < A.end; a0 += TA) {
+            const int na = std::min(TA, A.end - a0);
+            // same bucket: b tiles start at the a tile's first object so the pairs below the
+            // diagonal are covered once through the symmetric write
+            for (int b0 = (p == q ? a0 : B.begin); b0 < B.end; b0 += TB) {
+              const int nb = std::min(TB, B.end - b0);
+              It it;
+              it.cost = 128.0 * 128.0 * (RA + RB) * slices;
+              it.v[0] = g;
+              it.v[1] = a0;
+              it.v[2] = na;
+              it.v[3] = b0;
+              it.v[4] = nb;
+              it.v[5] = RA;
+              it.v[6] = (p == q && a0 == b0) ? 0 : 1;
+              it.v[7] = RB;
+              its.push_back(it);
+            }
+          }
+        }
+    }
+    std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+    P->mitems.resize(its.size() * 8);
+    for (size_t w = 0; w < its.size(); ++w)
+      for (int x = 0; x < 8; ++x) P->mitems[w * 8 + x] = its[w].v[x];
+    P->nmitems = (int)its.size();
+  }
   // adjoint tiles: the adjoint holds seven partial tiles per pair, so its side is the largest
   // one (at most the forward side) whose buffers fit a CTA at the bucket's largest rank;
   // that keeps most of the 512 threads busy with a 4 x 4 block each
@@ -255,6 +307,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
   P->smem = smem;
   size_t o = kWsHeader;
   P->o_items = o; o += a256(sizeof(int) * P->items.size());
+  P->o_mitems = o; o += a256(sizeof(int) * P->mitems.size());
   P->o_bitems = o; o += a256(sizeof(int) * P->bitems.size());
   P->o_off = o; o += a256(sizeof(long long) * P->objoff.size());
   P->o_rk = o; o += a256(sizeof(int) * P->objrk.size());
@@ -289,6 +342,7 @@ t3f_status gg_tables_upload(const Plan& P, char* w, cudaStream_t s) {
     const void* src;
     size_t bytes;
   } cps[] = {{P.o_items, P.items.data(), sizeof(int) * P.items.size()},
+             {P.o_mitems, P.mitems.data(), sizeof(int) * P.mitems.size()},
              {P.o_bitems, P.bitems.data(), sizeof(int) * P.bitems.size()},
              {P.o_off, P.objoff.data(), sizeof(long long) * P.objoff.size()},
              {P.o_rk, P.objrk.data(), sizeof(int) * P.objrk.size()},
@@ -323,22 +377,36 @@ extern "C" t3f_status t3f_gram_groups_prepare(const t3f_tt_ragged* X, int32_t ng
 }
 
 extern "C" t3f_status t3f_gram_groups(const t3f_tt_ragged* X, int32_t ngroups, const int32_t* gstart,
-                                      const int32_t* tiles, float* out, double* norms, void* ws, size_t ws_bytes,
-                                      t3f_stream_t stream) {
+                                      const int32_t* tiles, int32_t math, float* out, double* norms, void* ws,
+                                      size_t ws_bytes, t3f_stream_t stream) {
   Plan P;
   T3F_CHECK(build_plan(X, ngroups, gstart, tiles, &P));
   T3F_CHECK(check_ws(ws, ws_bytes, P.total));
   if (!out) return T3F_ERR_ARG;
+  if (math != T3F_MATH_FP32 && math != T3F_MATH_TF32 && math != T3F_MATH_BF16) return T3F_ERR_ARG;
+  if (math == T3F_MATH_TF32 && X->dtype != T3F_F32) return T3F_ERR_DTYPE;
   cudaStream_t s = (cudaStream_t)stream;
   char* w = static_cast<char*>(ws);
-  int* head = reinterpret_cast<int*>(w + sizeof(int));  // second word of the header
-  if (cudaMemsetAsync(w, 0, 2 * sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
-  T3F_CHECK(launch_gram_tile_table(X->cores, X->dtype, P.dmax, reinterpret_cast<const long long*>(w + P.o_off),
-                                   reinterpret_cast<const int*>(w + P.o_rk), reinterpret_cast<const int*>(w + P.o_nm),
-                                   reinterpret_cast<const int*>(w + P.o_items), P.nitems, head,
-                                   reinterpret_cast<const int*>(w + P.o_gs), reinterpret_cast<const int*>(w + P.o_gd),
-                                   out, reinterpret_cast<const long long*>(w + P.o_go),
-                                   reinterpret_cast<const int*>(w + P.o_perm), P.smem, s));
+  // header words: 0 error, 1 CUDA-core list head, 3 tensor-core list head
+  int* hw = reinterpret_cast<int*>(w);
+  if (cudaMemsetAsync(w, 0, 8 * sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
+  const long long* off = reinterpret_cast<const long long*>(w + P.o_off);
+  const int* rk = reinterpret_cast<const int*>(w + P.o_rk);
+  const int* nm = reinterpret_cast<const int*>(w + P.o_nm);
+  const int* gsd = reinterpret_cast<const int*>(w + P.o_gs);
+  const int* gdd = reinterpret_cast<const int*>(w + P.o_gd);
+  const long long* god = reinterpret_cast<const long long*>(w + P.o_go);
+  const int* pd = reinterpret_cast<const int*>(w + P.o_perm);
+  if (math == T3F_MATH_FP32) {
+    T3F_CHECK(launch_gram_tile_table(X->cores, X->dtype, P.dmax, off, rk, nm,
+                                     reinterpret_cast<const int*>(w + P.o_items), P.nitems, hw + 1, gsd, gdd, out,
+                                     god, pd, P.smem, s));
+  } else {
+    if (P.nmitems > 0)
+      T3F_CHECK(launch_gram_mma_list(math, X->cores, X->dtype, P.dmax, off, rk, nm,
+                                     reinterpret_cast<const int*>(w + P.o_mitems), P.nmitems, hw + 3, gsd, gdd, out,
+                                     god, pd, hw, s));
+  }
   if (norms) {
     k_group_norms<<<(P.count + 255) / 256, 256, 0, s>>>(out, reinterpret_cast<const long long*>(w + P.o_go),
                                                          reinterpret_cast<const int*>(w + P.o_gs), ngroups, norms);

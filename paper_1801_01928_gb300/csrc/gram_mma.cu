@@ -1,11 +1,11 @@
 // Tensor-core Gram sweep (paper Section 4 'gram'; batches of Section 3.1) with TF32 or BF16
 // operands and FP32 accumulation in tensor memory (tcgen05).
 //
-// A CTA owns a tile of TA x TB pairs (a, b) with TA = TB = 128 / R, R the ranks of both sides
-// zero-padded to 16, 32 or 64. Per mode slice i of core k the left-partial update
-// M'_ab = sum_i A_a,i^T M_ab B_b,i is two tensor-core products with M = 128 rows:
-//   MMA1 (one per b)  T[(a,al), bp]   = sum_be M_b[(a,al), be] B_b,i[be, bp]   TMEM columns b*R + bp
-//   MMA2 (one per a)  D_a[(b,bp), ap] += sum_al T_a[(b,bp), al] A_a,i[al, ap]  TMEM columns 128 + a*R + ap
+// A CTA owns a tile of TA x TB pairs (a, b) with TA = 128 / RA and TB = 128 / RB, RA and RB the
+// ranks of the two sides zero-padded to 16, 32 or 64. Per mode slice i of core k the
+// left-partial update M'_ab = sum_i A_a,i^T M_ab B_b,i is two tensor-core products with M = 128:
+//   MMA1 (one per b)  T[(a,al), bp]   = sum_be M_b[(a,al), be] B_b,i[be, bp]   TMEM columns b*RB + bp
+//   MMA2 (one per a)  D_a[(b,bp), ap] += sum_al T_a[(b,bp), al] A_a,i[al, ap]  TMEM columns 128 + a*RA + ap
 // T goes TMEM -> registers -> shared memory (rounded to the operand type) between the two
 // products; D accumulates the n_k slices of core k in FP32 and becomes the next core's M the
 // same way. The final M_d (1 x 1 per pair) is <A_a, B_b>.
@@ -15,6 +15,9 @@
 // writes of the epilogues fall on distinct banks) and SBO = (K / elements-per-16-bytes) * 144
 // bytes apart along M/N. Padded rows and columns hold exact zeros, so padding never changes a
 // result.
+#include <algorithm>
+#include <string.h>
+
 #include "t3f_internal.cuh"
 
 namespace t3f {
@@ -26,14 +29,57 @@ constexpr int kMmaThreads = 256;
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kSkew = 64;  // extra bytes between consecutive operands (16-bank shift)
 
-// Slice operands are double-buffered unless that would not fit (TF32 at R = 64).
-__host__ __device__ constexpr int slice_buffers(int kind, int R) { return (kind == 0 && R == 64) ? 1 : 2; }
+constexpr uint32_t kSmemCap = 227u * 1024u;
+
+// Shared-memory plan of a tile shape (RA, RB) for element size es: operand strides, region
+// offsets, and whether the slice operands fit twice (double buffering).
+struct MmaLayout {
+  uint32_t sbo_a, sbo_b, big_a, big_b, sl_a, sl_b;  // SBO and operand strides (bytes)
+  uint32_t o_as, o_mop, o_top, total;
+  int nbuf;
+};
+
+__host__ __device__ constexpr MmaLayout mma_layout(int es, int RA, int RB) {
+  MmaLayout L{};
+  const uint32_t T = 16u / (uint32_t)es;
+  L.sbo_a = (uint32_t)RA / T * kLBO;
+  L.sbo_b = (uint32_t)RB / T * kLBO;
+  L.big_a = 16u * L.sbo_a + kSkew;               // T_a: 128 rows, K = RA
+  L.big_b = 16u * L.sbo_b + kSkew;               // M_b: 128 rows, K = RB
+  L.sl_a = (uint32_t)RA / 8u * L.sbo_a + kSkew;  // A_a,i: RA rows, K = RA
+  L.sl_b = (uint32_t)RB / 8u * L.sbo_b + kSkew;  // B_b,i: RB rows, K = RB
+  const uint32_t TA = 128u / (uint32_t)RA, TB = 128u / (uint32_t)RB;
+  const uint32_t slices = TB * L.sl_b + TA * L.sl_a, bigs = TB * L.big_b + TA * L.big_a;
+  L.nbuf = 2u * slices + bigs <= kSmemCap ? 2 : 1;
+  // regions: B slices [nbuf][TB], A slices [nbuf][TA], M_b [TB], T_a [TA]
+  L.o_as = (uint32_t)L.nbuf * TB * L.sl_b;
+  L.o_mop = L.o_as + (uint32_t)L.nbuf * TA * L.sl_a;
+  L.o_top = L.o_mop + TB * L.big_b;
+  L.total = L.o_top + TA * L.big_a;
+  return L;
+}
 
 struct GramMmaArgs {
-  TTV A, B;
-  float* out;      // [bA][bB]
-  int* err;        // device error word (nullable)
+  TTV A, B;                   // uniform mode: the two batches (A the side of the smaller rank)
+  float* out;                 // uniform mode: out[a * ldo + b], or out[b * ldo + a] if swap
+  int ldo, swap;
+  int* err;                   // device error word (nullable)
   uint32_t smem_bytes;
+  int mode;                   // 0: tile from blockIdx (uniform), 1: persistent work list (groups)
+  // work-list mode: ragged objects in rank-sorted positions
+  const void* cores;
+  const long long* off;       // [pos][dmax] element offset of core k
+  const int* rk;              // [pos][dmax + 1] ranks
+  int dmax;
+  const int* nmodes;          // [group][dmax]
+  const int* gd;              // [group] d
+  const int* gstart;          // [group + 1]
+  const int* perm;            // [pos] index of the object within its group
+  const long long* gout_off;  // [group] offset of the group's S x S matrix in gout
+  float* gout;
+  const int* items;           // [item][8]: group, a0, na, b0, nb, RA, sym, RB
+  int nitems;
+  int* head;                  // work-list counter
 };
 
 template <int KIND>
@@ -158,47 +204,252 @@ __device__ __forceinline__ float ldc(const void* p, long long i) {
   return ldf<ST>(static_cast<const ST*>(p), i);
 }
 
-template <int KIND, int R, typename ST>
-__global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant__ GramMmaArgs g) {
+// Everything a CTA keeps across the tiles it processes.
+struct MmaState {
+  uint32_t tmem, bar1, bar2, ph1, ph2;
+  bool pending1, pending2;  // a committed product batch not yet waited for
+  int bad;                  // this thread saw a wait run out
+  long long* s_base;        // [2 core parities][2 sides][8 objects]
+  int* s_r0;
+  int* s_r1;
+};
+
+// One tile: na x nb pairs (a0.., b0..) of one group (or of the uniform batches), d cores.
+// Returns false (block-uniformly) when a tensor-core wait ran out.
+template <int KIND, int RA, int RB, typename ST>
+__device__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, int a0, int na, int b0, int nb,
+                         int sym, int d) {
   using O = OpT<KIND>;
   constexpr int ES = O::ES;
-  constexpr int T = 16 / ES;                                   // elements per 16 bytes
-  constexpr int TL = 128 / R;                                  // objects per tile side
-  constexpr int NBUF = slice_buffers(KIND, R);                 // slice double buffering
-  constexpr uint32_t SBO = (uint32_t)(R / T) * kLBO;          // every operand has K = R
-  constexpr uint32_t SZ_BIG = 16u * SBO + kSkew;               // stride of 128 x R operands (M_b, T_a)
-  constexpr uint32_t SZ_SL = (uint32_t)(R / 8) * SBO + kSkew;  // stride of R x R operands (slices)
-  constexpr uint32_t ID = idesc(O::FMT, R);
-  constexpr int KG = R / T;                                    // K groups of T elements
-  constexpr int UPT = TL * R * KG / kMmaThreads;               // staged K runs per thread and side
-  constexpr int USTEP = kMmaThreads / R;
-  static_assert(UPT * kMmaThreads == TL * R * KG && kMmaThreads % R == 0, "slice staging must divide evenly");
-
-  extern __shared__ __align__(128) char sm[];
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ uint32_t s_tmem;
+  constexpr int T = 16 / ES;
+  constexpr int TA = 128 / RA, TB = 128 / RB;
+  constexpr MmaLayout L = mma_layout(ES, RA, RB);
+  constexpr int NBUF = L.nbuf;
+  constexpr uint32_t SBOA = L.sbo_a, SBOB = L.sbo_b, BIGA = L.big_a, BIGB = L.big_b, SLA = L.sl_a, SLB = L.sl_b;
+  constexpr uint32_t ID1 = idesc(O::FMT, RB), ID2 = idesc(O::FMT, RA);
+  constexpr int KGA = RA / T, KGB = RB / T;                        // K groups of T elements
+  constexpr int UPA = TA * RA * KGA / kMmaThreads, UPB = TB * RB * KGB / kMmaThreads;
+  constexpr int USA = kMmaThreads / RA, USB = kMmaThreads / RB;
+  static_assert(UPA * kMmaThreads == TA * RA * KGA && UPB * kMmaThreads == TB * RB * KGB, "staging split");
+  static_assert(L.total <= kSmemCap, "tile does not fit");
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ntb = (g.B.batch + TL - 1) / TL;
-  const int a0 = (blockIdx.x / ntb) * TL, b0 = (blockIdx.x % ntb) * TL;
-  const int na = min(TL, g.A.batch - a0), nb = min(TL, g.B.batch - b0);
-  // regions: B slices [NBUF][TL], A slices [NBUF][TL], M_b [TL], T_a [TL]
   char* const bsl = sm;
-  char* const asl = sm + NBUF * TL * SZ_SL;
-  char* const mop = sm + 2 * NBUF * TL * SZ_SL;
-  char* const top = mop + TL * SZ_BIG;
+  char* const asl = sm + L.o_as;
+  char* const mop = sm + L.o_mop;
+  char* const top = sm + L.o_top;
+  const void* const Ap = g.mode == 0 ? g.A.p : g.cores;
+  const void* const Bp = g.mode == 0 ? g.B.p : g.cores;
+  const int q = warp & 3, h = warp >> 2;   // TMEM lane quarter, column half
+  const int row = q * 32 + lane;           // TMEM lane = operand row of this thread
+  const int srA = tid % RA, suA = tid / RA, srB = tid % RB, suB = tid / RB;
+  long long(*s_base)[2][8] = reinterpret_cast<long long(*)[2][8]>(st.s_base);
+  int(*s_r0)[2][8] = reinterpret_cast<int(*)[2][8]>(st.s_r0);
+  int(*s_r1)[2][8] = reinterpret_cast<int(*)[2][8]>(st.s_r1);
 
-  for (uint32_t e = (uint32_t)tid * 16u; e < g.smem_bytes; e += kMmaThreads * 16u)
-    *reinterpret_cast<uint4*>(sm + e) = make_uint4(0u, 0u, 0u, 0u);
+  auto nmode = [&](int k) { return g.mode == 0 ? g.A.n[k] : g.nmodes[grp * g.dmax + k]; };
+  // per-object core offsets and ranks of core k into parity slot par (missing objects: rank 0)
+  auto fill_info = [&](int k, int par) {
+    if (tid < 16) {
+      const int side = tid / 8, o = tid % 8, cnt = side ? nb : na, o0 = side ? b0 : a0;
+      long long base = 0;
+      int r0 = 0, r1 = 0;
+      if (o < cnt) {
+        if (g.mode == 0) {
+          const TTV& V = side ? g.B : g.A;
+          base = V.off[k] + (long long)(o0 + o) * V.osz[k];
+          r0 = V.r[k];
+          r1 = V.r[k + 1];
+        } else {
+          const int pos = o0 + o;
+          base = g.off[(long long)pos * g.dmax + k];
+          r0 = g.rk[(long long)pos * (g.dmax + 1) + k];
+          r1 = g.rk[(long long)pos * (g.dmax + 1) + k + 1];
+        }
+      }
+      s_base[par][side][o] = base;
+      s_r0[par][side][o] = r0;
+      s_r1[par][side][o] = r1;
+    }
+  };
+  // M_0 = 1 for every pair: zero all M_b, then element (row a*RA, col 0) of every M_b
+  for (uint32_t e = (uint32_t)tid * 16u; e < TB * BIGB; e += kMmaThreads * 16u)
+    *reinterpret_cast<uint4*>(mop + e) = make_uint4(0u, 0u, 0u, 0u);
+  fill_info(0, 0);
   __syncthreads();
-  // M_0 = 1 for every pair: element (row a*R, col 0) of every M_b
-  if (tid < TL * TL) O::st(mop + (tid / TL) * SZ_BIG + eoff<ES>((tid % TL) * R, 0, SBO), 1.0f);
+  if (tid < TA * TB) O::st(mop + (tid / TA) * BIGB + eoff<ES>((tid % TA) * RA, 0, SBOB), 1.0f);
+
+  // slice i of core k of both sides -> registers. K run j of this thread on side X covers
+  // object o = (suX + j*USX) / KGX, columns c = ((suX + j*USX) % KGX) * T + t, row srX
+  float pb[UPB][T], pa[UPA][T];
+  auto load_slice = [&](int k, int i) {
+    const int par = k & 1, n = nmode(k);
+#pragma unroll
+    for (int j = 0; j < UPB; ++j) {
+      const int w = suB + j * USB, o = w / KGB, c0 = (w % KGB) * T;
+      const int r0 = s_r0[par][1][o], r1 = s_r1[par][1][o];
+      const long long b = s_base[par][1][o] + (long long)i * r1 + srB, stp = (long long)n * r1;
+#pragma unroll
+      for (int t = 0; t < T; ++t) pb[j][t] = (c0 + t < r0 && srB < r1) ? ldc<ST>(Bp, b + (c0 + t) * stp) : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < UPA; ++j) {
+      const int w = suA + j * USA, o = w / KGA, c0 = (w % KGA) * T;
+      const int r0 = s_r0[par][0][o], r1 = s_r1[par][0][o];
+      const long long b = s_base[par][0][o] + (long long)i * r1 + srA, stp = (long long)n * r1;
+#pragma unroll
+      for (int t = 0; t < T; ++t) pa[j][t] = (c0 + t < r0 && srA < r1) ? ldc<ST>(Ap, b + (c0 + t) * stp) : 0.0f;
+    }
+  };
+  // registers -> slice buffer s: one 16-byte store per K run (a whole core-matrix row)
+  auto store_slice = [&](int s) {
+#pragma unroll
+    for (int j = 0; j < UPB; ++j) {
+      const int w = suB + j * USB, o = w / KGB, cg = w % KGB;
+      const uint32_t off = (uint32_t)(srB >> 3) * SBOB + (uint32_t)cg * kLBO + (uint32_t)(srB & 7) * 16u;
+      *reinterpret_cast<uint4*>(bsl + (s * TB + o) * SLB + off) = O::pack(pb[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < UPA; ++j) {
+      const int w = suA + j * USA, o = w / KGA, cg = w % KGA;
+      const uint32_t off = (uint32_t)(srA >> 3) * SBOA + (uint32_t)cg * kLBO + (uint32_t)(srA & 7) * 16u;
+      *reinterpret_cast<uint4*>(asl + (s * TA + o) * SLA + off) = O::pack(pa[j]);
+    }
+  };
+
+  int iter = 0;
+  load_slice(0, 0);
+  for (int k = 0; k < d; ++k) {
+    const int n = nmode(k);
+    if (k + 1 < d) fill_info(k + 1, (k + 1) & 1);  // read after the next block barrier
+    for (int i = 0; i < n; ++i, ++iter) {
+      const int s = NBUF == 2 ? (iter & 1) : 0;
+      if (NBUF == 1 && st.pending2) {  // the single slice buffer is still read by MMA2
+        st.bad |= !mbar_wait(st.bar2, st.ph2);
+        st.ph2 ^= 1u;
+        st.pending2 = false;
+      }
+      store_slice(s);
+      async_fence();
+      tc_before();
+      if (__syncthreads_or(st.bad)) return false;
+      // ---- MMA1: T for every b (TMEM columns b*RB .. b*RB + RB - 1)
+      if (tid == 0) {
+        tc_after();
+#pragma unroll 1
+        for (int b = 0; b < TB; ++b) {
+          const uint32_t am = su32(mop + b * BIGB), bm = su32(bsl + (s * TB + b) * SLB);
+#pragma unroll
+          for (int kk = 0; kk < RB / O::KI; ++kk)
+            mma<KIND>(st.tmem + (uint32_t)(b * RB), sdesc(am + kk * 2 * kLBO, SBOB), sdesc(bm + kk * 2 * kLBO, SBOB),
+                      ID1, kk > 0);
+        }
+        mma_commit(st.bar1);
+      }
+      st.pending1 = true;
+      // ---- prefetch the next slice while the products run
+      {
+        int k2 = k, i2 = i + 1;
+        if (i2 == n) { ++k2; i2 = 0; }
+        if (k2 < d) load_slice(k2, i2);
+      }
+      st.bad |= !mbar_wait(st.bar1, st.ph1);
+      st.ph1 ^= 1u;
+      st.pending1 = false;
+      if (st.pending2) {  // T_a is still read by the previous MMA2
+        st.bad |= !mbar_wait(st.bar2, st.ph2);
+        st.ph2 ^= 1u;
+        st.pending2 = false;
+      }
+      tc_after();
+      // ---- epilogue 1: T (rows (a, al), cols (b, bp)) -> T_a[(b, bp), al]
+      {
+        const int a = row / RA, al = row % RA;
+        char* dst = top + a * BIGA;
+#pragma unroll
+        for (int cc = 0; cc < 64; cc += 16) {
+          const int c0 = h * 64 + cc;
+          float v[16];
+          tmem_ld16(st.tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) O::st(dst + eoff<ES>(c0 + j, al, SBOA), v[j]);
+        }
+      }
+      async_fence();
+      tc_before();
+      if (__syncthreads_or(st.bad)) return false;
+      // ---- MMA2: D_a += T_a A_a,i for every a (TMEM columns 128 + a*RA ..)
+      if (tid == 0) {
+        tc_after();
+#pragma unroll 1
+        for (int a = 0; a < TA; ++a) {
+          const uint32_t am = su32(top + a * BIGA), bm = su32(asl + (s * TA + a) * SLA);
+#pragma unroll
+          for (int kk = 0; kk < RA / O::KI; ++kk)
+            mma<KIND>(st.tmem + 128u + (uint32_t)(a * RA), sdesc(am + kk * 2 * kLBO, SBOA),
+                      sdesc(bm + kk * 2 * kLBO, SBOA), ID2, (i > 0 || kk > 0) ? 1u : 0u);
+        }
+        mma_commit(st.bar2);
+      }
+      st.pending2 = true;
+    }
+    st.bad |= !mbar_wait(st.bar2, st.ph2);
+    st.ph2 ^= 1u;
+    st.pending2 = false;
+    tc_after();
+    // ---- epilogue 2: D (rows (b, bp), cols (a, ap)) -> M_b[(a, ap), bp], or the Gram entries
+    {
+      const int b = row / RB, bp = row % RB;
+#pragma unroll
+      for (int cc = 0; cc < 64; cc += 16) {
+        const int c0 = h * 64 + cc;
+        float v[16];
+        tmem_ld16(st.tmem + ((uint32_t)(q * 32) << 16) + 128u + (uint32_t)c0, v);
+        if (k + 1 < d) {
+          char* dst = mop + b * BIGB;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) O::st(dst + eoff<ES>(c0 + j, bp, SBOB), v[j]);
+        } else if (bp == 0 && b < nb) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = c0 + j, a = col / RA;
+            if (col % RA != 0 || a >= na) continue;
+            if (g.mode == 0) {
+              if (g.swap)
+                g.out[(long long)(b0 + b) * g.ldo + (a0 + a)] = v[j];
+              else
+                g.out[(long long)(a0 + a) * g.ldo + (b0 + b)] = v[j];
+            } else {
+              const long long S = g.gstart[grp + 1] - g.gstart[grp];
+              const int la = g.perm[a0 + a], lb = g.perm[b0 + b];
+              float* o = g.gout + g.gout_off[grp];
+              o[la * S + lb] = v[j];
+              if (sym) o[lb * S + la] = v[j];
+            }
+          }
+        }
+      }
+    }
+    async_fence();
+    tc_before();
+    if (__syncthreads_or(st.bad)) return false;
+    tc_after();
+  }
+  return true;
+}
+
+// Common prologue / epilogue of the kernels: TMEM allocation, barriers, and the release of
+// the tensor memory after a bounded wait for anything still in flight.
+__device__ __forceinline__ void mma_setup(MmaState& st, uint64_t* bars, uint32_t* s_tmem, char* sm, uint32_t bytes) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (uint32_t e = (uint32_t)tid * 16u; e < bytes; e += kMmaThreads * 16u)
+    *reinterpret_cast<uint4*>(sm + e) = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s_bar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&s_bar[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[1])));
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -206,190 +457,105 @@ __global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant_
   tc_before();
   __syncthreads();
   tc_after();
-  const uint32_t tmem = s_tmem;
-  const uint32_t bar1 = su32(&s_bar[0]), bar2 = su32(&s_bar[1]);
-  uint32_t ph1 = 0, ph2 = 0;
-  bool pending2 = false;   // an MMA2 batch has been committed and not yet waited for
-  int bad = 0;             // this thread saw a wait run out
-  bool failed = false;     // block-uniform
+  st.tmem = *s_tmem;
+  st.bar1 = su32(&bars[0]);
+  st.bar2 = su32(&bars[1]);
+  st.ph1 = st.ph2 = 0;
+  st.pending1 = st.pending2 = false;
+  st.bad = 0;
+}
 
-  const int q = warp & 3, h = warp >> 2;       // TMEM lane quarter, column half
-  const int row = q * 32 + lane;               // TMEM lane = operand row of this thread
-  const int sr = tid % R, su = tid / R;        // staging: operand row, first K-run index
-  const int d = g.A.d;
-
-  // slice i of core k of both sides -> registers: K run j of this thread covers object
-  // o = (su + j*USTEP) / KG, columns c = ((su + j*USTEP) % KG) * T + t, row sr
-  float pb[UPT][T], pa[UPT][T];
-  auto load_slice = [&](int k, int i) {
-    const int rA0 = g.A.r[k], rA1 = g.A.r[k + 1], rB0 = g.B.r[k], rB1 = g.B.r[k + 1], n = g.A.n[k];
-    const long long bA = g.A.off[k] + (long long)a0 * g.A.osz[k] + (long long)i * rA1 + sr;
-    const long long bB = g.B.off[k] + (long long)b0 * g.B.osz[k] + (long long)i * rB1 + sr;
-    const long long sA = (long long)n * rA1, sB = (long long)n * rB1;
-#pragma unroll
-    for (int j = 0; j < UPT; ++j) {
-      const int w = su + j * USTEP, o = w / KG, c0 = (w % KG) * T;
-#pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const int c = c0 + t;
-        pb[j][t] = (o < nb && c < rB0 && sr < rB1) ? ldc<ST>(g.B.p, bB + o * g.B.osz[k] + c * sB) : 0.0f;
-        pa[j][t] = (o < na && c < rA0 && sr < rA1) ? ldc<ST>(g.A.p, bA + o * g.A.osz[k] + c * sA) : 0.0f;
-      }
-    }
-  };
-  // registers -> slice buffer s: one 16-byte store per K run (a whole core-matrix row)
-  auto store_slice = [&](int s) {
-#pragma unroll
-    for (int j = 0; j < UPT; ++j) {
-      const int w = su + j * USTEP, o = w / KG, cg = w % KG;
-      const uint32_t off = (uint32_t)(sr >> 3) * SBO + (uint32_t)cg * kLBO + (uint32_t)(sr & 7) * 16u;
-      *reinterpret_cast<uint4*>(bsl + (s * TL + o) * SZ_SL + off) = O::pack(pb[j]);
-      *reinterpret_cast<uint4*>(asl + (s * TL + o) * SZ_SL + off) = O::pack(pa[j]);
-    }
-  };
-
-  int iter = 0;
-  load_slice(0, 0);
-  for (int k = 0; k < d && !failed; ++k) {
-    const int n = g.A.n[k];
-    for (int i = 0; i < n; ++i, ++iter) {
-      const int s = NBUF == 2 ? (iter & 1) : 0;
-      if (NBUF == 1 && pending2) {  // the single slice buffer is still read by MMA2
-        bad |= !mbar_wait(bar2, ph2);
-        ph2 ^= 1u;
-        pending2 = false;
-      }
-      store_slice(s);
-      async_fence();
-      tc_before();
-      if (__syncthreads_or(bad)) { failed = true; break; }
-      // ---- MMA1: T for every b (TMEM columns b*R .. b*R + R - 1)
-      if (tid == 0) {
-        tc_after();
-#pragma unroll 1
-        for (int b = 0; b < TL; ++b) {
-          const uint32_t am = su32(mop + b * SZ_BIG), bm = su32(bsl + (s * TL + b) * SZ_SL);
-#pragma unroll
-          for (int kk = 0; kk < R / O::KI; ++kk)
-            mma<KIND>(tmem + (uint32_t)(b * R), sdesc(am + kk * 2 * kLBO, SBO), sdesc(bm + kk * 2 * kLBO, SBO), ID,
-                      kk > 0);
-        }
-        mma_commit(bar1);
-      }
-      // ---- prefetch the next slice while the products run
-      {
-        int k2 = k, i2 = i + 1;
-        if (i2 == n) { ++k2; i2 = 0; }
-        if (k2 < d) load_slice(k2, i2);
-      }
-      bad |= !mbar_wait(bar1, ph1);
-      ph1 ^= 1u;
-      if (pending2) {  // T_a is still read by the previous MMA2
-        bad |= !mbar_wait(bar2, ph2);
-        ph2 ^= 1u;
-        pending2 = false;
-      }
-      tc_after();
-      // ---- epilogue 1: T (rows (a, al), cols (b, bp)) -> T_a[(b, bp), al]
-      {
-        const int a = row / R, al = row % R;
-        char* dst = top + a * SZ_BIG;
-#pragma unroll
-        for (int cc = 0; cc < 64; cc += 16) {
-          const int c0 = h * 64 + cc;
-          float v[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) O::st(dst + eoff<ES>(c0 + j, al, SBO), v[j]);
-        }
-      }
-      async_fence();
-      tc_before();
-      if (__syncthreads_or(bad)) { failed = true; break; }
-      // ---- MMA2: D_a += T_a A_a,i for every a (TMEM columns 128 + a*R ..)
-      if (tid == 0) {
-        tc_after();
-#pragma unroll 1
-        for (int a = 0; a < TL; ++a) {
-          const uint32_t am = su32(top + a * SZ_BIG), bm = su32(asl + (s * TL + a) * SZ_SL);
-#pragma unroll
-          for (int kk = 0; kk < R / O::KI; ++kk)
-            mma<KIND>(tmem + 128u + (uint32_t)(a * R), sdesc(am + kk * 2 * kLBO, SBO),
-                      sdesc(bm + kk * 2 * kLBO, SBO), ID, (i > 0 || kk > 0) ? 1u : 0u);
-        }
-        mma_commit(bar2);
-      }
-      pending2 = true;
-    }
-    if (failed) break;
-    bad |= !mbar_wait(bar2, ph2);
-    ph2 ^= 1u;
-    pending2 = false;
-    tc_after();
-    // ---- epilogue 2: D (rows (b, bp), cols (a, ap)) -> M_b[(a, ap), bp], or the Gram entries
-    {
-      const int b = row / R, bp = row % R;
-#pragma unroll
-      for (int cc = 0; cc < 64; cc += 16) {
-        const int c0 = h * 64 + cc;
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + 128u + (uint32_t)c0, v);
-        if (k + 1 < d) {
-          char* dst = mop + b * SZ_BIG;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) O::st(dst + eoff<ES>(c0 + j, bp, SBO), v[j]);
-        } else if (bp == 0 && b < nb) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = c0 + j;
-            if (col % R == 0 && col / R < na)
-              g.out[(long long)(a0 + col / R) * g.B.batch + (b0 + b)] = v[j];
-          }
-        }
-      }
-    }
-    async_fence();
-    tc_before();
-    if (__syncthreads_or(bad)) failed = true;
-    tc_after();
-  }
+__device__ __forceinline__ void mma_teardown(const GramMmaArgs& g, MmaState& st, bool failed) {
   if (failed) {
-    // a product did not signal completion: one more bounded wait for whatever is still
-    // in flight before the tensor memory is released, and report the timeout
-    if (tid == 0 && g.err) atomicExch(g.err, (int)T3F_ERR_TIMEOUT);
-    mbar_wait(bar1, ph1);
-    if (pending2) mbar_wait(bar2, ph2);
+    // a product did not signal completion: one more bounded wait for whatever is still in
+    // flight before the tensor memory is released, and report the timeout
+    if (threadIdx.x == 0 && g.err) atomicExch(g.err, (int)T3F_ERR_TIMEOUT);
+    if (st.pending1) mbar_wait(st.bar1, st.ph1);
+    if (st.pending2) mbar_wait(st.bar2, st.ph2);
   }
   tc_before();
   __syncthreads();
   tc_after();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(kTmemCols));
+}
+
+// Uniform batches: one tile per CTA, fixed (RA, RB).
+template <int KIND, int RA, int RB, typename ST>
+__global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant__ GramMmaArgs g) {
+  extern __shared__ __align__(128) char sm[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ long long s_base[2][2][8];
+  __shared__ int s_r0[2][2][8], s_r1[2][2][8];
+  MmaState st;
+  st.s_base = &s_base[0][0][0];
+  st.s_r0 = &s_r0[0][0][0];
+  st.s_r1 = &s_r1[0][0][0];
+  mma_setup(st, s_bar, &s_tmem, sm, g.smem_bytes);
+  constexpr int TA = 128 / RA, TB = 128 / RB;
+  const int ntb = (g.B.batch + TB - 1) / TB;
+  const int a0 = (blockIdx.x / ntb) * TA, b0 = (blockIdx.x % ntb) * TB;
+  const bool ok = mma_tile<KIND, RA, RB, ST>(g, sm, st, 0, a0, min(TA, g.A.batch - a0), b0,
+                                             min(TB, g.B.batch - b0), 0, g.A.d);
+  mma_teardown(g, st, !ok);
+}
+
+// Work-list mode: persistent CTAs drain tiles of any of the six shapes RA <= RB.
+template <int KIND, typename ST>
+__global__ void __launch_bounds__(kMmaThreads) k_gram_mma_list(const __grid_constant__ GramMmaArgs g) {
+  extern __shared__ __align__(128) char sm[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ long long s_base[2][2][8];
+  __shared__ int s_r0[2][2][8], s_r1[2][2][8];
+  __shared__ int s_item[8];
+  __shared__ int s_valid;
+  MmaState st;
+  st.s_base = &s_base[0][0][0];
+  st.s_r0 = &s_r0[0][0][0];
+  st.s_r1 = &s_r1[0][0][0];
+  mma_setup(st, s_bar, &s_tmem, sm, g.smem_bytes);
+  const int tid = threadIdx.x;
+  bool ok = true;
+  while (ok) {
+    __syncthreads();
+    if (tid == 0) {
+      const int w = atomicAdd(g.head, 1);
+      s_valid = w < g.nitems ? 1 : 0;
+      if (w < g.nitems)
+        for (int x = 0; x < 8; ++x) s_item[x] = g.items[w * 8 + x];
+    }
+    __syncthreads();
+    if (!s_valid) break;
+    const int grp = s_item[0], a0 = s_item[1], na = s_item[2], b0 = s_item[3], nb = s_item[4], RA = s_item[5],
+              sym = s_item[6], RB = s_item[7];
+    const int d = g.gd[grp];
+    const int key = RA * 1000 + RB;
+    switch (key) {
+      case 16016: ok = mma_tile<KIND, 16, 16, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
+      case 16032: ok = mma_tile<KIND, 16, 32, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
+      case 16064: ok = mma_tile<KIND, 16, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
+      case 32032: ok = mma_tile<KIND, 32, 32, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
+      case 32064: ok = mma_tile<KIND, 32, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
+      default: ok = mma_tile<KIND, 64, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
+    }
+  }
+  mma_teardown(g, st, !ok);
 }
 
 int pad_pow2_16(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : 64); }
 
-// Operand regions for rank R, in this order: B slices [NBUF][TL] (R x R), A slices, M_b [TL]
-// (128 x R), T_a [TL]. The square slice operands come first so that every address a
-// descriptor can form -- under either assignment of its two stride fields -- stays inside
-// the allocation; consecutive operands are kSkew bytes further apart than their size.
-uint32_t mma_smem_bytes(int kind, int R) {
-  const uint32_t T = 16u / (kind == 0 ? 4u : 2u);
-  const uint32_t sbo = (uint32_t)(R / (int)T) * kLBO;
-  const uint32_t TL = 128u / (uint32_t)R;
-  const uint32_t big = 16u * sbo + kSkew, sl = (uint32_t)(R / 8) * sbo + kSkew;
-  return 2u * (uint32_t)slice_buffers(kind, R) * TL * sl + 2u * TL * big;
-}
-
-template <int KIND, int R, typename ST>
+template <int KIND, int RA, int RB, typename ST>
 t3f_status launch_mma(const GramMmaArgs& g0, cudaStream_t s) {
   GramMmaArgs g = g0;
-  g.smem_bytes = mma_smem_bytes(KIND, R);
-  constexpr int TL = 128 / R;
-  const long long grid = (long long)((g.A.batch + TL - 1) / TL) * ((g.B.batch + TL - 1) / TL);
+  g.smem_bytes = mma_layout(OpT<KIND>::ES, RA, RB).total;
+  g.mode = 0;
+  constexpr int TA = 128 / RA, TB = 128 / RB;
+  const long long grid = (long long)((g.A.batch + TA - 1) / TA) * ((g.B.batch + TB - 1) / TB);
   if (grid <= 0) return T3F_OK;
   if (grid > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
-  auto kern = k_gram_mma<KIND, R, ST>;
+  auto kern = k_gram_mma<KIND, RA, RB, ST>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem_bytes) != cudaSuccess)
     return T3F_ERR_CUDA;
   kern<<<(unsigned)grid, kMmaThreads, g.smem_bytes, s>>>(g);
@@ -397,15 +563,75 @@ t3f_status launch_mma(const GramMmaArgs& g0, cudaStream_t s) {
 }
 
 template <int KIND, typename ST>
-t3f_status dispatch_r(int R, const GramMmaArgs& g, cudaStream_t s) {
-  switch (R) {
-    case 16: return launch_mma<KIND, 16, ST>(g, s);
-    case 32: return launch_mma<KIND, 32, ST>(g, s);
-    default: return launch_mma<KIND, 64, ST>(g, s);
+t3f_status dispatch_r(int RA, int RB, const GramMmaArgs& g, cudaStream_t s) {
+  switch (RA * 1000 + RB) {
+    case 16016: return launch_mma<KIND, 16, 16, ST>(g, s);
+    case 16032: return launch_mma<KIND, 16, 32, ST>(g, s);
+    case 16064: return launch_mma<KIND, 16, 64, ST>(g, s);
+    case 32032: return launch_mma<KIND, 32, 32, ST>(g, s);
+    case 32064: return launch_mma<KIND, 32, 64, ST>(g, s);
+    default: return launch_mma<KIND, 64, 64, ST>(g, s);
   }
 }
 
+uint32_t list_smem(int es) {
+  uint32_t m = 0;
+  const int rs[3] = {16, 32, 64};
+  for (int x = 0; x < 3; ++x)
+    for (int y = x; y < 3; ++y) m = std::max(m, mma_layout(es, rs[x], rs[y]).total);
+  return m;
+}
+
+template <int KIND, typename ST>
+t3f_status launch_list(const GramMmaArgs& g0, cudaStream_t s) {
+  GramMmaArgs g = g0;
+  g.smem_bytes = list_smem(OpT<KIND>::ES);
+  g.mode = 1;
+  if (g.nitems <= 0) return T3F_OK;
+  auto kern = k_gram_mma_list<KIND, ST>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem_bytes) != cudaSuccess)
+    return T3F_ERR_CUDA;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return T3F_ERR_CUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMmaThreads, g.smem_bytes) != cudaSuccess)
+    return T3F_ERR_CUDA;
+  const int grid = std::max(1, std::min(g.nitems, sms * std::max(per_sm, 1)));
+  kern<<<grid, kMmaThreads, g.smem_bytes, s>>>(g);
+  return launch_status();
+}
+
 }  // namespace
+
+// Persistent tensor-core Gram over a work list of rank-sorted ragged objects (groups mode);
+// every item is a tile of (128 / RA) x (128 / RB) pairs of one group, RA <= RB.
+t3f_status launch_gram_mma_list(int math, const void* cores, int dtype, int dmax, const long long* off,
+                                const int* rk, const int* nmodes, const int* items, int nitems, int* head,
+                                const int* gstart, const int* gd, float* gout, const long long* gout_off,
+                                const int* perm, int* err, cudaStream_t s) {
+  GramMmaArgs g;
+  memset(&g, 0, sizeof(g));
+  g.cores = cores;
+  g.off = off;
+  g.rk = rk;
+  g.dmax = dmax;
+  g.nmodes = nmodes;
+  g.gd = gd;
+  g.gstart = gstart;
+  g.perm = perm;
+  g.gout_off = gout_off;
+  g.gout = gout;
+  g.items = items;
+  g.nitems = nitems;
+  g.head = head;
+  g.err = err;
+  if (math == T3F_MATH_TF32) {
+    if (dtype != T3F_F32) return T3F_ERR_DTYPE;
+    return launch_list<0, float>(g, s);
+  }
+  if (dtype == T3F_BF16) return launch_list<1, __nv_bfloat16>(g, s);
+  return launch_list<1, float>(g, s);
+}
 
 bool gram_mma_supported(const TTV& A, const TTV& B, int math) {
   if (math != T3F_MATH_TF32 && math != T3F_MATH_BF16) return false;
@@ -419,14 +645,18 @@ bool gram_mma_supported(const TTV& A, const TTV& B, int math) {
 t3f_status run_gram_mma(const TTV& A, const TTV& B, float* out, int math, int* err, cudaStream_t s) {
   GramMmaArgs g;
   memset(&g, 0, sizeof(g));
-  g.A = A;
-  g.B = B;
+  const int RA = pad_pow2_16(A.rmax), RB = pad_pow2_16(B.rmax);
+  // the kernels take the side of the smaller padded rank as A; the output is transposed back
+  g.swap = RA > RB ? 1 : 0;
+  g.A = g.swap ? B : A;
+  g.B = g.swap ? A : B;
+  g.ldo = B.batch;
   g.out = out;
   g.err = err;
-  const int R = pad_pow2_16(A.rmax > B.rmax ? A.rmax : B.rmax);
-  if (math == T3F_MATH_TF32) return dispatch_r<0, float>(R, g, s);
-  if (A.dtype == T3F_BF16) return dispatch_r<1, __nv_bfloat16>(R, g, s);
-  return dispatch_r<1, float>(R, g, s);
+  const int ra = std::min(RA, RB), rb = std::max(RA, RB);
+  if (math == T3F_MATH_TF32) return dispatch_r<0, float>(ra, rb, g, s);
+  if (A.dtype == T3F_BF16) return dispatch_r<1, __nv_bfloat16>(ra, rb, g, s);
+  return dispatch_r<1, float>(ra, rb, g, s);
 }
 
 }  // namespace t3f

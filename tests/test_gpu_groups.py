@@ -128,3 +128,53 @@ def test_gram_groups_config4_sampled(lib):
             want.append(O.dot(objs[gstart[g] + a], objs[gstart[g] + b]))
         off += Sg * Sg
     assert rel_err(got, want) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("math_", ["tf32", "bf16"])
+def test_gram_groups_tensor_cores(lib, math_):
+    # every pair on the tensor cores in (128/RA) x (128/RB) tiles (RA, RB in 16/32/64 by rank
+    # bucket); one result matrix per group
+    objs, gstart = ragged_case(405)
+    if math_ == "tf32":
+        objs, dt = as_f32(objs), torch.float32
+    else:
+        objs, dt = [round_bf16(o) for o in objs], torch.bfloat16
+    X = lib.RaggedTT.from_objects([[torch.tensor(np.asarray(c)) for c in o] for o in objs], dtype=dt)
+    ws = lib.gram_groups_prepare(X, gstart)
+    G, nrm = lib.gram_groups(X, gstart, ws, math=math_)
+    torch.cuda.synchronize()
+    assert lib.device_status(ws) == 0
+    ref = oracle_groups(objs, gstart)
+    assert np.isfinite(G.cpu().numpy()).all()
+    assert rel_err(G.cpu().numpy(), ref) < TOL[math_]
+    assert rel_err(nrm.cpu().numpy(), [O.norm(o) for o in objs]) < TOL[math_]
+    # each group matrix is symmetric up to the operand rounding
+    off = 0
+    Gh = G.cpu().numpy()
+    for g in range(len(gstart) - 1):
+        S_ = gstart[g + 1] - gstart[g]
+        M = Gh[off:off + S_ * S_].reshape(S_, S_)
+        assert rel_err(M, M.T) < TOL[math_]
+        off += S_ * S_
+
+
+def test_gram_groups_config4_bf16_sampled(lib):
+    cfg = S.config4()
+    objs, gstart = [], [0]
+    for grp in cfg.groups:
+        objs += [round_bf16(o) for o in grp.cores]
+        gstart.append(len(objs))
+    X = lib.RaggedTT.from_objects([[torch.tensor(np.asarray(c)) for c in o] for o in objs], dtype=torch.bfloat16)
+    ws = lib.gram_groups_prepare(X, gstart)
+    G, nrm = lib.gram_groups(X, gstart, ws, math="bf16")
+    G = G.cpu().numpy()
+    rng = np.random.default_rng(406)
+    got, want, off = [], [], 0
+    for g in range(len(gstart) - 1):
+        Sg = gstart[g + 1] - gstart[g]
+        for a, b in [(0, 0), (Sg - 1, Sg - 1)] + [tuple(rng.integers(0, Sg, 2)) for _ in range(4)]:
+            got.append(G[off + a * Sg + b])
+            want.append(O.dot(objs[gstart[g] + a], objs[gstart[g] + b]))
+        off += Sg * Sg
+    assert rel_err(got, want) < TOL["bf16"]
+    assert rel_err(nrm.cpu().numpy()[[0, 100, 511]], [O.norm(objs[i]) for i in (0, 100, 511)]) < TOL["bf16"]

@@ -2,7 +2,8 @@
 FP64 oracle, at the stated tolerances (5e-3 TF32, 2e-2 BF16, normwise relative). TF32 runs on
 FP32 cores (the oracle sees the same FP32 values); BF16 runs on BF16 cores (the oracle sees the
 same BF16-rounded values), so the measured error is the arithmetic's alone. Shapes cover the
-three padded ranks (16, 32, 64), ragged tile edges and unequal ranks on the two sides."""
+three padded ranks (16, 32, 64), ragged tile edges and unequal padded ranks on the two sides
+(either order)."""
 import math
 
 import numpy as np
@@ -19,6 +20,8 @@ CASES = [  # (n, ranks of A, ranks of B, batch A, batch B)
     ([4, 3, 5, 2, 4], [1, 10, 7, 10, 9, 1], [1, 6, 10, 8, 10, 1], 37, 29),
     ([3, 4, 2, 3], [1, 3, 20, 17, 1], [1, 3, 12, 31, 1], 21, 14),
     ([2, 3, 4, 2], [1, 2, 6, 40, 1], [1, 2, 6, 64, 1], 5, 7),
+    ([3, 2, 4], [1, 12, 9, 1], [1, 50, 33, 1], 19, 6),     # padded ranks 16 x 64
+    ([4, 3, 3], [1, 30, 28, 1], [1, 7, 11, 1], 11, 23),    # 32 x 16: sides swapped inside
 ]
 
 
