@@ -26,7 +26,7 @@ namespace {
 
 constexpr uint32_t kLBO = 144;
 constexpr int kMmaThreads = 256;
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 256;  // T at columns 0..127, D at 128..255
 constexpr uint32_t kSkew = 64;  // extra bytes between consecutive operands (16-bank shift)
 
 constexpr uint32_t kSmemCap = 227u * 1024u;
@@ -204,6 +204,104 @@ __device__ __forceinline__ float ldc(const void* p, long long i) {
   return ldf<ST>(static_cast<const ST*>(p), i);
 }
 
+// Raw bits of one stored element (F32 or BF16), converted only when the slice is packed, so
+// the loads of a slice stay in flight while the products run.
+template <typename ST>
+__device__ __forceinline__ uint32_t ld_raw(const ST* p);
+template <>
+__device__ __forceinline__ uint32_t ld_raw<float>(const float* p) { return __float_as_uint(__ldg(p)); }
+template <>
+__device__ __forceinline__ uint32_t ld_raw<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p));
+}
+
+// T raw elements -> one 16-byte operand row (TF32: 4 x 4 bytes, BF16: 8 x 2 bytes)
+template <int KIND, typename ST, int T>
+__device__ __forceinline__ uint4 pack_raw(const uint32_t (&v)[T]) {
+  if constexpr (KIND == 0) {
+    return OpT<0>::pack({__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]), __uint_as_float(v[3])});
+  } else if constexpr (sizeof(ST) == 2) {
+    return make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16));
+  } else {
+    return make_uint4(OpT<1>::cv2(__uint_as_float(v[0]), __uint_as_float(v[1])),
+                      OpT<1>::cv2(__uint_as_float(v[2]), __uint_as_float(v[3])),
+                      OpT<1>::cv2(__uint_as_float(v[4]), __uint_as_float(v[5])),
+                      OpT<1>::cv2(__uint_as_float(v[6]), __uint_as_float(v[7])));
+  }
+}
+
+// Two 16-lane x 8-column TMEM loads (columns c and c + 8 of lanes L..L+15): thread t gets
+// lanes L + t/4 and L + 8 + t/4, columns 2(t%4) and 2(t%4)+1 of each 8-column block.
+__device__ __forceinline__ void tmem_ld_16x16(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%8];\n"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%4,%5,%6,%7}, [%9];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr), "r"(taddr + 8u)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t bf2(uint32_t lo, uint32_t hi) {
+  const __nv_bfloat162 b = __floats2bfloat162_rn(__uint_as_float(lo), __uint_as_float(hi));
+  return *reinterpret_cast<const uint32_t*>(&b);
+}
+
+// BF16 transposing epilogue: TMEM rows (x, kappa) (x = row / RL) and columns m = 0..127 go to
+// operand x at (row m, K = kappa) of a K-major BF16 operand array (operand stride BIG, row
+// groups SBO apart). Each warp covers the 32 lanes of its quarter and 64 of the columns; every
+// 16 x 16 block is two TMEM loads, four packs and one transposing matrix store.
+template <int RL, uint32_t SBO, uint32_t BIG>
+__device__ __forceinline__ void epi_bf16(uint32_t tcol, char* dst) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
+  const int mi = lane >> 3, j = lane & 7;
+#pragma unroll
+  for (int win = 0; win < 2; ++win) {
+    const int L0 = q * 32 + win * 16;
+    const int x = L0 / RL, k0 = L0 % RL;
+    uint32_t r[4][8];
+#pragma unroll
+    for (int cb = 0; cb < 4; ++cb) tmem_ld_16x16(tcol + ((uint32_t)L0 << 16) + (uint32_t)(h * 64 + cb * 16), r[cb]);
+    tmem_wait_ld();
+    char* base = dst + x * BIG + (uint32_t)(k0 / 8 + (mi & 1)) * kLBO + (uint32_t)j * 16u;
+#pragma unroll
+    for (int cb = 0; cb < 4; ++cb) {
+      const int col = h * 64 + cb * 16 + (mi >> 1) * 8;  // this lane's matrix column block
+      const uint32_t addr = su32(base + (uint32_t)(col >> 3) * SBO);
+      asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(addr),
+                   "r"(bf2(r[cb][0], r[cb][1])), "r"(bf2(r[cb][2], r[cb][3])), "r"(bf2(r[cb][4], r[cb][5])),
+                   "r"(bf2(r[cb][6], r[cb][7]))
+                   : "memory");
+    }
+  }
+}
+
+// Same transposition element by element (any operand type): thread = TMEM row.
+template <int KIND, int RL, uint32_t SBO, uint32_t BIG>
+__device__ __forceinline__ void epi_scalar(uint32_t tcol, char* dst) {
+  using O = OpT<KIND>;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
+  const int row = q * 32 + lane, x = row / RL, kk = row % RL;
+  char* d = dst + x * BIG;
+#pragma unroll
+  for (int cc = 0; cc < 64; cc += 16) {
+    const int c0 = h * 64 + cc;
+    float v[16];
+    tmem_ld16(tcol + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) O::st(d + eoff<O::ES>(c0 + jj, kk, SBO), v[jj]);
+  }
+}
+
+template <int KIND, int RL, uint32_t SBO, uint32_t BIG>
+__device__ __forceinline__ void epi_transpose(uint32_t tcol, char* dst) {
+  if constexpr (KIND == 1)
+    epi_bf16<RL, SBO, BIG>(tcol, dst);
+  else
+    epi_scalar<KIND, RL, SBO, BIG>(tcol, dst);
+}
+
 // Everything a CTA keeps across the tiles it processes.
 struct MmaState {
   uint32_t tmem, bar1, bar2, ph1, ph2;
@@ -217,8 +315,8 @@ struct MmaState {
 // One tile: na x nb pairs (a0.., b0..) of one group (or of the uniform batches), d cores.
 // Returns false (block-uniformly) when a tensor-core wait ran out.
 template <int KIND, int RA, int RB, typename ST>
-__device__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, int a0, int na, int b0, int nb,
-                         int sym, int d) {
+__device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int grp, int a0, int na, int b0, int nb,
+                              int sym, int d) {
   using O = OpT<KIND>;
   constexpr int ES = O::ES;
   constexpr int T = 16 / ES;
@@ -281,24 +379,32 @@ __device__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, 
 
   // slice i of core k of both sides -> registers. K run j of this thread on side X covers
   // object o = (suX + j*USX) / KGX, columns c = ((suX + j*USX) % KGX) * T + t, row srX
-  float pb[UPB][T], pa[UPA][T];
+  uint32_t pb[UPB][T], pa[UPA][T];
   auto load_slice = [&](int k, int i) {
     const int par = k & 1, n = nmode(k);
 #pragma unroll
     for (int j = 0; j < UPB; ++j) {
       const int w = suB + j * USB, o = w / KGB, c0 = (w % KGB) * T;
-      const int r0 = s_r0[par][1][o], r1 = s_r1[par][1][o];
-      const long long b = s_base[par][1][o] + (long long)i * r1 + srB, stp = (long long)n * r1;
+      const int r0 = s_r0[par][1][o], r1 = s_r1[par][1][o], stp = n * r1;
+      const ST* ptr = static_cast<const ST*>(Bp) + s_base[par][1][o] + (long long)c0 * stp + i * r1 + srB;
+      const bool rok = srB < r1;
 #pragma unroll
-      for (int t = 0; t < T; ++t) pb[j][t] = (c0 + t < r0 && srB < r1) ? ldc<ST>(Bp, b + (c0 + t) * stp) : 0.0f;
+      for (int t = 0; t < T; ++t) {
+        pb[j][t] = (rok && c0 + t < r0) ? ld_raw<ST>(ptr) : 0u;
+        ptr += stp;
+      }
     }
 #pragma unroll
     for (int j = 0; j < UPA; ++j) {
       const int w = suA + j * USA, o = w / KGA, c0 = (w % KGA) * T;
-      const int r0 = s_r0[par][0][o], r1 = s_r1[par][0][o];
-      const long long b = s_base[par][0][o] + (long long)i * r1 + srA, stp = (long long)n * r1;
+      const int r0 = s_r0[par][0][o], r1 = s_r1[par][0][o], stp = n * r1;
+      const ST* ptr = static_cast<const ST*>(Ap) + s_base[par][0][o] + (long long)c0 * stp + i * r1 + srA;
+      const bool rok = srA < r1;
 #pragma unroll
-      for (int t = 0; t < T; ++t) pa[j][t] = (c0 + t < r0 && srA < r1) ? ldc<ST>(Ap, b + (c0 + t) * stp) : 0.0f;
+      for (int t = 0; t < T; ++t) {
+        pa[j][t] = (rok && c0 + t < r0) ? ld_raw<ST>(ptr) : 0u;
+        ptr += stp;
+      }
     }
   };
   // registers -> slice buffer s: one 16-byte store per K run (a whole core-matrix row)
@@ -307,13 +413,13 @@ __device__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, 
     for (int j = 0; j < UPB; ++j) {
       const int w = suB + j * USB, o = w / KGB, cg = w % KGB;
       const uint32_t off = (uint32_t)(srB >> 3) * SBOB + (uint32_t)cg * kLBO + (uint32_t)(srB & 7) * 16u;
-      *reinterpret_cast<uint4*>(bsl + (s * TB + o) * SLB + off) = O::pack(pb[j]);
+      *reinterpret_cast<uint4*>(bsl + (s * TB + o) * SLB + off) = pack_raw<KIND, ST, T>(pb[j]);
     }
 #pragma unroll
     for (int j = 0; j < UPA; ++j) {
       const int w = suA + j * USA, o = w / KGA, cg = w % KGA;
       const uint32_t off = (uint32_t)(srA >> 3) * SBOA + (uint32_t)cg * kLBO + (uint32_t)(srA & 7) * 16u;
-      *reinterpret_cast<uint4*>(asl + (s * TA + o) * SLA + off) = O::pack(pa[j]);
+      *reinterpret_cast<uint4*>(asl + (s * TA + o) * SLA + off) = pack_raw<KIND, ST, T>(pa[j]);
     }
   };
 
@@ -336,14 +442,13 @@ __device__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, 
       // ---- MMA1: T for every b (TMEM columns b*RB .. b*RB + RB - 1)
       if (tid == 0) {
         tc_after();
-#pragma unroll 1
-        for (int b = 0; b < TB; ++b) {
-          const uint32_t am = su32(mop + b * BIGB), bm = su32(bsl + (s * TB + b) * SLB);
+        const uint64_t da = sdesc(su32(mop), SBOB), db = sdesc(su32(bsl + s * TB * SLB), SBOB);
+#pragma unroll
+        for (int b = 0; b < TB; ++b)
 #pragma unroll
           for (int kk = 0; kk < RB / O::KI; ++kk)
-            mma<KIND>(st.tmem + (uint32_t)(b * RB), sdesc(am + kk * 2 * kLBO, SBOB), sdesc(bm + kk * 2 * kLBO, SBOB),
-                      ID1, kk > 0);
-        }
+            mma<KIND>(st.tmem + (uint32_t)(b * RB), da + ((b * BIGB + kk * 2 * kLBO) >> 4),
+                      db + ((b * SLB + kk * 2 * kLBO) >> 4), ID1, kk > 0);
         mma_commit(st.bar1);
       }
       st.pending1 = true;
@@ -363,32 +468,20 @@ __device__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, 
       }
       tc_after();
       // ---- epilogue 1: T (rows (a, al), cols (b, bp)) -> T_a[(b, bp), al]
-      {
-        const int a = row / RA, al = row % RA;
-        char* dst = top + a * BIGA;
-#pragma unroll
-        for (int cc = 0; cc < 64; cc += 16) {
-          const int c0 = h * 64 + cc;
-          float v[16];
-          tmem_ld16(st.tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) O::st(dst + eoff<ES>(c0 + j, al, SBOA), v[j]);
-        }
-      }
+      epi_transpose<KIND, RA, SBOA, BIGA>(st.tmem, top);
       async_fence();
       tc_before();
       if (__syncthreads_or(st.bad)) return false;
       // ---- MMA2: D_a += T_a A_a,i for every a (TMEM columns 128 + a*RA ..)
       if (tid == 0) {
         tc_after();
-#pragma unroll 1
-        for (int a = 0; a < TA; ++a) {
-          const uint32_t am = su32(top + a * BIGA), bm = su32(asl + (s * TA + a) * SLA);
+        const uint64_t da = sdesc(su32(top), SBOA), db = sdesc(su32(asl + s * TA * SLA), SBOA);
+#pragma unroll
+        for (int a = 0; a < TA; ++a)
 #pragma unroll
           for (int kk = 0; kk < RA / O::KI; ++kk)
-            mma<KIND>(st.tmem + 128u + (uint32_t)(a * RA), sdesc(am + kk * 2 * kLBO, SBOA),
-                      sdesc(bm + kk * 2 * kLBO, SBOA), ID2, (i > 0 || kk > 0) ? 1u : 0u);
-        }
+            mma<KIND>(st.tmem + 128u + (uint32_t)(a * RA), da + ((a * BIGA + kk * 2 * kLBO) >> 4),
+                      db + ((a * SLA + kk * 2 * kLBO) >> 4), ID2, (i > 0 || kk > 0) ? 1u : 0u);
         mma_commit(st.bar2);
       }
       st.pending2 = true;
@@ -398,18 +491,16 @@ __device__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, 
     st.pending2 = false;
     tc_after();
     // ---- epilogue 2: D (rows (b, bp), cols (a, ap)) -> M_b[(a, ap), bp], or the Gram entries
-    {
+    if (k + 1 < d) {
+      epi_transpose<KIND, RB, SBOB, BIGB>(st.tmem + 128u, mop);
+    } else {
       const int b = row / RB, bp = row % RB;
 #pragma unroll
       for (int cc = 0; cc < 64; cc += 16) {
         const int c0 = h * 64 + cc;
         float v[16];
         tmem_ld16(st.tmem + ((uint32_t)(q * 32) << 16) + 128u + (uint32_t)c0, v);
-        if (k + 1 < d) {
-          char* dst = mop + b * BIGB;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) O::st(dst + eoff<ES>(c0 + j, bp, SBOB), v[j]);
-        } else if (bp == 0 && b < nb) {
+        if (bp == 0 && b < nb && k + 1 == d) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int col = c0 + j, a = col / RA;
@@ -436,6 +527,12 @@ __device__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, 
     tc_after();
   }
   return true;
+}
+
+template <int KIND, int RA, int RB, typename ST>
+__device__ __forceinline__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, int a0, int na,
+                                         int b0, int nb, int sym, int d) {
+  return mma_tile_sync<KIND, RA, RB, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d);
 }
 
 // Common prologue / epilogue of the kernels: TMEM allocation, barriers, and the release of
@@ -480,9 +577,14 @@ __device__ __forceinline__ void mma_teardown(const GramMmaArgs& g, MmaState& st,
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(kTmemCols));
 }
 
+// CTAs per SM the shared memory of a tile shape allows (at most 2: the tensor memory holds two)
+__host__ __device__ constexpr int mma_ctas_per_sm(int es, int RA, int RB) {
+  return mma_layout(es, RA, RB).total + 1024u <= kSmemCap / 2u ? 2 : 1;
+}
+
 // Uniform batches: one tile per CTA, fixed (RA, RB).
 template <int KIND, int RA, int RB, typename ST>
-__global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant__ GramMmaArgs g) {
+__global__ void __launch_bounds__(kMmaThreads, mma_ctas_per_sm(OpT<KIND>::ES, RA, RB)) k_gram_mma(const __grid_constant__ GramMmaArgs g) {
   extern __shared__ __align__(128) char sm[];
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
@@ -503,7 +605,7 @@ __global__ void __launch_bounds__(kMmaThreads) k_gram_mma(const __grid_constant_
 
 // Work-list mode: persistent CTAs drain tiles of any of the six shapes RA <= RB.
 template <int KIND, typename ST>
-__global__ void __launch_bounds__(kMmaThreads) k_gram_mma_list(const __grid_constant__ GramMmaArgs g) {
+__global__ void __launch_bounds__(kMmaThreads, 1) k_gram_mma_list(const __grid_constant__ GramMmaArgs g) {
   extern __shared__ __align__(128) char sm[];
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
