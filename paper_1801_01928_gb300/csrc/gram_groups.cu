@@ -27,6 +27,7 @@ t3f_status launch_gram_tile_table(const void* cores, int dtype, int dmax, const 
                                   const int* gd, float* out, const long long* gout_off, const int* perm, size_t smem,
                                   cudaStream_t s);
 size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB);
+bool gram_tile_bwd_fits(int na, int nb, int RA, int RB);
 t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, const long long* off, const int* rk,
                                       const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
                                       const int* gd, const int* perm, const float* dout, const long long* gout_off,
@@ -212,6 +213,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
               if (na * (RA / 4) * nb * (RB / 4) > 1024) return T3F_ERR_UNSUPPORTED;
               const size_t sm = bwd ? gram_tile_bwd_smem(na, nb, RA, RB) : gram_tile_smem(na, nb, RA, RB);
               if (sm > 200 * 1024) return T3F_ERR_UNSUPPORTED;
+              if (bwd && !gram_tile_bwd_fits(na, nb, RA, RB)) return T3F_ERR_UNSUPPORTED;
               if (!bwd && na * RA * RA + nb * RB * RB > 512 * 16) return T3F_ERR_UNSUPPORTED;
               It it;
               it.cost = (double)na * nb * RA * RB * (RA + RB) * slices;
@@ -280,7 +282,13 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
           }
         }
     }
-    std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+    // grouped by tile shape (largest first), then by cost: a CTA rarely switches between the
+    // shapes' code paths, which keeps the instruction cache warm
+    std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) {
+      if (x.v[7] != y.v[7]) return x.v[7] > y.v[7];
+      if (x.v[5] != y.v[5]) return x.v[5] > y.v[5];
+      return x.cost > y.cost;
+    });
     P->mitems.resize(its.size() * 8);
     for (size_t w = 0; w < its.size(); ++w)
       for (int x = 0; x < 8; ++x) P->mitems[w * 8 + x] = its[w].v[x];
@@ -294,7 +302,9 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
     const int R = kBucketMax[b];
     int side = 1;
     for (int t = 2; t <= tl[b]; ++t)
-      if ((long long)t * t * (R / 4) * (R / 4) <= 1024 && gram_tile_bwd_smem(t, t, R, R) <= 200 * 1024) side = t;
+      if ((long long)t * t * (R / 4) * (R / 4) <= 1024 && gram_tile_bwd_smem(t, t, R, R) <= 200 * 1024 &&
+          gram_tile_bwd_fits(t, t, R, R))
+        side = t;
     tlb[b] = side;
   }
   size_t bsmem = 0;

@@ -65,6 +65,9 @@ template <typename ST>
 __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramTileArgs g) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_item[8];
+  // per-core object info, two core parities: [side * 16 + object] core offset and ranks
+  __shared__ long long s_ob[2][32];
+  __shared__ int s_or0[2][32], s_or1[2][32], s_on[2];
   const int tid = threadIdx.x, nth = blockDim.x;
 
   for (int it = 0;; ++it) {
@@ -149,44 +152,40 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
     const void* Ap = g.mode == 0 ? g.A.p : g.gcores;
     const void* Bp = g.mode == 0 ? g.B.p : g.gcores;
     const int szA = na * RA * RA, szS = szA + nb * RB * RB;
-    // this thread's staging elements (fixed for the tile): side, object, row, col
-    int sdesc[kGTMaxPF];
-#pragma unroll
-    for (int u = 0; u < kGTMaxPF; ++u) {
-      const int e = tid + u * nth;
-      int dsc = -1;
-      if (e < szS) {
-        if (e < szA) {
-          const int t = e / (RA * RA), q = e % (RA * RA);
-          dsc = (0 << 30) | (t << 16) | ((q / RA) << 8) | (q % RA);
-        } else {
-          const int e2 = e - szA;
-          const int t = e2 / (RB * RB), q = e2 % (RB * RB);
-          dsc = (1 << 30) | (t << 16) | ((q / RB) << 8) | (q % RB);
-        }
+    // exact quotients of the staging indices (< 2^13) by R^2 and R through 32-bit reciprocals
+    const unsigned mAA = 0xffffffffu / (unsigned)(RA * RA) + 1u, mA = 0xffffffffu / (unsigned)RA + 1u;
+    const unsigned mBB = 0xffffffffu / (unsigned)(RB * RB) + 1u, mB = 0xffffffffu / (unsigned)RB + 1u;
+    // core offsets and ranks of the tile's objects for core k into parity slot par; the
+    // slots are filled ahead of use and published by a later block barrier
+    auto fill_info = [&](int k, int par) {
+      if (tid < 32) {
+        const int side = tid >> 4, t = tid & 15;
+        long long base = 0;
+        int r0 = 0, r1 = 0, n = 1;
+        if (side == 0 && t < na) objA(t, k, &base, &r0, &r1, &n);
+        if (side == 1 && t < nb) objB(t, k, &base, &r0, &r1, &n);
+        s_ob[par][tid] = base;
+        s_or0[par][tid] = r0;
+        s_or1[par][tid] = r1;
+        if (tid == 0) s_on[par] = n;
       }
-      sdesc[u] = dsc;
-    }
+    };
     // stage slice i of core k into `buf` (zero-padded): FP32 cores are copied asynchronously
     // (cp.async, 4 bytes, zero-fill outside the ranks), BF16 cores converted on the way
     auto stage = [&](int k, int i, float* buf) {
-      int rA0, rA1, nA, rB0, rB1, nB;
-      long long bA0, bB0;
-      objA(0, k, &bA0, &rA0, &rA1, &nA);
-      objB(0, k, &bB0, &rB0, &rB1, &nB);
-#pragma unroll
-      for (int u = 0; u < kGTMaxPF; ++u) {
-        const int dsc = sdesc[u];
-        if (dsc < 0) continue;
-        const int side = dsc >> 30, t = (dsc >> 16) & 0x3fff, row = (dsc >> 8) & 0xff, col = dsc & 0xff;
-        long long base;
-        int r0, r1, n;
-        if (side == 0) objA(t, k, &base, &r0, &r1, &n);
-        else objB(t, k, &base, &r0, &r1, &n);
+      const int par = k & 1, n = s_on[par];
+#pragma unroll 2
+      for (int e = tid; e < szS; e += nth) {
+        const int side = e < szA ? 0 : 1;
+        const unsigned e2 = (unsigned)(side ? e - szA : e), R = side ? RB : RA;
+        const unsigned t = __umulhi(e2, side ? mBB : mAA), qq = e2 - t * R * R;
+        const unsigned rq = __umulhi(qq, side ? mB : mA);
+        const int row = (int)rq, col = (int)(qq - rq * R);
+        const int slot = side * 16 + (int)t, r0 = s_or0[par][slot], r1 = s_or1[par][slot];
         const bool ok = row < r0 && col < r1 && i < n;
-        const long long idx = ok ? base + ((long long)row * n + i) * r1 + col : base;
+        const long long idx = ok ? s_ob[par][slot] + ((long long)row * n + i) * r1 + col : 0;
         const void* src = side == 0 ? Ap : Bp;
-        float* dst = buf + tid + u * nth;
+        float* dst = buf + e;
         if (sizeof(ST) == 4) {
           const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
           const float* gp = static_cast<const float*>(src) + idx;
@@ -224,15 +223,13 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
     const int mstep = na * RA;
     float* stg[2] = {As, As + szS};
     int k = 0, i = 0, cur = 0;
+    fill_info(0, 0);
+    if (d > 1) fill_info(1, 1);
+    __syncthreads();
     stage(0, 0, stg[0]);
     float acc[kGTMaxBlk][4][4];
     while (k < d) {
-      int nk;
-      {
-        long long bb;
-        int r0, r1;
-        objA(0, k, &bb, &r0, &r1, &nk);
-      }
+      const int nk = s_on[k & 1];
       if (i == 0) {
 #pragma unroll
         for (int q = 0; q < kGTMaxBlk; ++q)
@@ -294,6 +291,7 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
                 *reinterpret_cast<const float4*>(TT + r * TR + 4 * (unit ^ ((r >> 2) & 7))));
         }
       }
+      if (i + 1 == nk && k + 2 < d) fill_info(k + 2, k & 1);  // core k's slices are all staged
       __syncthreads();  // stg[cur] and TT are free again
       cur ^= 1;
       if (++i >= nk) {

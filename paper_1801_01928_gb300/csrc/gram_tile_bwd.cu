@@ -52,10 +52,15 @@ __device__ __forceinline__ void fma44b(float (&acc)[4][4], const float4 a, const
     for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
 }
 
+constexpr int kGTBMaxPF = 16;  // staging elements per thread and slice (tiles up to 8192 elements)
+
 template <typename ST>
 __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ GramBwdTileArgs g) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_item[8];
+  // per-core object info, two core parities: [side * 16 + object] core offset and ranks
+  __shared__ long long s_ob[2][32];
+  __shared__ int s_or0[2][32], s_or1[2][32], s_on[2];
   const int tid = threadIdx.x, nth = blockDim.x;
   float* scr = g.scratch + (long long)blockIdx.x * g.scratch_stride;
   for (int it = 0;; ++it) {
@@ -135,41 +140,53 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
       }
       gsm[p] = v;
     }
+    // core offsets and ranks of the tile's objects for core k into parity slot par; the
+    // slots are filled ahead of use and published by the barrier that ends a core
+    auto fill_info = [&](int k, int par) {
+      if (tid < 32) {
+        const int side = tid >> 4, t = tid & 15;
+        long long base = 0;
+        int r0 = 0, r1 = 0, n = 1;
+        if (t < (side ? nb : na)) objX(side, t, k, &base, &r0, &r1, &n);
+        s_ob[par][tid] = base;
+        s_or0[par][tid] = r0;
+        s_or1[par][tid] = r1;
+        if (tid == 0) s_on[par] = n;
+      }
+    };
+    // exact quotients of the staging indices (< 2^13) by R^2 and R through 32-bit reciprocals
+    const unsigned mAA = 0xffffffffu / (unsigned)(RA * RA) + 1u, mA = 0xffffffffu / (unsigned)RA + 1u;
+    const unsigned mBB = 0xffffffffu / (unsigned)(RB * RB) + 1u, mB = 0xffffffffu / (unsigned)RB + 1u;
     // stage slice i of core k: trans = 0 -> [t][row][col], trans = 1 -> [t][col][row]
     auto stage = [&](int k, int i, float* buf, int trans) {
-      int rA0, rA1, nA, rB0, rB1, nB;
-      long long bb;
-      objX(0, 0, k, &bb, &rA0, &rA1, &nA);
-      objX(1, 0, k, &bb, &rB0, &rB1, &nB);
+      const int par = k & 1, n = s_on[par];
+#pragma unroll 2
       for (int e = tid; e < szS; e += nth) {
         const int side = e < szA ? 0 : 1;
-        const int R = side == 0 ? RA : RB;
-        const int e2 = side == 0 ? e : e - szA;
-        const int t = e2 / (R * R), q = e2 % (R * R);
-        const int u = q / R, v = q % R;
-        const int row = trans ? v : u, col = trans ? u : v;
-        long long base;
-        int r0, r1, n;
-        objX(side, t, k, &base, &r0, &r1, &n);
+        const unsigned e2 = (unsigned)(side ? e - szA : e), R = side ? RB : RA;
+        const unsigned t = __umulhi(e2, side ? mBB : mAA), qq = e2 - t * R * R;
+        const unsigned xq = __umulhi(qq, side ? mB : mA);
+        const int x = (int)xq, y = (int)(qq - xq * R);
+        const int row = trans ? y : x, col = trans ? x : y, slot = side * 16 + t;
+        const int r0 = s_or0[par][slot], r1 = s_or1[par][slot];
         const bool ok = row < r0 && col < r1 && i < n;
-        const long long idx = ok ? base + ((long long)row * n + i) * r1 + col : base;
+        const long long idx = ok ? s_ob[par][slot] + ((long long)row * n + i) * r1 + col : 0;
         const void* src = side == 0 ? Ap : Bp;
+        float* dst = buf + e;
         if (sizeof(ST) == 4) {
-          const unsigned sa = (unsigned)__cvta_generic_to_shared(buf + e);
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
           const float* gp = static_cast<const float*>(src) + idx;
           asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gp), "r"(ok ? 4 : 0));
         } else {
-          buf[e] = ok ? ldf<ST>(static_cast<const ST*>(src), idx) : 0.0f;
+          *dst = ok ? ldf<ST>(static_cast<const ST*>(src), idx) : 0.0f;
         }
       }
       if (sizeof(ST) == 4) asm volatile("cp.async.commit_group;\n" ::);
     };
-    auto nmode = [&](int k) {
-      long long bb;
-      int r0, r1, n;
-      objX(0, 0, k, &bb, &r0, &r1, &n);
-      return n;
-    };
+    auto nmode = [&](int k) { return s_on[k & 1]; };
+    fill_info(0, 0);
+    if (d > 1) fill_info(1, 1);
+    __syncthreads();
     // ---------------- left sweep: M at every interface into the CTA scratch ------------
     // scratch layout per interface j: [a][al][b][be]
     for (int e = tid; e < P * PS; e += nth) {
@@ -257,6 +274,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
               }
             }
           }
+          if (k + 2 < d) fill_info(k + 2, k & 1);  // core k's slices are all staged
           __syncthreads();
           i = 0;
           ++k;
@@ -414,6 +432,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           }
         }
       }
+      if (k > 0) fill_info(k - 1, (k - 1) & 1);  // core k's slices are all staged
       __syncthreads();
     }
   }
@@ -422,6 +441,8 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
 // ---------------------------------------------------------------------------------------
 
 static int pad4b(int r) { return (r + 3) & ~3; }
+
+bool gram_tile_bwd_fits(int na, int nb, int RA, int RB) { return na * RA * RA + nb * RB * RB <= 512 * kGTBMaxPF; }
 
 size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB) {
   const size_t P = (size_t)na * nb, PS = (size_t)RA * RB;
@@ -439,6 +460,7 @@ void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB
   for (int ta = 1; ta <= 16 && ta <= batchA; ++ta)
     for (int tb = 1; tb <= 16 && tb <= batchB; ++tb) {
       if (ta * (RA / 4) * tb * (RB / 4) > 1024) continue;
+      if (ta * RA * RA + tb * RB * RB > 512 * kGTBMaxPF) continue;
       if (gram_tile_bwd_smem(ta, tb, RA, RB) > 200 * 1024) continue;
       const long long tiles = (long long)((batchA + ta - 1) / ta) * ((batchB + tb - 1) / tb);
       const long long per_sm = (tiles + sms - 1) / sms;
@@ -453,7 +475,8 @@ void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB
 
 bool gram_tile_bwd_supported(const TTV& A, const TTV& B) {
   const int RA = pad4b(A.rmax), RB = pad4b(B.rmax);
-  return RA <= 64 && RB <= 64 && gram_tile_bwd_smem(1, 1, RA, RB) <= 200 * 1024 && A.d <= T3F_MAX_D;
+  return RA <= 64 && RB <= 64 && gram_tile_bwd_smem(1, 1, RA, RB) <= 200 * 1024 && RA * RA + RB * RB <= 512 * kGTBMaxPF &&
+         A.d <= T3F_MAX_D;
 }
 
 size_t ws_gram_tile_bwd(const TTV& A, const TTV& B) {
