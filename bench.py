@@ -341,6 +341,19 @@ def run_step(w, timers=None, stream=None):
     return out
 
 
+def tensor_peaks():
+    """Dense tensor peaks (TFLOP/s) for a kernel timed alone: the measured cuBLAS BF16 burst
+    figure, and TF32 at NVIDIA's nominal TF32/BF16 ratio (1.1 / 2.25) of it."""
+    src, bf16 = "fallback", 1900.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+            src = "measured"
+    except (OSError, ValueError, KeyError):
+        pass
+    return {"bf16": bf16, "tf32": bf16 * 1.1 / 2.25}, src
+
+
 def reduced_precision(w, flops, flush, stream, reps=5):
     """TF32 / BF16 tensor-core Gram of config 3a and the uneven batch with BF16 cores, each
     timed with CUDA events (L2 flushed before every repetition) and compared with the FP32
@@ -372,11 +385,19 @@ def reduced_precision(w, flops, flush, stream, reps=5):
         return float((x.double() - y).norm() / y.norm())
 
     out = {}
+    peaks, psrc = tensor_peaks()
+
+    def roof(gflops, kind):
+        return {"bound": "tensor", "achieved": round(gflops / 1e3, 3), "peak": round(peaks[kind], 1),
+                "unit": "TFLOP/s", "frac": round(gflops / 1e3 / peaks[kind], 5), "peak_source": psrc,
+                "flops": "algorithmic (unpadded ranks)"}
+
     for math_ in ("tf32", "bf16"):
         ms = timed(lambda: t3f.gram(A3, B3, math=math_))
         G = t3f.gram(A3, B3, math=math_)
-        out[f"gram_{math_}"] = {"ms": round(ms, 4), "gflops": round(flops["gram"] / (ms * 1e-3) / 1e9, 1),
-                                "diff_vs_fp32": round(rel(G, G32), 6),
+        gf = flops["gram"] / (ms * 1e-3) / 1e9
+        out[f"gram_{math_}"] = {"ms": round(ms, 4), "gflops": round(gf, 1),
+                                "diff_vs_fp32": round(rel(G, G32), 6), "roofline": roof(gf, math_),
                                 "path": "tcgen05 " + math_ + " products, FP32 accumulation in TMEM"}
     for key, X_, ws_, math_, path in (
             ("uneven_bf16_cores", X4b, ws4b, "fp32", "BF16 cores, FP32 CUDA-core arithmetic (grouped work list)"),
@@ -384,8 +405,11 @@ def reduced_precision(w, flops, flush, stream, reps=5):
             ("uneven_bf16_tc", X4b, ws4b, "bf16", "BF16 cores; tcgen05 BF16 tiles, FP32 accumulation")):
         ms = timed(lambda: t3f.gram_groups(X_, w.gstart, ws_, w.tiles4, math=math_))
         Gx, _ = t3f.gram_groups(X_, w.gstart, ws_, w.tiles4, math=math_)
-        out[key] = {"ms": round(ms, 4), "gflops": round(flops["uneven"] / (ms * 1e-3) / 1e9, 1),
-                    "diff_vs_fp32": round(rel(Gx, G4_32), 6), "path": path}
+        gf = flops["uneven"] / (ms * 1e-3) / 1e9
+        out[key] = {"ms": round(ms, 4), "gflops": round(gf, 1), "diff_vs_fp32": round(rel(Gx, G4_32), 6),
+                    "path": path}
+        if math_ != "fp32":
+            out[key]["roofline"] = roof(gf, math_)
     return out
 
 

@@ -238,6 +238,9 @@ t3f_status t3f_orthogonalize(const t3f_tt* X, t3f_tt* U, t3f_tt* V, void* ws,
  * [Z->batch]; dU: F32 descriptor with U's shape. With Z->batch = 1 and c = 1 this is the
  * projection P_X Z ('project' in Table 1). The TT of S has cores [dU_1, U_1],
  * [[V_k, 0], [dU_k, U_k]], [[V_d], [dU_d]] (ranks <= 2 r).
+ * math: FP32; TF32 and BF16 are accepted when Z's ranks are < 16 (every contraction then has
+ * one side below the tensor-core threshold, and the FP32 CUDA-core sweeps run), else
+ * T3F_ERR_UNSUPPORTED.
  */
 t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3f_tt* Z,
                            const float* c, t3f_tt* dU, int32_t math, void* ws,

@@ -423,7 +423,9 @@ extern "C" t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3
   T3F_CHECK(check_like(dU, vu, &vd));
   if (!c) return T3F_ERR_ARG;
   if (math != T3F_MATH_FP32 && math != T3F_MATH_TF32 && math != T3F_MATH_BF16) return T3F_ERR_ARG;
-  if (math != T3F_MATH_FP32) return T3F_ERR_UNSUPPORTED;
+  // tensor cores only pay off when both ranks of a contraction are >= 16; below that the
+  // reduced-precision modes run the FP32 CUDA-core sweeps (at least as accurate)
+  if (math != T3F_MATH_FP32 && vz.rmax >= 16) return T3F_ERR_UNSUPPORTED;
   PsumLayout l = psum_layout(vu, vz, false);
   T3F_CHECK(check_ws(ws, ws_bytes, l.total));
   cudaStream_t s = (cudaStream_t)stream;

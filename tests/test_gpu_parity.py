@@ -351,3 +351,14 @@ def test_project_sum_fwd_bwd_shapes(lib, shape):
     rZ, rc = O.project_sum_vjp(Uo, Vo, objects(Z), c.astype(np.float64), host_objects(dU)[0])
     assert rel_err_cores(host_cores(dZ), batched(rZ)) < TOL["fp32"]
     assert rel_err(dc.cpu().numpy(), rc) < TOL["fp32"]
+
+
+def test_project_sum_reduced_precision_modes_below_threshold(lib):
+    # Z rank 2 < 16: the TF32 / BF16 modes run the FP32 sweeps and agree with FP32 exactly
+    cfg = S.config1()
+    X, Z = round32(cfg.X), round32(cfg.B)
+    U, V = _orth(lib, X, torch.float32)
+    Zt, c = dev_tt(lib, Z), torch.tensor(cfg.c.astype(np.float32), device="cuda")
+    ref = lib.project_sum(U, V, Zt, c).data
+    for m in ("tf32", "bf16"):
+        assert torch.equal(lib.project_sum(U, V, Zt, c, math=m).data, ref)
