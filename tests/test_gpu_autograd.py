@@ -22,14 +22,15 @@ def _host_cores(lib, data, like):
 
 
 def _fd(f, data, direction, h):
+    """Five-point central difference (truncation O(h^4)) of t -> f(data + t direction) at 0."""
     with torch.no_grad():
-        fp = float(f(data + h * direction))
-        fm = float(f(data - h * direction))
-    return (fp - fm) / (2 * h)
+        v = [float(f(data + t * h * direction)) for t in (-2, -1, 1, 2)]
+    return (v[0] - 8 * v[1] + 8 * v[2] - v[3]) / (12 * h)
 
 
 def test_completion_loss_autograd(lib):
     from paper_1801_01928_gb300 import autograd as AG
+    torch.manual_seed(500)
     rng = np.random.default_rng(500)
     n, r = [4, 3, 5, 3, 4], [1, 3, 4, 4, 2, 1]
     X = round32(S.random_tt(rng, 1, n, r, 0.6))
@@ -50,7 +51,7 @@ def test_completion_loss_autograd(lib):
     # central differences of the CUDA forward along a random direction
     D = torch.randn_like(Xt.data)
     f = lambda d: AG.completion_loss(lib.TT(d, Xt.n, Xt.ranks, 1), idx_d, y_d)
-    fd = _fd(f, Xt.data.detach(), D, 1e-3)
+    fd = _fd(f, Xt.data.detach(), D, 1e-2)
     ad = float((Xt.data.grad.double() * D.double()).sum()) / 3.0
     assert abs(fd - ad) / abs(ad) < 1e-3
 
@@ -70,6 +71,7 @@ def test_completion_loss_no_grad_matches(lib):
 @pytest.mark.parametrize("same", [False, True])
 def test_gram_autograd(lib, same):
     from paper_1801_01928_gb300 import autograd as AG
+    torch.manual_seed(501)
     rng = np.random.default_rng(501)
     n = [3, 4, 2, 5]
     A = round32(S.random_tt(rng, 7, n, [1, 3, 5, 2, 1], 0.5))
@@ -92,22 +94,23 @@ def test_gram_autograd(lib, same):
         assert rel_err_cores(_host_cores(lib, At.data.grad, At), batched(dA)) < TOL["fp32"]
         assert rel_err_cores(_host_cores(lib, Bt.data.grad, Bt), batched(dB)) < TOL["fp32"]
     # full(A) is multilinear in A's cores, so f is a polynomial of degree d (2d for B = A)
-    # along DA: a small step keeps the O(h^2) truncation far below the tolerance
+    # along DA; the five-point difference keeps its truncation far below the tolerance
     DA = torch.randn_like(At.data)
     if same:
         f = lambda d: (AG.gram(lib.TT(d, At.n, At.ranks, At.batch), lib.TT(d, At.n, At.ranks, At.batch)).double()
                        * W.double()).sum()
-        fd = _fd(f, At.data.detach(), DA, 1e-3)
+        fd = _fd(f, At.data.detach(), DA, 1e-2)
         ad = float((At.data.grad.double() * DA.double()).sum())
     else:
         f = lambda d: (AG.gram(lib.TT(d, At.n, At.ranks, At.batch), Bt).double() * W.double()).sum()
-        fd = _fd(f, At.data.detach(), DA, 1e-3)
+        fd = _fd(f, At.data.detach(), DA, 1e-2)
         ad = float((At.data.grad.double() * DA.double()).sum())
     assert abs(fd - ad) / abs(ad) < 1e-3
 
 
 def test_project_sum_autograd(lib):
     from paper_1801_01928_gb300 import autograd as AG
+    torch.manual_seed(502)
     cfg = S.config5(batch=23, d=5, n=4, rX=5, rZ=3, seed=502)
     X, Z = round32(cfg.X), round32(cfg.Z)
     c = cfg.c.astype(np.float32)
@@ -130,6 +133,6 @@ def test_project_sum_autograd(lib):
     DZ = torch.randn_like(Zt.data)
     f = lambda d: (AG.project_sum(U, V, lib.TT(d, Zt.n, Zt.ranks, Zt.batch), ct.detach()).data.double()
                    * Rbar.double()).sum()
-    fd = _fd(f, Zt.data.detach(), DZ, 1e-3)
+    fd = _fd(f, Zt.data.detach(), DZ, 1e-2)
     ad = float((Zt.data.grad.double() * DZ.double()).sum())
     assert abs(fd - ad) / abs(ad) < 1e-3
