@@ -190,16 +190,21 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
     // ---------------- left sweep: M at every interface into the CTA scratch ------------
     // scratch layout per interface j: [a][al][b][be]
     for (int e = tid; e < P * PS; e += nth) {
-      const int be = e % RB, b = (e / RB) % nb, al = (e / (RB * nb)) % RA;
-      Rm[e] = (al == 0 && be == 0) ? 1.0f : 0.0f;  // Rm holds M during the left sweep
-      scr[e] = Rm[e];
-      (void)b;
+      const int be = e % RB, b = (e / RB) % nb, al = (e / (RB * nb)) % RA, a = e / (RB * nb * RA);
+      const float v = (al == 0 && be == 0) ? 1.0f : 0.0f;
+      scr[e] = v;  // M_0 of every pair
+      MT[(((size_t)b * RB + be) * na + a) * RA + al] = v;  // MT holds M^T during the left sweep
     }
     {
       int k = 0, i = 0, cur = 0;
       stage(0, 0, Sg, 0);
       float acc[2][4][4];
       const int nblk = na * QA * nb * QB;
+      // with at most half as many 4 x 4 blocks as threads, two threads share a block and split
+      // its K range (T: be, M': al); their partial sums of M' are combined at the end of a core
+      const int ks = 2 * nblk <= nth ? 2 : 1;
+      const int hb = tid / nblk, bb = tid % nblk;  // split mode: half and block of this thread
+      float* T1 = Xm;                                // second half of T in split mode
       while (k < d) {
         const int nk = nmode(k);
         if (i == 0) {
@@ -224,53 +229,95 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         __syncthreads();
         const float* As = Sg + cur * szS;  // [a][al][ap]
         const float* Bs = As + szA;        // [b][be][bp]
-        // T[a][al][b][bp] = sum_be M[a][al][b][be] B[b][be][bp]  (T in RT's storage)
-        for (int blk = tid; blk < nblk; blk += nth) {
+        // T[a][al][b][bp] = sum_be M[a][al][b][be] B[b][be][bp]  (T in RT's storage; in split
+        // mode the second half of the be range goes to T1)
+        for (int blk = ks == 2 ? bb : tid; blk < nblk && hb < ks; blk += (ks == 2 ? nblk : nth)) {
           const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+          const int be0 = ks == 2 ? hb * (RB / 2) : 0, be1 = ks == 2 ? be0 + RB / 2 : RB;
           float t4[4][4];
 #pragma unroll
           for (int x = 0; x < 4; ++x)
 #pragma unroll
             for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
-          for (int be = 0; be < RB; ++be) {
-            float4 mv;
-            mv.x = Rm[(((size_t)a * RA + 4 * qa + 0) * nb + b) * RB + be];
-            mv.y = Rm[(((size_t)a * RA + 4 * qa + 1) * nb + b) * RB + be];
-            mv.z = Rm[(((size_t)a * RA + 4 * qa + 2) * nb + b) * RB + be];
-            mv.w = Rm[(((size_t)a * RA + 4 * qa + 3) * nb + b) * RB + be];
-            fma44b(t4, mv, *reinterpret_cast<const float4*>(Bs + ((size_t)b * RB + be) * RB + 4 * qb));
-          }
+          const float* mt = MT + ((size_t)b * RB * na + a) * RA + 4 * qa;  // + be * na * RA
+          for (int be = be0; be < be1; ++be)
+            fma44b(t4, *reinterpret_cast<const float4*>(mt + (size_t)be * na * RA),
+                   *reinterpret_cast<const float4*>(Bs + ((size_t)b * RB + be) * RB + 4 * qb));
+          float* tdst = (ks == 2 && hb == 1) ? T1 : RT;
 #pragma unroll
           for (int x = 0; x < 4; ++x)
-            *reinterpret_cast<float4*>(RT + (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb) =
+            *reinterpret_cast<float4*>(tdst + (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb) =
                 make_float4(t4[x][0], t4[x][1], t4[x][2], t4[x][3]);
+          if (ks == 2) break;
         }
         __syncthreads();
         // M'[a][ap][b][bp] += sum_al A[a][al][ap] T[a][al][b][bp]
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int blk = tid + q * nth;
-          if (blk < nblk) {
+        if (ks == 2) {
+          if (hb < 2) {
+            const int blk = bb;
             const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
-            for (int al = 0; al < RA; ++al)
-              fma44b(acc[q], *reinterpret_cast<const float4*>(As + ((size_t)a * RA + al) * RA + 4 * qa),
-                     *reinterpret_cast<const float4*>(RT + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb));
+            const int al0 = hb * (RA / 2), al1 = al0 + RA / 2;
+            for (int al = al0; al < al1; ++al) {
+              const size_t o = (((size_t)a * RA + al) * nb + b) * RB + 4 * qb;
+              const float4 t0 = *reinterpret_cast<const float4*>(RT + o);
+              const float4 t1 = *reinterpret_cast<const float4*>(T1 + o);
+              fma44b(acc[0], *reinterpret_cast<const float4*>(As + ((size_t)a * RA + al) * RA + 4 * qa),
+                     make_float4(t0.x + t1.x, t0.y + t1.y, t0.z + t1.z, t0.w + t1.w));
+            }
           }
-        }
-        __syncthreads();
-        cur ^= 1;
-        if (++i >= nk) {
+        } else {
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             const int blk = tid + q * nth;
             if (blk < nblk) {
               const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+              for (int al = 0; al < RA; ++al)
+                fma44b(acc[q], *reinterpret_cast<const float4*>(As + ((size_t)a * RA + al) * RA + 4 * qa),
+                       *reinterpret_cast<const float4*>(RT + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb));
+            }
+          }
+        }
+        __syncthreads();
+        cur ^= 1;
+        if (++i >= nk) {
+          // split mode: the second halves hand their partial sums to the first halves
+          if (ks == 2) {
+            if (hb == 1) {
+              const int qb = bb % QB, b = (bb / QB) % nb, qa = (bb / (QB * nb)) % QA, a = bb / (QB * nb * QA);
+#pragma unroll
+              for (int x = 0; x < 4; ++x)
+                *reinterpret_cast<float4*>(Ym + (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb) =
+                    make_float4(acc[0][x][0], acc[0][x][1], acc[0][x][2], acc[0][x][3]);
+            }
+            __syncthreads();
+            if (hb == 0) {
+              const int qb = bb % QB, b = (bb / QB) % nb, qa = (bb / (QB * nb)) % QA, a = bb / (QB * nb * QA);
 #pragma unroll
               for (int x = 0; x < 4; ++x) {
-                const size_t o = (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb;
+                const float4 v = *reinterpret_cast<const float4*>(Ym + (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb);
+                acc[0][x][0] += v.x;
+                acc[0][x][1] += v.y;
+                acc[0][x][2] += v.z;
+                acc[0][x][3] += v.w;
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int blk = ks == 2 ? (q == 0 && hb == 0 ? bb : nblk) : tid + q * nth;
+            if (blk < nblk) {
+              const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+#pragma unroll
+              for (int x = 0; x < 4; ++x) {
+                const int al = 4 * qa + x;
+                const size_t o = (((size_t)a * RA + al) * nb + b) * RB + 4 * qb;
                 const float4 v = make_float4(acc[q][x][0], acc[q][x][1], acc[q][x][2], acc[q][x][3]);
-                *reinterpret_cast<float4*>(Rm + o) = v;
                 *reinterpret_cast<float4*>(scr + (size_t)(k + 1) * P * PS + o) = v;
+                const size_t ot = (((size_t)b * RB + 4 * qb) * na + a) * RA + al;  // M^T for the next core
+                MT[ot] = v.x;
+                MT[ot + (size_t)na * RA] = v.y;
+                MT[ot + (size_t)2 * na * RA] = v.z;
+                MT[ot + (size_t)3 * na * RA] = v.w;
               }
             }
           }
@@ -299,6 +346,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         MT[(((size_t)b * RB + be) * na + a) * RA + al] = v;
       }
       float racc[2][4][4];
+      const int nr = na * QA * nb * QB;
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -355,7 +403,6 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         }
         __syncthreads();
         // (2) R'[a][al][b][be] += sum_bp X[al][bp] B[be][bp]
-        const int nr = na * QA * nb * QB;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int blk = tid + q * nth;
@@ -421,7 +468,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int blk = tid + q * nth;
-        if (blk < na * QA * nb * QB) {
+        if (blk < nr) {
           const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
 #pragma unroll
           for (int x = 0; x < 4; ++x) {
