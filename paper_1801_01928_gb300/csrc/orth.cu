@@ -111,25 +111,32 @@ __device__ void qr_step(const OrthArgs& a, double* base, Dims* dims, int k, int 
       for (int l = j + tid; l < c; l += nth) rowj[l] = s.W[(j - row0) * c + l];
     __syncthreads();
     cluster.sync();
-    // (2) gather the cluster sums (16 lanes per column, one per rank); the lane that owns
-    //     column j also forms the reflector (LAPACK dlarfg convention)
+    // (2) gather the cluster sums (8 lanes per column, each reading the partials of ranks g
+    //     and g + 8 in one round trip); the lane that owns column j also forms the reflector
+    //     (LAPACK dlarfg convention: beta = -sign(w) |x|, tau = (beta - w) / beta,
+    //     scale = 1 / (w - beta), with 1 / |x| from one reciprocal square root)
     const int jown = j / rp;
-    const int ng = ((c - j) * 16 + 31) & ~31;  // whole warps take part in the shuffles
+    const int ng = ((c - j) * 8 + 31) & ~31;  // whole warps take part in the shuffles
     for (int e = tid; e < ng; e += nth) {
-      const int l = j + e / 16, p = e % 16;
-      double v = 0.0, wl = 0.0;
-      if (p < P && l < c) v = cluster.map_shared_rank(pub, p)[l];
-      if (p == 0 && l < c) wl = cluster.map_shared_rank(rowj, jown)[l];  // issued with v
-      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
+      const int l = j + e / 8, p = e % 8;
+      double v = 0.0, v2 = 0.0, wl = 0.0;
+      if (l < c) {
+        if (p < P) v = cluster.map_shared_rank(pub, p)[l];
+        if (p + 8 < P) v2 = cluster.map_shared_rank(pub, p + 8)[l];
+        if (p == 0) wl = cluster.map_shared_rank(rowj, jown)[l];  // issued with v
+      }
+      v += v2;
+      for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 8);
       if (p == 0 && l < c) {
         s.gsum[l] = v;
         s.wj[l] = wl;
         if (l == j) {
           double beta = wl, tau = 0.0, scale = 0.0;
           if (v != 0.0) {
-            const double nrm = sqrt(wl * wl + v);
-            beta = wl >= 0.0 ? -nrm : nrm;
-            tau = (beta - wl) / beta;
+            const double x2 = wl * wl + v, rn = rsqrt(x2), nrm = x2 * rn;
+            const bool pos = wl >= 0.0;
+            beta = pos ? -nrm : nrm;
+            tau = pos ? 1.0 + wl * rn : 1.0 - wl * rn;  // 1 - wl / beta
             scale = 1.0 / (wl - beta);
           }
           s.refl[0] = beta;
@@ -199,23 +206,24 @@ __device__ void qr_step(const OrthArgs& a, double* base, Dims* dims, int k, int 
         const int l = g + 8 * u;
         x[u] = (qv && l < kk) ? qr[l] : 0.0;
       }
-      for (int b = 0; b < kk; ++b) {
-        const int ob = b % 8, ub = b / 8;
-        double xb = 0.0;
+      const int uend = (kk + 7) / 8;  // register slots holding columns < kk
+      // column b = 8 UB + ob lives in slot UB of lane ob; only the slots UB .. uend-1 hold
+      // columns l > b, so the loops start at UB at compile time and no update is issued
+      // for the slots below it (the FP64 pipe is the scarce one)
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (u == ub) xb = x[u];
-        xb = __shfl_sync(0xffffffffu, xb * s.rinv[b], ob, 8);
-        if (g == ob) {
+      for (int UB = 0; UB < 8; ++UB) {
+        if (UB >= uend) break;
+        for (int ob = 0; ob < 8; ++ob) {
+          const int b = 8 * UB + ob;
+          if (b >= kk) break;
+          double xb = __shfl_sync(0xffffffffu, x[UB] * s.rinv[b], ob, 8);
+          if (g == ob) x[UB] = xb;
+          const double* rb = s.Rs + b * T3F_MAX_RANK;
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (u == ub) x[u] = xb;
-        }
-        const double* rb = s.Rs + b * T3F_MAX_RANK;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int l = g + 8 * u;
-          if (l > b && l < kk) x[u] = fma(-xb, rb[l], x[u]);
+          for (int u = UB; u < 8; ++u) {
+            const int l = g + 8 * u;
+            if (u < uend && l > b && l < kk) x[u] = fma(-xb, rb[l], x[u]);
+          }
         }
       }
       if (qv) {
