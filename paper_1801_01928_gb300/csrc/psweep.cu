@@ -45,7 +45,21 @@ __device__ __forceinline__ void fma4x4(float (&acc)[4][4], const float4 a, const
 }
 
 // stage slice i of an X-side core (r0 x n x r1) as [K][m] (left: K = row, m = col;
-// right: K = col, m = row), zero-padded to RU x RU
+// right: K = col, m = row), zero-padded to RU x RU, with 4-byte asynchronous copies (the
+// elements outside the ranks are zero-filled); the caller commits and waits
+template <int RU>
+__device__ __forceinline__ void stage_x_slice_async(float* dst, const float* core, int r0, int n, int r1, int i,
+                                                    int dir, bool valid) {
+  for (int e = threadIdx.x; e < RU * RU; e += blockDim.x) {
+    const int K = e / RU, m = e % RU;
+    const int row = dir == 0 ? K : m, col = dir == 0 ? m : K;
+    const bool ok = valid && row < r0 && col < r1;
+    const float* src = ok ? core + ((long long)row * n + i) * r1 + col : core;
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + e);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(ok ? 4 : 0));
+  }
+}
+
 template <int RU>
 __device__ __forceinline__ void stage_x_slice(float* dst, const float* core, int r0, int n, int r1, int i,
                                               int dir, bool valid) {
@@ -73,8 +87,8 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
   const int obj = blockIdx.x * J + ol;
   const bool valid = obj < Z.batch;
   constexpr int NX = MIXED ? 3 : 1;
-  float* Xs = sm;                                  // [NX][SP][RU][RU]
-  float* Zc = Xs + (size_t)NX * SP * RU * RU;      // [J][8][nmax][8]
+  float* Xs = sm;                                  // [2][NX][SP][RU][RU] (double-buffered)
+  float* Zc = Xs + (size_t)2 * NX * SP * RU * RU;  // [J][8][nmax][8]
   float* C1 = Zc + (size_t)J * kRZ * nmax * kRZ;   // [J][8][RU]  (Cur transposed)
   float* C2 = C1 + (size_t)J * TS;                 // mixed only
   float* T1 = C2 + (MIXED ? (size_t)J * TS : 0);   // [J][SP][RU][8]
@@ -93,6 +107,24 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
       if (MIXED) a.st2[a.ioff[j0] + obj] = 0.0f;
     }
   }
+  // X slices of batch ib of core k (sweep step st) into buffer buf, one commit group
+  auto issue_batch = [&](int st, int ib, int buf) {
+    const int kx = a.dir == 0 ? st : d - 1 - st;
+    const int xr0 = a.ra[kx], xr1 = a.ra[kx + 1], xn = Z.n[kx];
+    float* X0 = Xs + (size_t)buf * NX * SP * RU * RU;
+    for (int hh = 0; hh < SP; ++hh) {
+      const int i = ib * SP + hh;
+      stage_x_slice_async<RU>(X0 + (size_t)hh * RU * RU, a.A + a.Aoff[kx], xr0, xn, xr1, i, a.dir, i < xn);
+      if (MIXED) {
+        stage_x_slice_async<RU>(X0 + (size_t)(SP + hh) * RU * RU, a.B1 + a.B1off[kx], xr0, xn, xr1, i, a.dir, i < xn);
+        stage_x_slice_async<RU>(X0 + (size_t)(2 * SP + hh) * RU * RU, a.B2 + a.B2off[kx], xr0, xn, xr1, i, a.dir,
+                                i < xn);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  int bt = 0;  // running batch index: buffer bt & 1
+  issue_batch(0, 0, 0);
   for (int s = 0; s < d; ++s) {
     const int k = a.dir == 0 ? s : d - 1 - s;
     const int r0 = a.ra[k], r1 = a.ra[k + 1], z0 = Z.r[k], z1 = Z.r[k + 1], n = Z.n[k];
@@ -114,17 +146,20 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
         acc1[x][y] = 0.0f;
         acc2[x][y] = 0.0f;
       }
-    for (int ib = 0; ib * SP < n; ++ib) {
-      __syncthreads();
-      for (int hh = 0; hh < SP; ++hh) {
-        const int i = ib * SP + hh;
-        stage_x_slice<RU>(Xs + (size_t)hh * RU * RU, a.A + a.Aoff[k], r0, n, r1, i, a.dir, i < n);
-        if (MIXED) {
-          stage_x_slice<RU>(Xs + (size_t)(SP + hh) * RU * RU, a.B1 + a.B1off[k], r0, n, r1, i, a.dir, i < n);
-          stage_x_slice<RU>(Xs + (size_t)(2 * SP + hh) * RU * RU, a.B2 + a.B2off[k], r0, n, r1, i, a.dir, i < n);
+    for (int ib = 0; ib * SP < n; ++ib, ++bt) {
+      __syncthreads();  // the other buffer's batch has been consumed
+      {
+        int s2 = s, ib2 = ib + 1;
+        if (ib2 * SP >= n) { ++s2; ib2 = 0; }
+        if (s2 < d) {
+          issue_batch(s2, ib2, (bt + 1) & 1);
+          asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+          asm volatile("cp.async.wait_group 0;\n" ::);
         }
       }
       __syncthreads();
+      float* const XsB = Xs + (size_t)(bt & 1) * NX * SP * RU * RU;
       const int i = ib * SP + h;
       // T-step: T[m][b] = sum_K CurT[K][m] Zs[K][b]
       if (i < n) {
@@ -160,10 +195,10 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
       __syncthreads();
       // accumulate step: Next[m][b] += sum_K As[K][m] T[K][b]
       if (i < n) {
-        const float* As = Xs + (size_t)h * RU * RU;
+        const float* As = XsB + (size_t)h * RU * RU;
         const float* tb1 = T1 + ((size_t)ol * SP + h) * TS;
-        const float* Bs1 = Xs + (size_t)(SP + h) * RU * RU;
-        const float* Bs2 = Xs + (size_t)(2 * SP + h) * RU * RU;
+        const float* Bs1 = XsB + (size_t)(SP + h) * RU * RU;
+        const float* Bs2 = XsB + (size_t)(2 * SP + h) * RU * RU;
         const float* tb2 = T2 + ((size_t)ol * SP + h) * TS;
 #pragma unroll 4
         for (int K = 0; K < RU; ++K) {
@@ -488,7 +523,7 @@ static void plan_tiles(int RU, int batch, int* J, int* SP) {
 
 static size_t psweep_smem(int RU, bool mixed, int J, int SP, int nmax) {
   const size_t TS = (size_t)RU * kRZ;
-  size_t f = (size_t)(mixed ? 3 : 1) * SP * RU * RU + (size_t)J * kRZ * nmax * kRZ + (size_t)J * TS * (mixed ? 2 : 1) +
+  size_t f = (size_t)2 * (mixed ? 3 : 1) * SP * RU * RU + (size_t)J * kRZ * nmax * kRZ + (size_t)J * TS * (mixed ? 2 : 1) +
              (size_t)J * SP * TS * (mixed ? 2 : 1);
   return f * sizeof(float);
 }
