@@ -60,18 +60,6 @@ __device__ __forceinline__ void stage_x_slice_async(float* dst, const float* cor
   }
 }
 
-template <int RU>
-__device__ __forceinline__ void stage_x_slice(float* dst, const float* core, int r0, int n, int r1, int i,
-                                              int dir, bool valid) {
-  for (int e = threadIdx.x; e < RU * RU; e += blockDim.x) {
-    const int K = e / RU, m = e % RU;
-    const int row = dir == 0 ? K : m, col = dir == 0 ? m : K;
-    float v = 0.0f;
-    if (valid && row < r0 && col < r1) v = __ldg(core + ((long long)row * n + i) * r1 + col);
-    dst[e] = v;
-  }
-}
-
 template <int RU, bool MIXED>
 __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepArgs a) {
   extern __shared__ __align__(16) float sm[];
@@ -389,7 +377,7 @@ struct PGradFastArgs {
 };
 
 template <int RU>
-__global__ void __launch_bounds__(512) k_pgrad(const __grid_constant__ PGradFastArgs a) {
+__global__ void __launch_bounds__(256) k_pgrad(const __grid_constant__ PGradFastArgs a) {
   extern __shared__ __align__(16) float sm[];
   constexpr int QB = kRZ / 4, G = (RU / 4) * QB, TS = RU * kRZ;
   const TTV& Z = a.Z;
@@ -420,15 +408,20 @@ __global__ void __launch_bounds__(512) k_pgrad(const __grid_constant__ PGradFast
   }
   const float cj = valid ? a.c[obj] : 0.0f;
   float* outb = valid ? a.dZ + core_base(Z, k, obj) : nullptr;
-  for (int ib = 0; ib * SP < n; ++ib) {
-    __syncthreads();
+  // slices of batch ib, right-style (As[K][m] = X_k[m][i][K]), as one commit group; the next
+  // batch is issued once the current one has been consumed, so its copies overlap the dZ step
+  auto issue_batch = [&](int ib) {
     for (int hh = 0; hh < SP; ++hh) {
       const int i = ib * SP + hh;
-      // right-style staging: As[K][m] = X_k[m][i][K]
-      stage_x_slice<RU>(Xs + (size_t)(0 * SP + hh) * RU * RU, a.V + a.Xoff[k], r0, n, r1, i, 1, i < n);
-      stage_x_slice<RU>(Xs + (size_t)(1 * SP + hh) * RU * RU, a.W + a.Xoff[k], r0, n, r1, i, 1, i < n);
-      stage_x_slice<RU>(Xs + (size_t)(2 * SP + hh) * RU * RU, a.U + a.Xoff[k], r0, n, r1, i, 1, i < n);
+      stage_x_slice_async<RU>(Xs + (size_t)(0 * SP + hh) * RU * RU, a.V + a.Xoff[k], r0, n, r1, i, 1, i < n);
+      stage_x_slice_async<RU>(Xs + (size_t)(1 * SP + hh) * RU * RU, a.W + a.Xoff[k], r0, n, r1, i, 1, i < n);
+      stage_x_slice_async<RU>(Xs + (size_t)(2 * SP + hh) * RU * RU, a.U + a.Xoff[k], r0, n, r1, i, 1, i < n);
     }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  issue_batch(0);
+  for (int ib = 0; ib * SP < n; ++ib) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     const int i = ib * SP + h;
     if (i < n) {
@@ -461,6 +454,7 @@ __global__ void __launch_bounds__(512) k_pgrad(const __grid_constant__ PGradFast
       }
     }
     __syncthreads();
+    if ((ib + 1) * SP < n) issue_batch(ib + 1);
     // dZ_i[beta][b] = c_j sum_m (P[m][beta] X1[m][b] + L[m][beta] X2[m][b]); G threads per
     // (object, slice) cover the 8 x 8 block as 16 rows-of-4
     if (i < n && valid) {
@@ -622,11 +616,11 @@ template <int RU>
 static t3f_status launch_pgrad_t(PGradFastArgs& a, cudaStream_t s) {
   const size_t TS = (size_t)RU * kRZ;
   const size_t smem = sizeof(float) * ((size_t)3 * a.SPLIT * RU * RU + (size_t)a.J * 4 * TS + (size_t)a.J * a.SPLIT * 2 * TS);
-  if (smem > 227 * 1024) return T3F_ERR_UNSUPPORTED;
+  const int G = (RU / 4) * (kRZ / 4);
+  if (smem > 227 * 1024 || a.J * a.SPLIT * G > 256) return T3F_ERR_UNSUPPORTED;
   auto kern = k_pgrad<RU>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return T3F_ERR_CUDA;
-  const int G = (RU / 4) * (kRZ / 4);
   kern<<<(unsigned)(a.ntiles * a.Z.d), a.J * a.SPLIT * G, smem, s>>>(a);
   return launch_status();
 }
