@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
     float* Mm = RT + P * PS;             // [a][al][b][be] g * M   (K rows (a, al) for dB)
     float* MT = Mm + P * PS;             // [b][be][a][al] M       (K rows (b, be) for dA)
     float* Xm = MT + P * PS;             // [a][al][b][bp] X       (K rows (a, al) for dB)
-    float* XT = Xm + P * PS;             // [p][bp][al]    X^T     (K rows bp for R')
+    float* XT = Xm + P * PS;             // [p][bp][al]    X^T     (K rows bp for R'; the 4-float
+                                         // column chunk c of row bp sits at chunk (c + bp/4) mod RA/4)
     float* Ym = XT + P * PS;             // [b][be][a][ap] g Y     (K rows (b, be) for dA)
     float* Sg = Ym + P * PS;             // staging: [2][AT (na RA RA) + BT (nb RB RB)]
     const int szA = na * RA * RA, szS = szA + nb * RB * RB;
@@ -309,16 +310,14 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
               const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
 #pragma unroll
               for (int x = 0; x < 4; ++x) {
-                const int al = 4 * qa + x;
-                const size_t o = (((size_t)a * RA + al) * nb + b) * RB + 4 * qb;
-                const float4 v = make_float4(acc[q][x][0], acc[q][x][1], acc[q][x][2], acc[q][x][3]);
-                *reinterpret_cast<float4*>(scr + (size_t)(k + 1) * P * PS + o) = v;
-                const size_t ot = (((size_t)b * RB + 4 * qb) * na + a) * RA + al;  // M^T for the next core
-                MT[ot] = v.x;
-                MT[ot + (size_t)na * RA] = v.y;
-                MT[ot + (size_t)2 * na * RA] = v.z;
-                MT[ot + (size_t)3 * na * RA] = v.w;
+                const size_t o = (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb;
+                *reinterpret_cast<float4*>(scr + (size_t)(k + 1) * P * PS + o) =
+                    make_float4(acc[q][x][0], acc[q][x][1], acc[q][x][2], acc[q][x][3]);
               }
+#pragma unroll
+              for (int y = 0; y < 4; ++y)  // M^T for the next core
+                *reinterpret_cast<float4*>(MT + (((size_t)b * RB + 4 * qb + y) * na + a) * RA + 4 * qa) =
+                    make_float4(acc[q][0][y], acc[q][1][y], acc[q][2][y], acc[q][3][y]);
             }
           }
           if (k + 2 < d) fill_info(k + 2, k & 1);  // core k's slices are all staged
@@ -380,13 +379,16 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             for (int ap = 0; ap < RA; ++ap)
               fma44b(t4, *reinterpret_cast<const float4*>(at + ap * RA), *reinterpret_cast<const float4*>(rr + ap * RB));
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
-              const int al = 4 * qa + x;
-              *reinterpret_cast<float4*>(Xm + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb) =
+            for (int x = 0; x < 4; ++x)
+              *reinterpret_cast<float4*>(Xm + (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb) =
                   make_float4(t4[x][0], t4[x][1], t4[x][2], t4[x][3]);
+            // X^T rows 4qb..4qb+3: chunk qa rotated by qb spreads a warp's stores over the banks
+            int cx = qa + qb;
+            while (cx >= QA) cx -= QA;
 #pragma unroll
-              for (int y = 0; y < 4; ++y) XT[((size_t)(a * nb + b) * RB + 4 * qb + y) * RA + al] = t4[x][y];
-            }
+            for (int y = 0; y < 4; ++y)
+              *reinterpret_cast<float4*>(XT + ((size_t)(a * nb + b) * RB + 4 * qb + y) * RA + 4 * cx) =
+                  make_float4(t4[0][y], t4[1][y], t4[2][y], t4[3][y]);
           } else {
             const int bl = blk - nx;
             const int qa = bl % QA, a = (bl / QA) % na, qb = (bl / (QA * na)) % QB, b = bl / (QA * na * QB);
@@ -408,10 +410,18 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           const int blk = tid + q * nth;
           if (blk < nr) {
             const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
-            const float* xt = XT + (size_t)(a * nb + b) * PS + 4 * qa;  // + bp * RA
-            const float* bt = BT + (size_t)b * RB * RB + 4 * qb;        // + bp * RB
-            for (int bp = 0; bp < RB; ++bp)
-              fma44b(racc[q], *reinterpret_cast<const float4*>(xt + bp * RA), *reinterpret_cast<const float4*>(bt + bp * RB));
+            const float* xt = XT + (size_t)(a * nb + b) * PS;     // + bp * RA + rotated chunk
+            const float* bt = BT + (size_t)b * RB * RB + 4 * qb;  // + bp * RB
+            int cx = qa;  // chunk of X^T column block qa in rows 4bq..4bq+3
+            for (int bq = 0; bq < QB; ++bq) {
+#pragma unroll
+              for (int y = 0; y < 4; ++y) {
+                const int bp = 4 * bq + y;
+                fma44b(racc[q], *reinterpret_cast<const float4*>(xt + bp * RA + 4 * cx),
+                       *reinterpret_cast<const float4*>(bt + bp * RB));
+              }
+              if (++cx == QA) cx = 0;
+            }
           }
         }
         // (3) dA_a,i[al][ap] = sum_{b,be} M[al][be] Y'[be][ap];  dB_b,i[be][bp] = sum_{a,al} gM[al][be] X[al][bp]
@@ -471,12 +481,13 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         if (blk < nr) {
           const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
 #pragma unroll
-          for (int x = 0; x < 4; ++x) {
+          for (int x = 0; x < 4; ++x)
             *reinterpret_cast<float4*>(Rm + (size_t)(a * nb + b) * PS + (4 * qa + x) * RB + 4 * qb) =
                 make_float4(racc[q][x][0], racc[q][x][1], racc[q][x][2], racc[q][x][3]);
 #pragma unroll
-            for (int y = 0; y < 4; ++y) RT[(size_t)(a * nb + b) * PS + (4 * qb + y) * RA + 4 * qa + x] = racc[q][x][y];
-          }
+          for (int y = 0; y < 4; ++y)
+            *reinterpret_cast<float4*>(RT + (size_t)(a * nb + b) * PS + (4 * qb + y) * RA + 4 * qa) =
+                make_float4(racc[q][0][y], racc[q][1][y], racc[q][2][y], racc[q][3][y]);
         }
       }
       if (k > 0) fill_info(k - 1, (k - 1) & 1);  // core k's slices are all staged

@@ -130,6 +130,37 @@ def test_gram_groups_config4_sampled(lib):
     assert rel_err(got, want) < TOL["fp32"]
 
 
+def test_gram_groups_config4_backward_sampled(lib):
+    # the full uneven batch (8 groups x 64 TTs, ranks up to 64) through the persistent adjoint;
+    # one sampled object per group (the highest rank and a random one alternately) against the
+    # oracle's cotangent of sum_ab dG_ab <X_a, X_b>: object a collects (dG_ab + dG_ba) times
+    # the derivative of <X_a, X_b> in its first argument
+    cfg = S.config4()
+    objs, gstart = [], [0]
+    for grp in cfg.groups:
+        objs += [round32(o) for o in grp.cores]
+        gstart.append(len(objs))
+    X = lib.RaggedTT.from_objects([[np.asarray(c, np.float32) for c in o] for o in objs])
+    ws = lib.gram_groups_prepare(X, gstart)
+    G, _ = lib.gram_groups(X, gstart, ws)
+    rng = np.random.default_rng(405)
+    dout = rng.normal(size=G.numel()).astype(np.float32)
+    dX = lib.gram_groups_backward(X, gstart, ws, torch.tensor(dout, device="cuda"))
+    view = lib.RaggedTT(dX, X.dims, X.modes, X.ranks, X.offsets)
+    off = 0
+    for g in range(len(gstart) - 1):
+        grp = objs[gstart[g]:gstart[g + 1]]
+        Sg = len(grp)
+        dG = dout[off:off + Sg * Sg].reshape(Sg, Sg).astype(np.float64)
+        off += Sg * Sg
+        ranks = [max(np.asarray(c).shape[0] for c in o) for o in grp]
+        a = int(np.argmax(ranks)) if g % 2 == 0 else int(rng.integers(0, Sg))
+        w = (dG[a, :] + dG[:, a])[None, :]
+        dA, _ = O.gram_vjp([grp[a]], grp, w)
+        got = [c.double().cpu().numpy() for c in view.object_cores(gstart[g] + a)]
+        assert rel_err_cores(got, dA[0]) < TOL["fp32"], (g, a)
+
+
 @pytest.mark.parametrize("math_", ["tf32", "bf16"])
 def test_gram_groups_tensor_cores(lib, math_):
     # every pair on the tensor cores in (128/RA) x (128/RB) tiles (RA, RB in 16/32/64 by rank
