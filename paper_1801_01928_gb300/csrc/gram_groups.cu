@@ -212,7 +212,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
               // a tile must fit one CTA of 512 threads: 2 blocks each, staging bounds
               if (na * (RA / 4) * nb * (RB / 4) > 1024) return T3F_ERR_UNSUPPORTED;
               const size_t sm = bwd ? gram_tile_bwd_smem(na, nb, RA, RB) : gram_tile_smem(na, nb, RA, RB);
-              if (sm > 200 * 1024) return T3F_ERR_UNSUPPORTED;
+              if (!bwd && sm > 200 * 1024) return T3F_ERR_UNSUPPORTED;
               if (bwd && !gram_tile_bwd_fits(na, nb, RA, RB)) return T3F_ERR_UNSUPPORTED;
               if (!bwd && na * RA * RA + nb * RB * RB > 512 * 16) return T3F_ERR_UNSUPPORTED;
               It it;
@@ -302,8 +302,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
     const int R = kBucketMax[b];
     int side = 1;
     for (int t = 2; t <= tl[b]; ++t)
-      if ((long long)t * t * (R / 4) * (R / 4) <= 1024 && gram_tile_bwd_smem(t, t, R, R) <= 200 * 1024 &&
-          gram_tile_bwd_fits(t, t, R, R))
+      if ((long long)t * t * (R / 4) * (R / 4) <= 1024 && gram_tile_bwd_fits(t, t, R, R))
         side = t;
     tlb[b] = side;
   }

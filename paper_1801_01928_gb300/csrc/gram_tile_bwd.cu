@@ -108,6 +108,14 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
     float* Sg = Ym + P * PS;             // staging: [2][AT (na RA RA) + BT (nb RB RB)]
     const int szA = na * RA * RA, szS = szA + nb * RB * RB;
     float* gsm = Sg + 2 * szS;           // [P] cotangents of the tile's pairs
+    // block decode tables (a | qa << 4 | b << 8 | qb << 12), filled once per tile so that the
+    // per-slice phases need no integer division: dP = pair-layout 4 x 4 blocks (qb fastest,
+    // then b, qa, a), dY = Y-layout blocks (qa fastest, then a, qb, b), d3 = gradient blocks
+    // (dA: a | qa << 4 | qp << 8, qp fastest; then dB: b | qb << 4 | qp << 8)
+    const int nblk = na * QA * nb * QB, nda = na * QA * QA, ndb = nb * QB * QB;
+    int* dP = reinterpret_cast<int*>(gsm + P);
+    int* dY = dP + nblk;
+    int* d3 = dY + nblk;
     // per-object access
     auto objX = [&](int side, int t, int k, long long* base, int* r0, int* r1, int* n) {
       if (g.mode == 0) {
@@ -140,6 +148,24 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         if (sym) v += o[(long long)lb * S + la];
       }
       gsm[p] = v;
+    }
+    for (int j = tid; j < nblk; j += nth) {
+      {
+        const int qb = j % QB, b = (j / QB) % nb, qa = (j / (QB * nb)) % QA, a = j / (QB * nb * QA);
+        dP[j] = a | qa << 4 | b << 8 | qb << 12;
+      }
+      {
+        const int qa = j % QA, a = (j / QA) % na, qb = (j / (QA * na)) % QB, b = j / (QA * na * QB);
+        dY[j] = a | qa << 4 | b << 8 | qb << 12;
+      }
+    }
+    for (int j = tid; j < nda + ndb; j += nth) {
+      if (j < nda) {
+        d3[j] = j / (QA * QA) | ((j / QA) % QA) << 4 | (j % QA) << 8;
+      } else {
+        const int bl = j - nda;
+        d3[j] = bl / (QB * QB) | ((bl / QB) % QB) << 4 | (bl % QB) << 8;
+      }
     }
     // core offsets and ranks of the tile's objects for core k into parity slot par; the
     // slots are filled ahead of use and published by the barrier that ends a core
@@ -200,7 +226,6 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
       int k = 0, i = 0, cur = 0;
       stage(0, 0, Sg, 0);
       float acc[2][4][4];
-      const int nblk = na * QA * nb * QB;
       // with at most half as many 4 x 4 blocks as threads, two threads share a block and split
       // its K range (T: be, M': al); their partial sums of M' are combined at the end of a core
       const int ks = 2 * nblk <= nth ? 2 : 1;
@@ -233,7 +258,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         // T[a][al][b][bp] = sum_be M[a][al][b][be] B[b][be][bp]  (T in RT's storage; in split
         // mode the second half of the be range goes to T1)
         for (int blk = ks == 2 ? bb : tid; blk < nblk && hb < ks; blk += (ks == 2 ? nblk : nth)) {
-          const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+          const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
           const int be0 = ks == 2 ? hb * (RB / 2) : 0, be1 = ks == 2 ? be0 + RB / 2 : RB;
           float t4[4][4];
 #pragma unroll
@@ -256,7 +281,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         if (ks == 2) {
           if (hb < 2) {
             const int blk = bb;
-            const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+            const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
             const int al0 = hb * (RA / 2), al1 = al0 + RA / 2;
             for (int al = al0; al < al1; ++al) {
               const size_t o = (((size_t)a * RA + al) * nb + b) * RB + 4 * qb;
@@ -271,7 +296,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           for (int q = 0; q < 2; ++q) {
             const int blk = tid + q * nth;
             if (blk < nblk) {
-              const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+              const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
               for (int al = 0; al < RA; ++al)
                 fma44b(acc[q], *reinterpret_cast<const float4*>(As + ((size_t)a * RA + al) * RA + 4 * qa),
                        *reinterpret_cast<const float4*>(RT + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb));
@@ -284,7 +309,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           // split mode: the second halves hand their partial sums to the first halves
           if (ks == 2) {
             if (hb == 1) {
-              const int qb = bb % QB, b = (bb / QB) % nb, qa = (bb / (QB * nb)) % QA, a = bb / (QB * nb * QA);
+              const int dv = dP[bb], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
 #pragma unroll
               for (int x = 0; x < 4; ++x)
                 *reinterpret_cast<float4*>(Ym + (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb) =
@@ -292,7 +317,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             }
             __syncthreads();
             if (hb == 0) {
-              const int qb = bb % QB, b = (bb / QB) % nb, qa = (bb / (QB * nb)) % QA, a = bb / (QB * nb * QA);
+              const int dv = dP[bb], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
 #pragma unroll
               for (int x = 0; x < 4; ++x) {
                 const float4 v = *reinterpret_cast<const float4*>(Ym + (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb);
@@ -307,7 +332,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           for (int q = 0; q < 2; ++q) {
             const int blk = ks == 2 ? (q == 0 && hb == 0 ? bb : nblk) : tid + q * nth;
             if (blk < nblk) {
-              const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+              const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
 #pragma unroll
               for (int x = 0; x < 4; ++x) {
                 const size_t o = (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb;
@@ -337,12 +362,23 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
     }
     for (int k = d - 1; k >= 0; --k) {
       const int nk = nmode(k);
-      // M at interface k: Mm = g M in [a][al][b][be], MT = M in [b][be][a][al]
-      for (int e = tid; e < P * PS; e += nth) {
-        const int be = e % RB, b = (e / RB) % nb, al = (e / (RB * nb)) % RA, a = e / (RB * nb * RA);
-        const float v = scr[(size_t)k * P * PS + e];
-        Mm[e] = gsm[a * nb + b] * v;
-        MT[(((size_t)b * RB + be) * na + a) * RA + al] = v;
+      // M at interface k, one 4 x 4 block per step: Mm = g M in [a][al][b][be], MT = M in
+      // [b][be][a][al]
+      for (int j = tid; j < nblk; j += nth) {
+        const int dv = dP[j], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
+        const float gg = gsm[a * nb + b];
+        float4 v[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const size_t o = (((size_t)a * RA + 4 * qa + x) * nb + b) * RB + 4 * qb;
+          v[x] = *reinterpret_cast<const float4*>(scr + (size_t)k * P * PS + o);
+          *reinterpret_cast<float4*>(Mm + o) = make_float4(gg * v[x].x, gg * v[x].y, gg * v[x].z, gg * v[x].w);
+        }
+        float* mt = MT + (((size_t)b * RB + 4 * qb) * na + a) * RA + 4 * qa;
+        *reinterpret_cast<float4*>(mt) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+        *reinterpret_cast<float4*>(mt + (size_t)na * RA) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+        *reinterpret_cast<float4*>(mt + (size_t)2 * na * RA) = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
+        *reinterpret_cast<float4*>(mt + (size_t)3 * na * RA) = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
       }
       float racc[2][4][4];
       const int nr = na * QA * nb * QB;
@@ -373,7 +409,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
 #pragma unroll
             for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
           if (blk < nx) {
-            const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+            const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
             const float* rr = Rm + (size_t)(a * nb + b) * PS + 4 * qb;  // + ap * RB
             const float* at = AT + (size_t)a * RA * RA + 4 * qa;        // + ap * RA
             for (int ap = 0; ap < RA; ++ap)
@@ -391,7 +427,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
                   make_float4(t4[0][y], t4[1][y], t4[2][y], t4[3][y]);
           } else {
             const int bl = blk - nx;
-            const int qa = bl % QA, a = (bl / QA) % na, qb = (bl / (QA * na)) % QB, b = bl / (QA * na * QB);
+            const int dv = dY[bl], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
             const float* rt = RT + (size_t)(a * nb + b) * PS + 4 * qa;  // + bp * RA
             const float* bt = BT + (size_t)b * RB * RB + 4 * qb;        // + bp * RB
             for (int bp = 0; bp < RB; ++bp)
@@ -409,7 +445,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         for (int q = 0; q < 2; ++q) {
           const int blk = tid + q * nth;
           if (blk < nr) {
-            const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+            const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
             const float* xt = XT + (size_t)(a * nb + b) * PS;     // + bp * RA + rotated chunk
             const float* bt = BT + (size_t)b * RB * RB + 4 * qb;  // + bp * RB
             int cx = qa;  // chunk of X^T column block qa in rows 4bq..4bq+3
@@ -433,14 +469,14 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
 #pragma unroll
             for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
           if (blk < nda) {
-            const int qp = blk % QA, qa = (blk / QA) % QA, a = blk / (QA * QA);
+            const int dv = d3[blk], qp = dv >> 8, qa = (dv >> 4) & 15, a = dv & 15;
             for (int b = 0; b < nb; ++b)
               for (int be = 0; be < RB; ++be)
                 fma44b(t4, *reinterpret_cast<const float4*>(MT + (((size_t)b * RB + be) * na + a) * RA + 4 * qa),
                        *reinterpret_cast<const float4*>(Ym + (((size_t)b * RB + be) * na + a) * RA + 4 * qp));
-            long long base;
-            int r0, r1, n;
-            objX(0, a, k, &base, &r0, &r1, &n);
+            // core k's object info (slot k & 1, filled before the core's first slice)
+            const long long base = s_ob[k & 1][a];
+            const int r0 = s_or0[k & 1][a], r1 = s_or1[k & 1][a], n = nk;
             float* dst = g.mode == 0 ? g.dA : g.dX;
             if (dst)
 #pragma unroll
@@ -451,15 +487,13 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
                 if (al < r0 && ap < r1 && t4[x][y] != 0.0f) atomicAdd(dst + base + ((long long)al * n + i) * r1 + ap, t4[x][y]);
               }
           } else {
-            const int bl = blk - nda;
-            const int qp = bl % QB, qb = (bl / QB) % QB, b = bl / (QB * QB);
+            const int dv = d3[blk], qp = dv >> 8, qb = (dv >> 4) & 15, b = dv & 15;
             for (int a = 0; a < na; ++a)
               for (int al = 0; al < RA; ++al)
                 fma44b(t4, *reinterpret_cast<const float4*>(Mm + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb),
                        *reinterpret_cast<const float4*>(Xm + (((size_t)a * RA + al) * nb + b) * RB + 4 * qp));
-            long long base;
-            int r0, r1, n;
-            objX(1, b, k, &base, &r0, &r1, &n);
+            const long long base = s_ob[k & 1][16 + b];
+            const int r0 = s_or0[k & 1][16 + b], r1 = s_or1[k & 1][16 + b], n = nk;
             float* dst = g.mode == 0 ? g.dB : g.dX;
             if (dst)
 #pragma unroll
@@ -479,7 +513,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
       for (int q = 0; q < 2; ++q) {
         const int blk = tid + q * nth;
         if (blk < nr) {
-          const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
+          const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
 #pragma unroll
           for (int x = 0; x < 4; ++x)
             *reinterpret_cast<float4*>(Rm + (size_t)(a * nb + b) * PS + (4 * qa + x) * RB + 4 * qb) =
@@ -500,12 +534,18 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
 
 static int pad4b(int r) { return (r + 3) & ~3; }
 
-bool gram_tile_bwd_fits(int na, int nb, int RA, int RB) { return na * RA * RA + nb * RB * RB <= 512 * kGTBMaxPF; }
-
 size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB) {
   const size_t P = (size_t)na * nb, PS = (size_t)RA * RB;
   const size_t szS = (size_t)na * RA * RA + (size_t)nb * RB * RB;
-  return sizeof(float) * (7 * P * PS + 2 * szS + P);
+  const size_t QA = RA / 4, QB = RB / 4;
+  const size_t tables = 2 * P * QA * QB + na * QA * QA + nb * QB * QB;  // block decode tables
+  return sizeof(float) * (7 * P * PS + 2 * szS + P) + sizeof(int) * tables;
+}
+
+constexpr size_t kGTBMaxSmem = 220 * 1024;
+
+bool gram_tile_bwd_fits(int na, int nb, int RA, int RB) {
+  return na * RA * RA + nb * RB * RB <= 512 * kGTBMaxPF && gram_tile_bwd_smem(na, nb, RA, RB) <= kGTBMaxSmem;
 }
 
 // Largest balanced tile whose buffers fit one CTA (512 threads, 2 blocks per thread).
@@ -518,8 +558,7 @@ void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB
   for (int ta = 1; ta <= 16 && ta <= batchA; ++ta)
     for (int tb = 1; tb <= 16 && tb <= batchB; ++tb) {
       if (ta * (RA / 4) * tb * (RB / 4) > 1024) continue;
-      if (ta * RA * RA + tb * RB * RB > 512 * kGTBMaxPF) continue;
-      if (gram_tile_bwd_smem(ta, tb, RA, RB) > 200 * 1024) continue;
+      if (!gram_tile_bwd_fits(ta, tb, RA, RB)) continue;
       const long long tiles = (long long)((batchA + ta - 1) / ta) * ((batchB + tb - 1) / tb);
       const long long per_sm = (tiles + sms - 1) / sms;
       const double work = (double)per_sm * ta * tb * (1.0 + 0.5 / ta + 0.5 / tb);
@@ -533,7 +572,7 @@ void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB
 
 bool gram_tile_bwd_supported(const TTV& A, const TTV& B) {
   const int RA = pad4b(A.rmax), RB = pad4b(B.rmax);
-  return RA <= 64 && RB <= 64 && gram_tile_bwd_smem(1, 1, RA, RB) <= 200 * 1024 && RA * RA + RB * RB <= 512 * kGTBMaxPF &&
+  return RA <= 64 && RB <= 64 && gram_tile_bwd_fits(1, 1, RA, RB) &&
          A.d <= T3F_MAX_D;
 }
 
