@@ -294,21 +294,89 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
       for (int x = 0; x < 8; ++x) P->mitems[w * 8 + x] = its[w].v[x];
     P->nmitems = (int)its.size();
   }
-  // adjoint tiles: the adjoint holds seven partial tiles per pair, so its side is the largest
-  // one (at most the forward side) whose buffers fit a CTA at the bucket's largest rank;
-  // that keeps most of the 512 threads busy with a 4 x 4 block each
-  int tlb[kBuckets];
-  for (int b = 0; b < kBuckets; ++b) {
-    const int R = kBucketMax[b];
-    int side = 1;
-    for (int t = 2; t <= tl[b]; ++t)
-      if ((long long)t * t * (R / 4) * (R / 4) <= 1024 && gram_tile_bwd_fits(t, t, R, R))
-        side = t;
-    tlb[b] = side;
-  }
+  // adjoint tiles: the adjoint holds seven partial tiles per pair, so its tiles are cut per
+  // bucket range from the objects' own padded ranks: a run of consecutive objects (sorted by
+  // rank) grows while its square self-tile fits one CTA (at most the forward side), so the
+  // lower-rank runs of a bucket get more pairs per CTA; a cross tile of two runs whose
+  // buffers do not fit is halved along b until it does
   size_t bsmem = 0;
   long long bpmax = 0;
-  T3F_CHECK(make_items(tlb, true, &P->bitems, &bsmem, &bpmax));
+  {
+    auto padr = [&](int pos0, int n) {
+      int R = 4;
+      for (int x = pos0; x < pos0 + n; ++x) R = std::max(R, (rmax[P->sorted[x]] + 3) & ~3);
+      return R;
+    };
+    auto tile_ok = [&](int na, int nb, int RA, int RB) {
+      return na * (RA / 4) * nb * (RB / 4) <= 1024 && gram_tile_bwd_fits(na, nb, RA, RB);
+    };
+    auto cut = [&](const Range& Rg, int side_max, std::vector<std::pair<int, int>>* out) {
+      for (int s0 = Rg.begin; s0 < Rg.end;) {
+        int n = 1;
+        while (n < side_max && s0 + n < Rg.end) {
+          const int R = padr(s0, n + 1);
+          if (!tile_ok(n + 1, n + 1, R, R)) break;
+          ++n;
+        }
+        out->push_back({s0, n});
+        s0 += n;
+      }
+    };
+    struct It {
+      double cost;
+      int v[8];
+    };
+    std::vector<It> its;
+    for (int g = 0; g < ngroups; ++g) {
+      double slices = 0;
+      for (int k = 0; k < P->gd[g]; ++k) slices += P->nmodes[(size_t)g * dmax + k];
+      for (int p = 0; p < kBuckets; ++p)
+        for (int q = p; q < kBuckets; ++q) {
+          const Range& A = P->br[(size_t)g * kBuckets + p];
+          const Range& B = P->br[(size_t)g * kBuckets + q];
+          if (A.end == A.begin || B.end == B.begin) continue;
+          std::vector<std::pair<int, int>> ta, tb;
+          cut(A, tl[p], &ta);
+          cut(B, tl[q], &tb);
+          for (size_t ia = 0; ia < ta.size(); ++ia) {
+            const int a0 = ta[ia].first, na = ta[ia].second, RA = padr(a0, na);
+            // same bucket: the b runs start at the a run, the diagonal tile covers its square
+            for (size_t ib = (p == q ? ia : 0); ib < tb.size(); ++ib) {
+              const int sym = (p == q && ib == ia) ? 0 : 1;
+              std::vector<std::pair<int, int>> todo{tb[ib]};
+              while (!todo.empty()) {
+                const int b0 = todo.back().first, nb = todo.back().second;
+                todo.pop_back();
+                const int RB = padr(b0, nb);
+                if (!tile_ok(na, nb, RA, RB)) {
+                  if (nb == 1) return T3F_ERR_UNSUPPORTED;
+                  todo.push_back({b0 + nb / 2, nb - nb / 2});
+                  todo.push_back({b0, nb / 2});
+                  continue;
+                }
+                It it;
+                it.cost = (double)na * nb * RA * RB * (3.0 * RA + 4.0 * RB) * slices;
+                it.v[0] = g;
+                it.v[1] = a0;
+                it.v[2] = na;
+                it.v[3] = b0;
+                it.v[4] = nb;
+                it.v[5] = RA;
+                it.v[6] = RB;
+                it.v[7] = sym;
+                its.push_back(it);
+                bsmem = std::max(bsmem, gram_tile_bwd_smem(na, nb, RA, RB));
+                bpmax = std::max(bpmax, (long long)na * nb * RA * RB);
+              }
+            }
+          }
+        }
+    }
+    std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+    P->bitems.resize(its.size() * 8);
+    for (size_t w = 0; w < its.size(); ++w)
+      for (int q = 0; q < 8; ++q) P->bitems[w * 8 + q] = its[w].v[q];
+  }
   P->nbitems = (int)(P->bitems.size() / 8);
   P->bsmem = bsmem;
   P->bstride = (long long)(dmax + 1) * bpmax;
