@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
     int* dP = reinterpret_cast<int*>(gsm + P);
     int* dY = dP + nblk;
     int* d3 = dY + nblk;
+    int* sp = d3 + nda + ndb;  // [nth] this thread's R' / dA-dB assignment of the right sweep
     // per-object access
     auto objX = [&](int side, int t, int k, long long* base, int* r0, int* r1, int* n) {
       if (g.mode == 0) {
@@ -354,6 +355,57 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
     }
     __syncthreads();
     // ---------------- right sweep with the gradient products ---------------------------
+    // Per slice, R' (nblk blocks, K = RB) and dA / dB (nda + ndb blocks, K = nb RB / na RA)
+    // share one barrier interval. Small tiles leave most threads idle there, so the K range
+    // of a block may be split among s2 (R') or s3 (dA / dB) threads of different warps: part
+    // p of block j runs on thread p * (block count rounded up to a warp) + j, so the lanes of a
+    // warp still read the same K row. R' parts keep their sums in registers until the end of
+    // the core; each dA / dB part adds its own sum to the gradient. The dA / dB items are
+    // counted from warp off3 on, past the warps that hold R' blocks. s2, s3 minimise the
+    // largest per-thread number of K steps; a split is taken only when it fits one round.
+    int l2 = 0, l3 = 0;
+    {
+      const int nrw = (nblk + 31) & ~31, n3b = nda + ndb, n3w = (n3b + 31) & ~31;
+      const int K3 = max(nb * RB, na * RA);
+      int best = 0x7fffffff, off3 = 0;
+      for (int a2 = 0; a2 <= 2; ++a2) {
+        const int c2 = 1 << a2;
+        if (c2 > 1 && (c2 * nrw > nth || QB % c2 != 0)) break;
+        const int u2 = c2 == 1 ? min(nblk, nth) : c2 * nrw;
+        const int load2 = c2 == 1 ? ((nblk + nth - 1) / nth) * RB : RB / c2;
+        const int o3 = (u2 & ~31) % nth, f = nth - o3;
+        for (int a3 = 0; a3 <= 2; ++a3) {
+          const int c3 = 1 << a3;
+          if (c3 > 1 && (c3 * n3w > nth || K3 < 8 * c3)) break;
+          const int n3 = c3 == 1 ? n3b : c3 * n3w, k3 = K3 / c3 + (c3 > 1 ? 2 : 0);
+          const int cb = (n3 + nth - 1) / nth, ca = n3 > f ? (n3 - f + nth - 1) / nth : 0;
+          int m = max(cb * k3, load2 + ca * k3);
+          if (u2 > o3) m = max(m, load2 + cb * k3);
+          if (m < best) {
+            best = m;
+            l2 = a2;
+            l3 = a3;
+            off3 = o3;
+          }
+        }
+      }
+      // sp[tid]: low half = R' part << 12 | block (0xffff: none; unused without a split),
+      // high half = dA / dB part << 12 | block, or without a split the first item index
+      int v2 = 0xffff, v3;
+      const int tr = (tid + nth - off3) % nth;
+      if (l2 > 0) {
+        const int part = tid / nrw, blk = tid - part * nrw;
+        if (part < (1 << l2) && blk < nblk) v2 = part << 12 | blk;
+      }
+      if (l3 > 0) {
+        const int part = tr / n3w, blk = tr - part * n3w;
+        v3 = (part < (1 << l3) && blk < n3b) ? (part << 12 | blk) : 0xffff;
+      } else {
+        v3 = tr;
+      }
+      sp[tid] = (int)((unsigned)v2 | (unsigned)v3 << 16);  // read back by this thread only
+    }
+    const int s2 = 1 << l2, s3 = 1 << l3;
     // R at interface d = 1
     for (int e = tid; e < P * PS; e += nth) {
       const int q = e % PS;
@@ -440,16 +492,25 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           }
         }
         __syncthreads();
-        // (2) R'[a][al][b][be] += sum_bp X[al][bp] B[be][bp]
+        // (2) R'[a][al][b][be] += sum_bp X[al][bp] B[be][bp]  (bp range split s2 ways)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const int blk = tid + q * nth;
+          int blk, part = 0;
+          if (s2 == 1) {
+            blk = tid + q * nth;
+          } else {
+            const int v2 = sp[tid] & 0xffff;
+            blk = (q == 0 && v2 != 0xffff) ? (v2 & 0xfff) : nr;
+            part = v2 >> 12;
+          }
           if (blk < nr) {
             const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
             const float* xt = XT + (size_t)(a * nb + b) * PS;     // + bp * RA + rotated chunk
             const float* bt = BT + (size_t)b * RB * RB + 4 * qb;  // + bp * RB
-            int cx = qa;  // chunk of X^T column block qa in rows 4bq..4bq+3
-            for (int bq = 0; bq < QB; ++bq) {
+            const int bq0 = (part * QB) >> l2, bq1 = ((part + 1) * QB) >> l2;
+            int cx = qa + bq0;  // chunk of X^T column block qa in rows 4bq..4bq+3
+            while (cx >= QA) cx -= QA;
+            for (int bq = bq0; bq < bq1; ++bq) {
 #pragma unroll
               for (int y = 0; y < 4; ++y) {
                 const int bp = 4 * bq + y;
@@ -461,8 +522,9 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           }
         }
         // (3) dA_a,i[al][ap] = sum_{b,be} M[al][be] Y'[be][ap];  dB_b,i[be][bp] = sum_{a,al} gM[al][be] X[al][bp]
-        const int nda = na * QA * QA, ndb = nb * QB * QB;
-        for (int blk = tid; blk < nda + ndb; blk += nth) {
+        const int v3 = (int)((unsigned)sp[tid] >> 16);
+        for (int w = s3 == 1 ? v3 : 0; s3 == 1 ? w < nda + ndb : (w == 0 && v3 != 0xffff); w += (s3 == 1 ? nth : 1)) {
+          const int blk = s3 == 1 ? w : (v3 & 0xfff), part = s3 == 1 ? 0 : v3 >> 12;
           float t4[4][4];
 #pragma unroll
           for (int x = 0; x < 4; ++x)
@@ -470,10 +532,10 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
           if (blk < nda) {
             const int dv = d3[blk], qp = dv >> 8, qa = (dv >> 4) & 15, a = dv & 15;
-            for (int b = 0; b < nb; ++b)
-              for (int be = 0; be < RB; ++be)
-                fma44b(t4, *reinterpret_cast<const float4*>(MT + (((size_t)b * RB + be) * na + a) * RA + 4 * qa),
-                       *reinterpret_cast<const float4*>(Ym + (((size_t)b * RB + be) * na + a) * RA + 4 * qp));
+            const int KK = nb * RB, kk1 = ((part + 1) * KK) >> l3;
+            for (int kk = (part * KK) >> l3; kk < kk1; ++kk)
+              fma44b(t4, *reinterpret_cast<const float4*>(MT + ((size_t)kk * na + a) * RA + 4 * qa),
+                     *reinterpret_cast<const float4*>(Ym + ((size_t)kk * na + a) * RA + 4 * qp));
             // core k's object info (slot k & 1, filled before the core's first slice)
             const long long base = s_ob[k & 1][a];
             const int r0 = s_or0[k & 1][a], r1 = s_or1[k & 1][a], n = nk;
@@ -488,10 +550,10 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
               }
           } else {
             const int dv = d3[blk], qp = dv >> 8, qb = (dv >> 4) & 15, b = dv & 15;
-            for (int a = 0; a < na; ++a)
-              for (int al = 0; al < RA; ++al)
-                fma44b(t4, *reinterpret_cast<const float4*>(Mm + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb),
-                       *reinterpret_cast<const float4*>(Xm + (((size_t)a * RA + al) * nb + b) * RB + 4 * qp));
+            const int KK = na * RA, kk1 = ((part + 1) * KK) >> l3;
+            for (int kk = (part * KK) >> l3; kk < kk1; ++kk)
+              fma44b(t4, *reinterpret_cast<const float4*>(Mm + ((size_t)kk * nb + b) * RB + 4 * qb),
+                     *reinterpret_cast<const float4*>(Xm + ((size_t)kk * nb + b) * RB + 4 * qp));
             const long long base = s_ob[k & 1][16 + b];
             const int r0 = s_or0[k & 1][16 + b], r1 = s_or1[k & 1][16 + b], n = nk;
             float* dst = g.mode == 0 ? g.dB : g.dX;
@@ -508,10 +570,37 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         __syncthreads();
         cur ^= 1;
       }
-      // R at interface k
+      // R at interface k; with an R' split, parts 1.. hand their sums to part 0 through the
+      // free X / X^T / Y buffers (nblk blocks of 16 values each, at most three parts)
+      int rblk = nr;
+      if (s2 > 1) {
+        const int v2 = sp[tid] & 0xffff, part = v2 >> 12, blk = v2 & 0xfff;
+        if (v2 != 0xffff && part > 0) {
+          float* xb = part == 1 ? Xm : (part == 2 ? XT : Ym);
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+            *reinterpret_cast<float4*>(xb + ((size_t)blk * 4 + x) * 4) =
+                make_float4(racc[0][x][0], racc[0][x][1], racc[0][x][2], racc[0][x][3]);
+        }
+        __syncthreads();
+        if (v2 != 0xffff && part == 0) {
+          rblk = blk;
+          for (int pp = 1; pp < s2; ++pp) {
+            const float* xb = pp == 1 ? Xm : (pp == 2 ? XT : Ym);
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              const float4 v = *reinterpret_cast<const float4*>(xb + ((size_t)blk * 4 + x) * 4);
+              racc[0][x][0] += v.x;
+              racc[0][x][1] += v.y;
+              racc[0][x][2] += v.z;
+              racc[0][x][3] += v.w;
+            }
+          }
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int blk = tid + q * nth;
+        const int blk = s2 == 1 ? tid + q * nth : (q == 0 ? rblk : nr);
         if (blk < nr) {
           const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
 #pragma unroll
@@ -538,7 +627,7 @@ size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB) {
   const size_t P = (size_t)na * nb, PS = (size_t)RA * RB;
   const size_t szS = (size_t)na * RA * RA + (size_t)nb * RB * RB;
   const size_t QA = RA / 4, QB = RB / 4;
-  const size_t tables = 2 * P * QA * QB + na * QA * QA + nb * QB * QB;  // block decode tables
+  const size_t tables = 2 * P * QA * QB + na * QA * QA + nb * QB * QB + 512;  // decode + split tables
   return sizeof(float) * (7 * P * PS + 2 * szS + P) + sizeof(int) * tables;
 }
 
