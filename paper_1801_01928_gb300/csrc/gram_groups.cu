@@ -296,9 +296,9 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
   }
   // adjoint tiles: the adjoint holds seven partial tiles per pair, so its tiles are cut per
   // bucket range from the objects' own padded ranks: a run of consecutive objects (sorted by
-  // rank) grows while its square self-tile fits one CTA (at most the forward side), so the
-  // lower-rank runs of a bucket get more pairs per CTA; a cross tile of two runs whose
-  // buffers do not fit is halved along b until it does
+  // rank) grows while its square self-tile fits one CTA (side at most 16, independent of the
+  // forward tiles), so the lower-rank runs of a bucket get more pairs per CTA; a cross tile
+  // of two runs whose buffers do not fit is halved along b until it does
   size_t bsmem = 0;
   long long bpmax = 0;
   {
@@ -336,8 +336,8 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
           const Range& B = P->br[(size_t)g * kBuckets + q];
           if (A.end == A.begin || B.end == B.begin) continue;
           std::vector<std::pair<int, int>> ta, tb;
-          cut(A, tl[p], &ta);
-          cut(B, tl[q], &tb);
+          cut(A, 16, &ta);
+          cut(B, 16, &tb);
           for (size_t ia = 0; ia < ta.size(); ++ia) {
             const int a0 = ta[ia].first, na = ta[ia].second, RA = padr(a0, na);
             // same bucket: the b runs start at the a run, the diagonal tile covers its square
