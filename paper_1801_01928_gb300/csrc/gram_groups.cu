@@ -183,9 +183,36 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
     }
     for (int k = 0; k <= d; ++k) P->objrk[(size_t)pos * (dmax + 1) + k] = X->ranks[roff[o] + k];
   }
-  // tiles of the upper triangle of every group, cut per bucket pair; `fits` bounds a tile
-  auto make_items = [&](const int* side, bool bwd, std::vector<int>* out, size_t* smem_out,
+  // CUDA-core tiles of the upper triangle of every group, cut per bucket pair from the
+  // objects' own padded ranks: a run of consecutive objects (sorted by rank) grows up to the
+  // side cap while its square self-tile fits one CTA, so the lower-rank runs of a bucket get
+  // more pairs per CTA; a cross tile of two runs that does not fit is halved along b until
+  // it does. A tile that is a sub-tile of a diagonal square covers ordered pairs (sym = 0).
+  auto padr = [&](int pos0, int n) {
+    int R = 4;
+    for (int x = pos0; x < pos0 + n; ++x) R = std::max(R, (rmax[P->sorted[x]] + 3) & ~3);
+    return R;
+  };
+  auto make_items = [&](const int* cap, bool bwd, std::vector<int>* out, size_t* smem_out,
                         long long* pmax_out) -> t3f_status {
+    // a tile must fit one CTA of 512 threads: at most 2 blocks each, staging and shared memory
+    auto tile_ok = [&](int na, int nb, int RA, int RB) {
+      if (na * (RA / 4) * nb * (RB / 4) > 1024) return false;
+      if (bwd) return gram_tile_bwd_fits(na, nb, RA, RB);
+      return gram_tile_smem(na, nb, RA, RB) <= 200 * 1024 && na * RA * RA + nb * RB * RB <= 512 * 16;
+    };
+    auto cut = [&](const Range& Rg, int side_max, std::vector<std::pair<int, int>>* runs) {
+      for (int s0 = Rg.begin; s0 < Rg.end;) {
+        int n = 1;
+        while (n < side_max && s0 + n < Rg.end) {
+          const int R = padr(s0, n + 1);
+          if (!tile_ok(n + 1, n + 1, R, R)) break;
+          ++n;
+        }
+        runs->push_back({s0, n});
+        s0 += n;
+      }
+    };
     struct It {
       double cost;
       int v[8];
@@ -201,33 +228,39 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
           const Range& A = P->br[(size_t)g * kBuckets + p];
           const Range& B = P->br[(size_t)g * kBuckets + q];
           if (A.end == A.begin || B.end == B.begin) continue;
-          for (int a0 = A.begin; a0 < A.end; a0 += side[p]) {
-            const int na = std::min(side[p], A.end - a0);
-            int RA = 4;
-            for (int x = a0; x < a0 + na; ++x) RA = std::max(RA, (rmax[P->sorted[x]] + 3) & ~3);
-            for (int b0 = (p == q ? a0 : B.begin); b0 < B.end; b0 += side[q]) {
-              const int nb = std::min(side[q], B.end - b0);
-              int RB = 4;
-              for (int x = b0; x < b0 + nb; ++x) RB = std::max(RB, (rmax[P->sorted[x]] + 3) & ~3);
-              // a tile must fit one CTA of 512 threads: 2 blocks each, staging bounds
-              if (na * (RA / 4) * nb * (RB / 4) > 1024) return T3F_ERR_UNSUPPORTED;
-              const size_t sm = bwd ? gram_tile_bwd_smem(na, nb, RA, RB) : gram_tile_smem(na, nb, RA, RB);
-              if (!bwd && sm > 200 * 1024) return T3F_ERR_UNSUPPORTED;
-              if (bwd && !gram_tile_bwd_fits(na, nb, RA, RB)) return T3F_ERR_UNSUPPORTED;
-              if (!bwd && na * RA * RA + nb * RB * RB > 512 * 16) return T3F_ERR_UNSUPPORTED;
-              It it;
-              it.cost = (double)na * nb * RA * RB * (RA + RB) * slices;
-              it.v[0] = g;
-              it.v[1] = a0;
-              it.v[2] = na;
-              it.v[3] = b0;
-              it.v[4] = nb;
-              it.v[5] = RA;
-              it.v[6] = RB;
-              it.v[7] = (p == q && a0 == b0) ? 0 : 1;
-              its.push_back(it);
-              smem = std::max(smem, sm);
-              pmax = std::max(pmax, (long long)na * nb * RA * RB);
+          std::vector<std::pair<int, int>> ta, tb;
+          cut(A, cap[p], &ta);
+          cut(B, cap[q], &tb);
+          for (size_t ia = 0; ia < ta.size(); ++ia) {
+            const int a0 = ta[ia].first, na = ta[ia].second, RA = padr(a0, na);
+            // same bucket: the b runs start at the a run, the diagonal tile covers its square
+            for (size_t ib = (p == q ? ia : 0); ib < tb.size(); ++ib) {
+              const int sym = (p == q && ib == ia) ? 0 : 1;
+              std::vector<std::pair<int, int>> todo{tb[ib]};
+              while (!todo.empty()) {
+                const int b0 = todo.back().first, nb = todo.back().second;
+                todo.pop_back();
+                const int RB = padr(b0, nb);
+                if (!tile_ok(na, nb, RA, RB)) {
+                  if (nb == 1) return T3F_ERR_UNSUPPORTED;
+                  todo.push_back({b0 + nb / 2, nb - nb / 2});
+                  todo.push_back({b0, nb / 2});
+                  continue;
+                }
+                It it;
+                it.cost = (double)na * nb * RA * RB * (bwd ? 3.0 * RA + 4.0 * RB : (double)(RA + RB)) * slices;
+                it.v[0] = g;
+                it.v[1] = a0;
+                it.v[2] = na;
+                it.v[3] = b0;
+                it.v[4] = nb;
+                it.v[5] = RA;
+                it.v[6] = RB;
+                it.v[7] = sym;
+                its.push_back(it);
+                smem = std::max(smem, bwd ? gram_tile_bwd_smem(na, nb, RA, RB) : gram_tile_smem(na, nb, RA, RB));
+                pmax = std::max(pmax, (long long)na * nb * RA * RB);
+              }
             }
           }
         }
@@ -294,88 +327,13 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
       for (int x = 0; x < 8; ++x) P->mitems[w * 8 + x] = its[w].v[x];
     P->nmitems = (int)its.size();
   }
-  // adjoint tiles: the adjoint holds seven partial tiles per pair, so its tiles are cut per
-  // bucket range from the objects' own padded ranks: a run of consecutive objects (sorted by
-  // rank) grows while its square self-tile fits one CTA (side at most 16, independent of the
-  // forward tiles), so the lower-rank runs of a bucket get more pairs per CTA; a cross tile
-  // of two runs whose buffers do not fit is halved along b until it does
+  // adjoint tiles (seven partial tiles per pair): the same cut with side cap 16, whatever
+  // the forward sides, so every run takes as many pairs as one CTA holds
   size_t bsmem = 0;
   long long bpmax = 0;
   {
-    auto padr = [&](int pos0, int n) {
-      int R = 4;
-      for (int x = pos0; x < pos0 + n; ++x) R = std::max(R, (rmax[P->sorted[x]] + 3) & ~3);
-      return R;
-    };
-    auto tile_ok = [&](int na, int nb, int RA, int RB) {
-      return na * (RA / 4) * nb * (RB / 4) <= 1024 && gram_tile_bwd_fits(na, nb, RA, RB);
-    };
-    auto cut = [&](const Range& Rg, int side_max, std::vector<std::pair<int, int>>* out) {
-      for (int s0 = Rg.begin; s0 < Rg.end;) {
-        int n = 1;
-        while (n < side_max && s0 + n < Rg.end) {
-          const int R = padr(s0, n + 1);
-          if (!tile_ok(n + 1, n + 1, R, R)) break;
-          ++n;
-        }
-        out->push_back({s0, n});
-        s0 += n;
-      }
-    };
-    struct It {
-      double cost;
-      int v[8];
-    };
-    std::vector<It> its;
-    for (int g = 0; g < ngroups; ++g) {
-      double slices = 0;
-      for (int k = 0; k < P->gd[g]; ++k) slices += P->nmodes[(size_t)g * dmax + k];
-      for (int p = 0; p < kBuckets; ++p)
-        for (int q = p; q < kBuckets; ++q) {
-          const Range& A = P->br[(size_t)g * kBuckets + p];
-          const Range& B = P->br[(size_t)g * kBuckets + q];
-          if (A.end == A.begin || B.end == B.begin) continue;
-          std::vector<std::pair<int, int>> ta, tb;
-          cut(A, 16, &ta);
-          cut(B, 16, &tb);
-          for (size_t ia = 0; ia < ta.size(); ++ia) {
-            const int a0 = ta[ia].first, na = ta[ia].second, RA = padr(a0, na);
-            // same bucket: the b runs start at the a run, the diagonal tile covers its square
-            for (size_t ib = (p == q ? ia : 0); ib < tb.size(); ++ib) {
-              const int sym = (p == q && ib == ia) ? 0 : 1;
-              std::vector<std::pair<int, int>> todo{tb[ib]};
-              while (!todo.empty()) {
-                const int b0 = todo.back().first, nb = todo.back().second;
-                todo.pop_back();
-                const int RB = padr(b0, nb);
-                if (!tile_ok(na, nb, RA, RB)) {
-                  if (nb == 1) return T3F_ERR_UNSUPPORTED;
-                  todo.push_back({b0 + nb / 2, nb - nb / 2});
-                  todo.push_back({b0, nb / 2});
-                  continue;
-                }
-                It it;
-                it.cost = (double)na * nb * RA * RB * (3.0 * RA + 4.0 * RB) * slices;
-                it.v[0] = g;
-                it.v[1] = a0;
-                it.v[2] = na;
-                it.v[3] = b0;
-                it.v[4] = nb;
-                it.v[5] = RA;
-                it.v[6] = RB;
-                it.v[7] = sym;
-                its.push_back(it);
-                bsmem = std::max(bsmem, gram_tile_bwd_smem(na, nb, RA, RB));
-                bpmax = std::max(bpmax, (long long)na * nb * RA * RB);
-              }
-            }
-          }
-        }
-    }
-    std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
-    P->bitems.resize(its.size() * 8);
-    for (size_t w = 0; w < its.size(); ++w)
-      for (int q = 0; q < 8; ++q) P->bitems[w * 8 + q] = its[w].v[q];
+    const int cap16[kBuckets] = {16, 16, 16, 16};
+    T3F_CHECK(make_items(cap16, true, &P->bitems, &bsmem, &bpmax));
   }
   P->nbitems = (int)(P->bitems.size() / 8);
   P->bsmem = bsmem;
