@@ -61,6 +61,10 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
   // per-core object info, two core parities: [side * 16 + object] core offset and ranks
   __shared__ long long s_ob[2][32];
   __shared__ int s_or0[2][32], s_or1[2][32], s_on[2];
+  // effective ranks of a core over the tile's objects (padded to 4): [parity][A left, A right,
+  // B left, B right]; products skip the 4 x 4 blocks and K steps beyond them (boundary cores
+  // have rank 1 on their outer side)
+  __shared__ int s_er[2][4];
   const int tid = threadIdx.x, nth = blockDim.x;
   float* scr = g.scratch + (long long)blockIdx.x * g.scratch_stride;
   for (int it = 0;; ++it) {
@@ -180,6 +184,16 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         s_or0[par][tid] = r0;
         s_or1[par][tid] = r1;
         if (tid == 0) s_on[par] = n;
+        int m0 = r0, m1 = r1;  // maxima over each half-warp (one side's objects)
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+          m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        }
+        if (t == 0) {
+          s_er[par][2 * side] = max(4, (m0 + 3) & ~3);
+          s_er[par][2 * side + 1] = max(4, (m1 + 3) & ~3);
+        }
       }
     };
     // exact quotients of the staging indices (< 2^13) by R^2 and R through 32-bit reciprocals
@@ -256,11 +270,16 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         __syncthreads();
         const float* As = Sg + cur * szS;  // [a][al][ap]
         const float* Bs = As + szA;        // [b][be][bp]
+        const int eA0 = s_er[k & 1][0], eA1 = s_er[k & 1][1], eB0 = s_er[k & 1][2], eB1 = s_er[k & 1][3];
         // T[a][al][b][bp] = sum_be M[a][al][b][be] B[b][be][bp]  (T in RT's storage; in split
-        // mode the second half of the be range goes to T1)
+        // mode the second half of the be range goes to T1); al < eA0, bp < eB1, be < eB0
         for (int blk = ks == 2 ? bb : tid; blk < nblk && hb < ks; blk += (ks == 2 ? nblk : nth)) {
           const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
-          const int be0 = ks == 2 ? hb * (RB / 2) : 0, be1 = ks == 2 ? be0 + RB / 2 : RB;
+          if (4 * qa >= eA0 || 4 * qb >= eB1) {
+            if (ks == 2) break;
+            continue;
+          }
+          const int be0 = ks == 2 ? hb * (eB0 / 2) : 0, be1 = (ks == 2 && hb == 0) ? eB0 / 2 : eB0;
           float t4[4][4];
 #pragma unroll
           for (int x = 0; x < 4; ++x)
@@ -278,12 +297,11 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           if (ks == 2) break;
         }
         __syncthreads();
-        // M'[a][ap][b][bp] += sum_al A[a][al][ap] T[a][al][b][bp]
+        // M'[a][ap][b][bp] += sum_al A[a][al][ap] T[a][al][b][bp]; ap < eA1, bp < eB1, al < eA0
         if (ks == 2) {
-          if (hb < 2) {
-            const int blk = bb;
-            const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
-            const int al0 = hb * (RA / 2), al1 = al0 + RA / 2;
+          const int dv = dP[bb], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
+          if (hb < 2 && 4 * qa < eA1 && 4 * qb < eB1) {
+            const int al0 = hb * (eA0 / 2), al1 = hb == 0 ? eA0 / 2 : eA0;
             for (int al = al0; al < al1; ++al) {
               const size_t o = (((size_t)a * RA + al) * nb + b) * RB + 4 * qb;
               const float4 t0 = *reinterpret_cast<const float4*>(RT + o);
@@ -298,7 +316,8 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             const int blk = tid + q * nth;
             if (blk < nblk) {
               const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
-              for (int al = 0; al < RA; ++al)
+              const int al1 = (4 * qa < eA1 && 4 * qb < eB1) ? eA0 : 0;
+              for (int al = 0; al < al1; ++al)
                 fma44b(acc[q], *reinterpret_cast<const float4*>(As + ((size_t)a * RA + al) * RA + 4 * qa),
                        *reinterpret_cast<const float4*>(RT + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb));
             }
@@ -452,7 +471,9 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         __syncthreads();
         const float* AT = Sg + cur * szS;  // [a][ap][al]  (A_i transposed)
         const float* BT = AT + szA;        // [b][bp][be]  (B_i transposed)
-        // (1) X[a][al][b][bp] = sum_ap A[al][ap] R[ap][bp]; Y'[b][be][a][ap] = g sum_bp B[be][bp] R[ap][bp]
+        const int eA0 = s_er[k & 1][0], eA1 = s_er[k & 1][1], eB0 = s_er[k & 1][2], eB1 = s_er[k & 1][3];
+        // (1) X[a][al][b][bp] = sum_ap A[al][ap] R[ap][bp] (al < eA0, bp < eB1, ap < eA1);
+        //     Y'[b][be][a][ap] = g sum_bp B[be][bp] R[ap][bp] (be < eB0, ap < eA1, bp < eB1)
         const int nx = na * QA * nb * QB, ny = nb * QB * na * QA;
         for (int blk = tid; blk < nx + ny; blk += nth) {
           float t4[4][4];
@@ -462,9 +483,10 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
           if (blk < nx) {
             const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
+            if (4 * qa >= eA0 || 4 * qb >= eB1) continue;
             const float* rr = Rm + (size_t)(a * nb + b) * PS + 4 * qb;  // + ap * RB
             const float* at = AT + (size_t)a * RA * RA + 4 * qa;        // + ap * RA
-            for (int ap = 0; ap < RA; ++ap)
+            for (int ap = 0; ap < eA1; ++ap)
               fma44b(t4, *reinterpret_cast<const float4*>(at + ap * RA), *reinterpret_cast<const float4*>(rr + ap * RB));
 #pragma unroll
             for (int x = 0; x < 4; ++x)
@@ -480,9 +502,10 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           } else {
             const int bl = blk - nx;
             const int dv = dY[bl], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
+            if (4 * qb >= eB0 || 4 * qa >= eA1) continue;
             const float* rt = RT + (size_t)(a * nb + b) * PS + 4 * qa;  // + bp * RA
             const float* bt = BT + (size_t)b * RB * RB + 4 * qb;        // + bp * RB
-            for (int bp = 0; bp < RB; ++bp)
+            for (int bp = 0; bp < eB1; ++bp)
               fma44b(t4, *reinterpret_cast<const float4*>(bt + bp * RB), *reinterpret_cast<const float4*>(rt + bp * RA));
             const float gg = gsm[a * nb + b];
 #pragma unroll
@@ -505,9 +528,10 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           }
           if (blk < nr) {
             const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
+            if (4 * qa >= eA0 || 4 * qb >= eB0) continue;  // al < eA0, be < eB0, bp < eB1
             const float* xt = XT + (size_t)(a * nb + b) * PS;     // + bp * RA + rotated chunk
             const float* bt = BT + (size_t)b * RB * RB + 4 * qb;  // + bp * RB
-            const int bq0 = (part * QB) >> l2, bq1 = ((part + 1) * QB) >> l2;
+            const int nbq = eB1 >> 2, bq0 = (part * nbq) >> l2, bq1 = ((part + 1) * nbq) >> l2;
             int cx = qa + bq0;  // chunk of X^T column block qa in rows 4bq..4bq+3
             while (cx >= QA) cx -= QA;
             for (int bq = bq0; bq < bq1; ++bq) {
@@ -532,10 +556,20 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
           if (blk < nda) {
             const int dv = d3[blk], qp = dv >> 8, qa = (dv >> 4) & 15, a = dv & 15;
-            const int KK = nb * RB, kk1 = ((part + 1) * KK) >> l3;
-            for (int kk = (part * KK) >> l3; kk < kk1; ++kk)
-              fma44b(t4, *reinterpret_cast<const float4*>(MT + ((size_t)kk * na + a) * RA + 4 * qa),
-                     *reinterpret_cast<const float4*>(Ym + ((size_t)kk * na + a) * RA + 4 * qp));
+            if (4 * qa >= eA0 || 4 * qp >= eA1) continue;  // al < eA0, ap < eA1, be < eB0
+            if (eB0 == RB) {
+              const int KK = nb * RB, kk1 = ((part + 1) * KK) >> l3;
+              for (int kk = (part * KK) >> l3; kk < kk1; ++kk)
+                fma44b(t4, *reinterpret_cast<const float4*>(MT + ((size_t)kk * na + a) * RA + 4 * qa),
+                       *reinterpret_cast<const float4*>(Ym + ((size_t)kk * na + a) * RA + 4 * qp));
+            } else if (part == 0) {
+              for (int b = 0; b < nb; ++b)
+                for (int be = 0; be < eB0; ++be) {
+                  const size_t kk = (size_t)b * RB + be;
+                  fma44b(t4, *reinterpret_cast<const float4*>(MT + (kk * na + a) * RA + 4 * qa),
+                         *reinterpret_cast<const float4*>(Ym + (kk * na + a) * RA + 4 * qp));
+                }
+            }
             // core k's object info (slot k & 1, filled before the core's first slice)
             const long long base = s_ob[k & 1][a];
             const int r0 = s_or0[k & 1][a], r1 = s_or1[k & 1][a], n = nk;
@@ -550,10 +584,20 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
               }
           } else {
             const int dv = d3[blk], qp = dv >> 8, qb = (dv >> 4) & 15, b = dv & 15;
-            const int KK = na * RA, kk1 = ((part + 1) * KK) >> l3;
-            for (int kk = (part * KK) >> l3; kk < kk1; ++kk)
-              fma44b(t4, *reinterpret_cast<const float4*>(Mm + ((size_t)kk * nb + b) * RB + 4 * qb),
-                     *reinterpret_cast<const float4*>(Xm + ((size_t)kk * nb + b) * RB + 4 * qp));
+            if (4 * qb >= eB0 || 4 * qp >= eB1) continue;  // be < eB0, bp < eB1, al < eA0
+            if (eA0 == RA) {
+              const int KK = na * RA, kk1 = ((part + 1) * KK) >> l3;
+              for (int kk = (part * KK) >> l3; kk < kk1; ++kk)
+                fma44b(t4, *reinterpret_cast<const float4*>(Mm + ((size_t)kk * nb + b) * RB + 4 * qb),
+                       *reinterpret_cast<const float4*>(Xm + ((size_t)kk * nb + b) * RB + 4 * qp));
+            } else if (part == 0) {
+              for (int a = 0; a < na; ++a)
+                for (int al = 0; al < eA0; ++al) {
+                  const size_t kk = (size_t)a * RA + al;
+                  fma44b(t4, *reinterpret_cast<const float4*>(Mm + (kk * nb + b) * RB + 4 * qb),
+                         *reinterpret_cast<const float4*>(Xm + (kk * nb + b) * RB + 4 * qp));
+                }
+            }
             const long long base = s_ob[k & 1][16 + b];
             const int r0 = s_or0[k & 1][16 + b], r1 = s_or1[k & 1][16 + b], n = nk;
             float* dst = g.mode == 0 ? g.dB : g.dX;
