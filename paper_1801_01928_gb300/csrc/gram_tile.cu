@@ -68,6 +68,10 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
   // per-core object info, two core parities: [side * 16 + object] core offset and ranks
   __shared__ long long s_ob[2][32];
   __shared__ int s_or0[2][32], s_or1[2][32], s_on[2];
+  // effective ranks of a core over the tile's objects (padded to 4): [parity][A left, A right,
+  // B left, B right]; the products skip the 4 x 4 blocks and K steps beyond them (boundary
+  // cores have rank 1 on their outer side)
+  __shared__ int s_er[2][4];
   const int tid = threadIdx.x, nth = blockDim.x;
 
   for (int it = 0;; ++it) {
@@ -168,6 +172,16 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
         s_or0[par][tid] = r0;
         s_or1[par][tid] = r1;
         if (tid == 0) s_on[par] = n;
+        int m0 = r0, m1 = r1;  // maxima over each half-warp (one side's objects)
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+          m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        }
+        if (t == 0) {
+          s_er[par][2 * side] = max(4, (m0 + 3) & ~3);
+          s_er[par][2 * side + 1] = max(4, (m1 + 3) & ~3);
+        }
       }
     };
     // stage slice i of core k into `buf` (zero-padded): FP32 cores are copied asynchronously
@@ -208,14 +222,14 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
           const int qa = blk % QA, a = (blk / QA) % na, qb = (blk / (QA * na)) % QB, b = blk / (QA * na * QB);
           g1m[q] = (b * RB * na + a) * RA + 4 * qa;
           g1b[q] = b * RB * RB + 4 * qb;
-          g1t[q] = (a * RA + 4 * qa) * TR;                 // row base; unit = b * QB + qb
-          g1b[q] |= (b * QB + qb) << 20;
+          g1t[q] = (a * RA + 4 * qa) | qb << 16;           // first T row | qb
+          g1b[q] |= (b * QB + qb) << 20 | (int)((unsigned)qa << 28);  // unit = b * QB + qb | qa
         }
         {
           const int qb = blk % QB, b = (blk / QB) % nb, qa = (blk / (QB * nb)) % QA, a = blk / (QB * nb * QA);
           g2a[q] = a * RA * RA + 4 * qa;
-          g2t[q] = (a * RA) * TR;                          // row base of al = 0
-          g2a[q] |= (b * QB + qb) << 20;
+          g2t[q] = a * RA | qb << 16;                      // T row of al = 0 | qb
+          g2a[q] |= (b * QB + qb) << 20 | (int)((unsigned)qa << 28);  // unit | qa (the ap block)
           g2w[q] = ((b * RB + 4 * qb) * na + a) * RA + 4 * qa;
         }
       }
@@ -255,10 +269,13 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
       __syncthreads();
       const float* Asb = stg[cur];
       const float* Bsb = stg[cur] + szA;
-      // GEMM1: T[a][al][b][bp] = sum_be MT[b][be][a][al] Bs[b][be][bp]
+      const int eA0 = s_er[k & 1][0], eA1 = s_er[k & 1][1], eB0 = s_er[k & 1][2], eB1 = s_er[k & 1][3];
+      // GEMM1: T[a][al][b][bp] = sum_be MT[b][be][a][al] Bs[b][be][bp]  (al < eA0, bp < eB1,
+      // be < eB0)
 #pragma unroll
       for (int q = 0; q < kGTMaxBlk; ++q) {
         if (g1m[q] < 0) continue;
+        if (4 * (int)((unsigned)g1b[q] >> 28) >= eA0 || 4 * (g1t[q] >> 16) >= eB1) continue;
         float t4[4][4];
 #pragma unroll
         for (int x = 0; x < 4; ++x)
@@ -266,10 +283,10 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
           for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
         const float* mrow = MT + g1m[q];
         const float* brow = Bsb + (g1b[q] & 0xfffff);
-        for (int be = 0; be < RB; ++be)
+        for (int be = 0; be < eB0; ++be)
           fma44(t4, *reinterpret_cast<const float4*>(mrow + be * mstep), *reinterpret_cast<const float4*>(brow + be * RB));
-        const int unit = g1b[q] >> 20;
-        const int row0t = g1t[q] / TR;
+        const int unit = (g1b[q] >> 20) & 0xff;
+        const int row0t = g1t[q] & 0xffff;
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
           const int r = row0t + x;
@@ -278,14 +295,16 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
         }
       }
       __syncthreads();
-      // GEMM2: acc[a][ap][b][bp] += sum_al As[a][al][ap] T[a][al][b][bp]
+      // GEMM2: acc[a][ap][b][bp] += sum_al As[a][al][ap] T[a][al][b][bp]  (ap < eA1, bp < eB1,
+      // al < eA0)
 #pragma unroll
       for (int q = 0; q < kGTMaxBlk; ++q) {
-        if (g2a[q] < 0) continue;
+        if (g2w[q] < 0) continue;
+        if (4 * (int)((unsigned)g2a[q] >> 28) >= eA1 || 4 * (g2t[q] >> 16) >= eB1) continue;
         const float* arow = Asb + (g2a[q] & 0xfffff);
-        const int unit = g2a[q] >> 20;
-        const int rbase = g2t[q] / TR;
-        for (int al = 0; al < RA; ++al) {
+        const int unit = (g2a[q] >> 20) & 0xff;
+        const int rbase = g2t[q] & 0xffff;
+        for (int al = 0; al < eA0; ++al) {
           const int r = rbase + al;
           fma44(acc[q], *reinterpret_cast<const float4*>(arow + al * RA),
                 *reinterpret_cast<const float4*>(TT + r * TR + 4 * (unit ^ ((r >> 2) & 7))));
