@@ -67,6 +67,41 @@ def test_gram_groups_forward_norms_backward(lib):
             assert rel_err_cores(got, want) < TOL["fp32"], (g, j)
 
 
+def test_gram_groups_varying_core_ranks(lib):
+    # interior ranks that change from core to core (and d = 1, n_k = 1 groups): the kernels
+    # bound each core's products by the tile's largest ranks on either side of that core
+    rng = np.random.default_rng(402)
+    groups = []
+    for d, n, S_ in ((1, [5], 3), (2, [1, 3], 4), (4, [3, 1, 2, 4], 7), (5, [2, 3, 2, 2, 3], 6)):
+        objs = []
+        for _ in range(S_):
+            ranks = [1] + [int(rng.integers(1, 40)) for _ in range(d - 1)] + [1]
+            objs.append([c[0] for c in S.random_tt(rng, 1, n, ranks, 0.3)])
+        groups.append(objs)
+    gstart = [0]
+    for objs in groups:
+        gstart.append(gstart[-1] + len(objs))
+    objs = as_f32([o for g in groups for o in g])
+    X = lib.RaggedTT.from_objects([[np.asarray(c, np.float32) for c in o] for o in objs])
+    ws = lib.gram_groups_prepare(X, gstart)
+    G, nrm = lib.gram_groups(X, gstart, ws)
+    assert rel_err(G.cpu().numpy(), oracle_groups(objs, gstart)) < TOL["fp32"]
+    assert rel_err(nrm.cpu().numpy(), [O.norm(o) for o in objs]) < TOL["fp32"]
+    dout = rng.normal(size=G.numel()).astype(np.float32)
+    dX = lib.gram_groups_backward(X, gstart, ws, torch.tensor(dout, device="cuda"))
+    view = lib.RaggedTT(dX, X.dims, X.modes, X.ranks, X.offsets)
+    off = 0
+    for g in range(len(gstart) - 1):
+        grp = objs[gstart[g]:gstart[g + 1]]
+        Sg = len(grp)
+        dG = dout[off:off + Sg * Sg].reshape(Sg, Sg).astype(np.float64)
+        off += Sg * Sg
+        dA, dB = O.gram_vjp(grp, grp, dG)
+        for j in range(Sg):
+            got = [c.double().cpu().numpy() for c in view.object_cores(gstart[g] + j)]
+            assert rel_err_cores(got, [a + b for a, b in zip(dA[j], dB[j])]) < TOL["fp32"], (g, j)
+
+
 def test_gram_groups_bf16_storage(lib):
     objs, gstart = ragged_case(402)
     objs_b = [round_bf16(o) for o in objs]
