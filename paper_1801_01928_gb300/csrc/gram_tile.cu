@@ -156,9 +156,8 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
     const void* Ap = g.mode == 0 ? g.A.p : g.gcores;
     const void* Bp = g.mode == 0 ? g.B.p : g.gcores;
     const int szA = na * RA * RA, szS = szA + nb * RB * RB;
-    // exact quotients of the staging indices (< 2^13) by R^2 and R through 32-bit reciprocals
-    const unsigned mAA = 0xffffffffu / (unsigned)(RA * RA) + 1u, mA = 0xffffffffu / (unsigned)RA + 1u;
-    const unsigned mBB = 0xffffffffu / (unsigned)(RB * RB) + 1u, mB = 0xffffffffu / (unsigned)RB + 1u;
+    // exact quotients of the line indices (< 2^10) by R through 32-bit reciprocals
+    const unsigned mA = 0xffffffffu / (unsigned)RA + 1u, mB = 0xffffffffu / (unsigned)RB + 1u;
     // core offsets and ranks of the tile's objects for core k into parity slot par; the
     // slots are filled ahead of use and published by a later block barrier
     auto fill_info = [&](int k, int par) {
@@ -185,27 +184,44 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
       }
     };
     // stage slice i of core k into `buf` (zero-padded): FP32 cores are copied asynchronously
-    // (cp.async, 4 bytes, zero-fill outside the ranks), BF16 cores converted on the way
+    // (cp.async, 4 bytes, zero-fill outside the ranks), BF16 cores converted on the way. The
+    // padded slices are cut into rows of R elements; 2^lt consecutive threads share a row, so
+    // an object's offset and ranks are read once per row. lt (2, 3 or 4) minimises rows per
+    // thread x (row setup + elements per thread).
+    const int nlA = na * RA, nl = nlA + nb * RB;
+    int lt = 4;
+    {
+      int best = 0x7fffffff;
+      for (int c = 2; c <= 4; ++c) {
+        const int lines = (nl + (nth >> c) - 1) / (nth >> c), per = (max(RA, RB) + (1 << c) - 1) >> c;
+        const int cost = lines * (4 + per);
+        if (cost < best) {
+          best = cost;
+          lt = c;
+        }
+      }
+    }
     auto stage = [&](int k, int i, float* buf) {
-      const int par = k & 1, n = s_on[par];
-#pragma unroll 2
-      for (int e = tid; e < szS; e += nth) {
-        const int side = e < szA ? 0 : 1;
-        const unsigned e2 = (unsigned)(side ? e - szA : e), R = side ? RB : RA;
-        const unsigned t = __umulhi(e2, side ? mBB : mAA), qq = e2 - t * R * R;
-        const unsigned rq = __umulhi(qq, side ? mB : mA);
-        const int row = (int)rq, col = (int)(qq - rq * R);
+      const int par = k & 1, n = s_on[par], p0 = tid & ((1 << lt) - 1);
+      for (int ln = tid >> lt; ln < nl; ln += nth >> lt) {
+        const int side = ln < nlA ? 0 : 1;
+        const unsigned l2 = (unsigned)(side ? ln - nlA : ln), R = side ? RB : RA;
+        const unsigned t = __umulhi(l2, side ? mB : mA), w = l2 - t * R;  // object, row in it
         const int slot = side * 16 + (int)t, r0 = s_or0[par][slot], r1 = s_or1[par][slot];
-        const bool ok = row < r0 && col < r1 && i < n;
-        const long long idx = ok ? s_ob[par][slot] + ((long long)row * n + i) * r1 + col : 0;
+        const int lim = (int)w < r0 ? r1 : 0;  // columns p < lim are inside the core
+        const long long idx0 = s_ob[par][slot] + ((long long)w * n + i) * r1;
+        float* dst = buf + (side ? szA : 0) + (t * R + w) * R;
         const void* src = side == 0 ? Ap : Bp;
-        float* dst = buf + e;
-        if (sizeof(ST) == 4) {
-          const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-          const float* gp = static_cast<const float*>(src) + idx;
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gp), "r"(ok ? 4 : 0));
-        } else {
-          *dst = ok ? ldv<ST>(src, idx) : 0.0f;
+        for (int p = p0; p < (int)R; p += 1 << lt) {
+          const bool ok = p < lim;
+          const long long idx = ok ? idx0 + p : 0;
+          if (sizeof(ST) == 4) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + p);
+            const float* gp = static_cast<const float*>(src) + idx;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gp), "r"(ok ? 4 : 0));
+          } else {
+            dst[p] = ok ? ldv<ST>(src, idx) : 0.0f;
+          }
         }
       }
       if (sizeof(ST) == 4) asm volatile("cp.async.commit_group;\n" ::);
