@@ -118,13 +118,22 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
     const int r0 = a.ra[k], r1 = a.ra[k + 1], z0 = Z.r[k], z1 = Z.r[k + 1], n = Z.n[k];
     __syncthreads();
     // stage this CTA's Z cores of core k as [K][i][b] (left: K = row, b = col; right: transposed)
-    for (int e = tid; e < J * kRZ * n * kRZ; e += blockDim.x) {
-      const int b = e % kRZ, i = (e / kRZ) % n, K = (e / (kRZ * n)) % kRZ, o = e / (kRZ * n * kRZ);
-      const int row = a.dir == 0 ? K : b, col = a.dir == 0 ? b : K;
-      const int ob = blockIdx.x * J + o;
-      float v = 0.0f;
-      if (ob < Z.batch && row < z0 && col < z1) v = __ldg(Zp + core_base(Z, k, ob) + ((long long)row * n + i) * z1 + col);
-      Zc[(((size_t)o * kRZ + K) * nmax + i) * kRZ + b] = v;
+    // with 4-byte asynchronous copies (zero-filled outside the ranks), one commit group that
+    // the first batch's wait covers; e = ((o * 8 + K) * n + i) * 8 + b, the quotient by n taken
+    // through an exact 32-bit reciprocal (indices < 2^13)
+    {
+      const unsigned mn = 0xffffffffu / (unsigned)n + 1u;
+      for (int e = tid; e < J * kRZ * n * kRZ; e += blockDim.x) {
+        const unsigned x = (unsigned)e >> 3, q = n == 1 ? x : __umulhi(x, mn);
+        const int b = e & 7, i = (int)(x - q * (unsigned)n), K = (int)(q & 7), o = (int)(q >> 3);
+        const int row = a.dir == 0 ? K : b, col = a.dir == 0 ? b : K;
+        const int ob = blockIdx.x * J + o;
+        const bool ok = ob < Z.batch && row < z0 && col < z1;
+        const float* src = ok ? Zp + core_base(Z, k, ob) + ((long long)row * n + i) * z1 + col : Zp;
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(Zc + (((size_t)o * kRZ + K) * nmax + i) * kRZ + b);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(ok ? 4 : 0));
+      }
+      asm volatile("cp.async.commit_group;\n" ::);
     }
     float acc1[4][4], acc2[4][4];
 #pragma unroll
@@ -285,6 +294,7 @@ __global__ void __launch_bounds__(512) k_passemble(const __grid_constant__ PAsse
 #pragma unroll
     for (int y = 0; y < 16; ++y) acc[x][y] = 0.0f;
   const int jb = rg * a.range, je = min(Z.batch, jb + a.range);
+  const unsigned mn = 0xffffffffu / (unsigned)n + 1u, mNC = 0xffffffffu / (unsigned)NC + 1u;
   for (int j0 = jb; j0 < je; j0 += kAsmChunk) {
     __syncthreads();
     for (int e = tid; e < kAsmChunk * kRZ * RU; e += blockDim.x) {
@@ -300,7 +310,9 @@ __global__ void __launch_bounds__(512) k_passemble(const __grid_constant__ PAsse
       Rk[e] = v;
     }
     for (int e = tid; e < kAsmChunk * kRZ * n * kRZ; e += blockDim.x) {
-      const int col = e % kRZ, i = (e / kRZ) % n, row = (e / (kRZ * n)) % kRZ, o = e / (kRZ * n * kRZ);
+      // quotient by n through an exact 32-bit reciprocal (indices < 2^13)
+      const unsigned x = (unsigned)e >> 3, q = n == 1 ? x : __umulhi(x, mn);
+      const int col = e & 7, i = (int)(x - q * (unsigned)n), row = (int)(q & 7), o = (int)(q >> 3);
       const int j = j0 + o;
       float v = 0.0f;
       if (j < je && row < z0 && col < z1) v = __ldg(Zp + core_base(Z, k, j) + ((long long)row * n + i) * z1 + col);
@@ -309,7 +321,8 @@ __global__ void __launch_bounds__(512) k_passemble(const __grid_constant__ PAsse
     __syncthreads();
     // S^T[o][b][(i, a')] = sum_delta R[a'][delta] Z[b][i][delta]
     for (int e = tid; e < kAsmChunk * kRZ * NC; e += blockDim.x) {
-      const int col = e % NC, b = (e / NC) % kRZ, o = e / (NC * kRZ);
+      const unsigned qn = __umulhi((unsigned)e, mNC);  // e / NC, exact for e < 2^16
+      const int col = e - (int)qn * NC, b = (int)(qn & 7), o = (int)(qn >> 3);
       const int i = col / RU, ap = col % RU;
       const float* rr = Rk + (o * RU + ap) * kRZ;
       const float* zz = Zk + ((o * kRZ + b) * n + i) * kRZ;
