@@ -10,6 +10,8 @@
 
 namespace t3f {
 
+constexpr int kMvRegN = 8;  // column modes n up to this keep A[a, i, :, a'] in registers
+
 struct MatvecArgs {
   TTV A, x, C;
   int bA, bx, P;       // batches; P = number of products
@@ -33,18 +35,35 @@ __global__ void __launch_bounds__(256) k_matvec(const __grid_constant__ MatvecAr
   __syncthreads();
   float* Cp = static_cast<float*>(a.C.p) + core_base(a.C, k, p);
   const int rowlen = m * ra1 * rx1;            // contiguous (i, a', b') block of one row
-  const int nrows = ra0 * rx0;
-  const long long total = (long long)nrows * rowlen;
-  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
-    const int row = (int)(e / rowlen), q = (int)(e % rowlen);
-    const int al = row / rx0, be = row % rx0;
-    const int i = q / (ra1 * rx1), c1 = q % (ra1 * rx1);
-    const int ap = c1 / rx1, bp = c1 % rx1;
+  // an item is (a, q) with q = (i, a', b') a position of the row block; its thread walks the
+  // rows (a, b), b < r_x, so the index split is paid once per r_x outputs; consecutive
+  // threads write consecutive addresses
+  for (int e = threadIdx.x; e < ra0 * rowlen; e += blockDim.x) {
+    const int al = e / rowlen, q = e - al * rowlen;
+    const int i = q / (ra1 * rx1), c1 = q - i * (ra1 * rx1);
+    const int ap = c1 / rx1, bp = c1 - ap * rx1;
     const float* Ar = As + ((al * m + i) * n) * ra1 + ap;  // A[al, i, j, ap] at j * ra1
-    const float* Xr = Xs + (be * n) * rx1 + bp;            // x[be, j, bp] at j * rx1
-    float s = 0.0f;
-    for (int j = 0; j < n; ++j) s = fmaf(Ar[j * ra1], Xr[j * rx1], s);
-    Cp[e] = s;
+    float* cq = Cp + (long long)al * rx0 * rowlen + q;
+    if (n <= kMvRegN) {
+      float av[kMvRegN];  // A[al, i, :, ap], reused for every row b
+#pragma unroll
+      for (int j = 0; j < kMvRegN; ++j) av[j] = j < n ? Ar[j * ra1] : 0.0f;
+      for (int be = 0; be < rx0; ++be) {
+        const float* Xr = Xs + (be * n) * rx1 + bp;        // x[be, j, bp] at j * rx1
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kMvRegN; ++j)
+          if (j < n) s = fmaf(av[j], Xr[j * rx1], s);
+        cq[(long long)be * rowlen] = s;
+      }
+    } else {
+      for (int be = 0; be < rx0; ++be) {
+        const float* Xr = Xs + (be * n) * rx1 + bp;
+        float s = 0.0f;
+        for (int j = 0; j < n; ++j) s = fmaf(Ar[j * ra1], Xr[j * rx1], s);
+        cq[(long long)be * rowlen] = s;
+      }
+    }
   }
 }
 
