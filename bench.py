@@ -702,7 +702,8 @@ def gpu_arm(args):
                    "parallelism": f"replicas{world}", "step_gflop": round(step_flops / 1e9, 3),
                    "streams": "2: orthogonalisation chain (orth2, rgrad, orth5, project_sum, adjoint) "
                               "on a side stream, concurrent with the rest",
-                   "ms_per_step_one_stream": round(seq_ms, 4)},
+                   "ms_per_step_one_stream": round(seq_ms, 4),
+                   "uneven_tiles": list(w.tiles4)},
         "roofline": {"bound": "alu", "kernel_op": dom, "achieved": round(ach, 3),
                      "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
                      "frac": round(ach / FP32_PEAK_TFLOPS, 4), "traffic": traffic,

@@ -28,11 +28,12 @@ t3f_status launch_gram_tile_table(const void* cores, int dtype, int dmax, const 
                                   cudaStream_t s);
 size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB);
 bool gram_tile_bwd_fits(int na, int nb, int RA, int RB);
+bool gram_tile_bwd_fits_small(int na, int nb, int RA, int RB);
 t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, const long long* off, const int* rk,
                                       const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
                                       const int* gd, const int* perm, const float* dout, const long long* gout_off,
                                       float* dX, float* scratch, long long scratch_stride, size_t smem, int grid,
-                                      cudaStream_t s);
+                                      int threads, cudaStream_t s);
 
 t3f_status launch_gram_mma_list(int math, const void* cores, int dtype, int dmax, const long long* off,
                                 const int* rk, const int* nmodes, const int* items, int nitems, int* head,
@@ -67,11 +68,16 @@ struct Plan {
   std::vector<int> items;    // 8 ints per item (forward tiles, all bucket pairs)
   std::vector<int> mitems;   // tensor-core tiles (every bucket pair)
   int nmitems = 0;
-  std::vector<int> bitems;   // 8 ints per item (adjoint tiles)
+  std::vector<int> bitems;   // 8 ints per item (adjoint tiles for 512-thread CTAs, one per SM)
   int nbitems = 0;
   size_t bsmem = 0;
   long long bstride = 0;     // scratch floats per CTA of the adjoint
   int bgrid = 0;
+  std::vector<int> sitems;   // adjoint tiles for 256-thread CTAs, two per SM
+  int nsitems = 0;
+  size_t ssmem = 0;
+  long long sstride = 0;
+  int sgrid = 0;
   std::vector<long long> objoff;  // [pos][dmax]
   std::vector<int> objrk;    // [pos][dmax + 1]
   std::vector<int> nmodes;   // [group][dmax]
@@ -81,7 +87,7 @@ struct Plan {
   std::vector<Range> br;     // [group][bucket]
   size_t smem = 0;
   // workspace layout (bytes)
-  size_t o_items, o_mitems, o_bitems, o_off, o_rk, o_nm, o_gs, o_gd, o_go, o_perm, o_scr, total;
+  size_t o_items, o_mitems, o_bitems, o_sitems, o_off, o_rk, o_nm, o_gs, o_gd, o_go, o_perm, o_scr, o_sscr, total;
 };
 
 int bucket_of(int r) {
@@ -327,23 +333,123 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
       for (int x = 0; x < 8; ++x) P->mitems[w * 8 + x] = its[w].v[x];
     P->nmitems = (int)its.size();
   }
-  // adjoint tiles (seven partial tiles per pair): the same cut with side cap 16, whatever
-  // the forward sides, so every run takes as many pairs as one CTA holds
-  size_t bsmem = 0;
-  long long bpmax = 0;
+  // adjoint tiles (seven partial tiles per pair). Runs of rank-sorted objects grow (side at
+  // most 16) while their square tile fits a full-size CTA (512 threads, one per SM); a tile
+  // that does not fit is halved along b, then along a. Tiles that also fit a half-size CTA
+  // (256 threads, half an SM's shared memory) go to a second list run with two CTAs per SM,
+  // where one CTA's barrier waits overlap the other's work. Sub-tiles of a diagonal square
+  // cover ordered pairs (sym = 0).
   {
-    const int cap16[kBuckets] = {16, 16, 16, 16};
-    T3F_CHECK(make_items(cap16, true, &P->bitems, &bsmem, &bpmax));
+    auto padr = [&](int pos0, int n) {
+      int R = 4;
+      for (int x = pos0; x < pos0 + n; ++x) R = std::max(R, (rmax[P->sorted[x]] + 3) & ~3);
+      return R;
+    };
+    auto fits_big = [&](int na, int nb, int RA, int RB) {
+      return na * (RA / 4) * nb * (RB / 4) <= 1024 && gram_tile_bwd_fits(na, nb, RA, RB);
+    };
+    struct It {
+      double cost;
+      int v[8];
+    };
+    std::vector<It> big, small;
+    size_t bsm = 0, ssm = 0;
+    long long bpm = 0, spm = 0;
+    for (int g = 0; g < ngroups; ++g) {
+      double slices = 0;
+      for (int k = 0; k < P->gd[g]; ++k) slices += P->nmodes[(size_t)g * dmax + k];
+      auto cut = [&](const Range& Rg, std::vector<std::pair<int, int>>* runs) {
+        for (int s0 = Rg.begin; s0 < Rg.end;) {
+          int n = 1;
+          while (n < 16 && s0 + n < Rg.end) {
+            const int R = padr(s0, n + 1);
+            if (!fits_big(n + 1, n + 1, R, R)) break;
+            ++n;
+          }
+          runs->push_back({s0, n});
+          s0 += n;
+        }
+      };
+      for (int p = 0; p < kBuckets; ++p)
+        for (int q = p; q < kBuckets; ++q) {
+          const Range& A = P->br[(size_t)g * kBuckets + p];
+          const Range& B = P->br[(size_t)g * kBuckets + q];
+          if (A.end == A.begin || B.end == B.begin) continue;
+          std::vector<std::pair<int, int>> ta, tb;
+          cut(A, &ta);
+          cut(B, &tb);
+          for (size_t ia = 0; ia < ta.size(); ++ia)
+            for (size_t ib = (p == q ? ia : 0); ib < tb.size(); ++ib) {
+              const int sym = (p == q && ib == ia) ? 0 : 1;
+              struct Tl {
+                int a0, na, b0, nb;
+              };
+              std::vector<Tl> todo{{ta[ia].first, ta[ia].second, tb[ib].first, tb[ib].second}};
+              while (!todo.empty()) {
+                const Tl t = todo.back();
+                todo.pop_back();
+                const int RA = padr(t.a0, t.na), RB = padr(t.b0, t.nb);
+                const bool fb = fits_big(t.na, t.nb, RA, RB);
+                if (!fb && t.nb > 1) {
+                  todo.push_back({t.a0, t.na, t.b0 + t.nb / 2, t.nb - t.nb / 2});
+                  todo.push_back({t.a0, t.na, t.b0, t.nb / 2});
+                  continue;
+                }
+                if (!fb && t.na > 1) {
+                  todo.push_back({t.a0 + t.na / 2, t.na - t.na / 2, t.b0, t.nb});
+                  todo.push_back({t.a0, t.na / 2, t.b0, t.nb});
+                  continue;
+                }
+                if (!fb) return T3F_ERR_UNSUPPORTED;
+                const bool fs = gram_tile_bwd_fits_small(t.na, t.nb, RA, RB);
+                It it;
+                it.cost = (double)t.na * t.nb * RA * RB * (3.0 * RA + 4.0 * RB) * slices;
+                it.v[0] = g;
+                it.v[1] = t.a0;
+                it.v[2] = t.na;
+                it.v[3] = t.b0;
+                it.v[4] = t.nb;
+                it.v[5] = RA;
+                it.v[6] = RB;
+                it.v[7] = sym;
+                const size_t sm = gram_tile_bwd_smem(t.na, t.nb, RA, RB);
+                const long long pe = (long long)t.na * t.nb * RA * RB;
+                if (fs) {
+                  small.push_back(it);
+                  ssm = std::max(ssm, sm);
+                  spm = std::max(spm, pe);
+                } else {
+                  big.push_back(it);
+                  bsm = std::max(bsm, sm);
+                  bpm = std::max(bpm, pe);
+                }
+              }
+            }
+        }
+    }
+    auto flat = [](std::vector<It>& its, std::vector<int>* out) {
+      std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+      out->resize(its.size() * 8);
+      for (size_t w = 0; w < its.size(); ++w)
+        for (int q = 0; q < 8; ++q) (*out)[w * 8 + q] = its[w].v[q];
+    };
+    flat(big, &P->bitems);
+    flat(small, &P->sitems);
+    P->nbitems = (int)big.size();
+    P->bsmem = bsm;
+    P->bstride = (long long)(dmax + 1) * bpm;
+    P->bgrid = std::max(1, std::min(P->nbitems, sm_count_gg()));
+    P->nsitems = (int)small.size();
+    P->ssmem = ssm;
+    P->sstride = (long long)(dmax + 1) * spm;
+    P->sgrid = std::max(1, std::min(P->nsitems, 2 * sm_count_gg()));
   }
-  P->nbitems = (int)(P->bitems.size() / 8);
-  P->bsmem = bsmem;
-  P->bstride = (long long)(dmax + 1) * bpmax;
-  P->bgrid = std::max(1, std::min(P->nbitems, sm_count_gg()));
   P->smem = smem;
   size_t o = kWsHeader;
   P->o_items = o; o += a256(sizeof(int) * P->items.size());
   P->o_mitems = o; o += a256(sizeof(int) * P->mitems.size());
   P->o_bitems = o; o += a256(sizeof(int) * P->bitems.size());
+  P->o_sitems = o; o += a256(sizeof(int) * P->sitems.size());
   P->o_off = o; o += a256(sizeof(long long) * P->objoff.size());
   P->o_rk = o; o += a256(sizeof(int) * P->objrk.size());
   P->o_nm = o; o += a256(sizeof(int) * P->nmodes.size());
@@ -352,6 +458,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
   P->o_go = o; o += a256(sizeof(long long) * P->gout.size());
   P->o_perm = o; o += a256(sizeof(int) * P->perm.size());
   P->o_scr = o; o += a256(sizeof(float) * (size_t)P->bstride * P->bgrid);
+  P->o_sscr = o; o += a256(sizeof(float) * (size_t)P->sstride * P->sgrid);
   P->total = o;
   return T3F_OK;
 }
@@ -379,6 +486,7 @@ t3f_status gg_tables_upload(const Plan& P, char* w, cudaStream_t s) {
   } cps[] = {{P.o_items, P.items.data(), sizeof(int) * P.items.size()},
              {P.o_mitems, P.mitems.data(), sizeof(int) * P.mitems.size()},
              {P.o_bitems, P.bitems.data(), sizeof(int) * P.bitems.size()},
+             {P.o_sitems, P.sitems.data(), sizeof(int) * P.sitems.size()},
              {P.o_off, P.objoff.data(), sizeof(long long) * P.objoff.size()},
              {P.o_rk, P.objrk.data(), sizeof(int) * P.objrk.size()},
              {P.o_nm, P.nmodes.data(), sizeof(int) * P.nmodes.size()},
@@ -422,7 +530,8 @@ extern "C" t3f_status t3f_gram_groups(const t3f_tt_ragged* X, int32_t ngroups, c
   if (math == T3F_MATH_TF32 && X->dtype != T3F_F32) return T3F_ERR_DTYPE;
   cudaStream_t s = (cudaStream_t)stream;
   char* w = static_cast<char*>(ws);
-  // header words: 0 error, 1 CUDA-core list head, 3 tensor-core list head
+  // header words: 0 error, 1 CUDA-core list head, 3 tensor-core list head (2 and 4: the
+  // adjoint lists)
   int* hw = reinterpret_cast<int*>(w);
   if (cudaMemsetAsync(w, 0, 8 * sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
   const long long* off = reinterpret_cast<const long long*>(w + P.o_off);
@@ -471,13 +580,27 @@ extern "C" t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t n
     }
   }
   if (cudaMemsetAsync(dcores, 0, sizeof(float) * nel, s) != cudaSuccess) return T3F_ERR_CUDA;
-  int* head = reinterpret_cast<int*>(w + 2 * sizeof(int));  // third word of the header
+  // list heads: header word 2 (full-size CTAs) and word 4 (half-size CTAs)
+  int* head = reinterpret_cast<int*>(w + 2 * sizeof(int));
+  int* shead = reinterpret_cast<int*>(w + 4 * sizeof(int));
   if (cudaMemsetAsync(head, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
-  return launch_gram_tile_bwd_table(
-      X->cores, X->dtype, P.dmax, reinterpret_cast<const long long*>(w + P.o_off),
-      reinterpret_cast<const int*>(w + P.o_rk), reinterpret_cast<const int*>(w + P.o_nm),
-      reinterpret_cast<const int*>(w + P.o_bitems), P.nbitems, head, reinterpret_cast<const int*>(w + P.o_gs),
-      reinterpret_cast<const int*>(w + P.o_gd), reinterpret_cast<const int*>(w + P.o_perm), dout,
-      reinterpret_cast<const long long*>(w + P.o_go), dcores, reinterpret_cast<float*>(w + P.o_scr), P.bstride,
-      P.bsmem, P.bgrid, s);
+  if (cudaMemsetAsync(shead, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
+  // the full-size list first (its items are the most expensive), then the half-size one
+  if (P.nbitems > 0)
+    T3F_CHECK(launch_gram_tile_bwd_table(
+        X->cores, X->dtype, P.dmax, reinterpret_cast<const long long*>(w + P.o_off),
+        reinterpret_cast<const int*>(w + P.o_rk), reinterpret_cast<const int*>(w + P.o_nm),
+        reinterpret_cast<const int*>(w + P.o_bitems), P.nbitems, head, reinterpret_cast<const int*>(w + P.o_gs),
+        reinterpret_cast<const int*>(w + P.o_gd), reinterpret_cast<const int*>(w + P.o_perm), dout,
+        reinterpret_cast<const long long*>(w + P.o_go), dcores, reinterpret_cast<float*>(w + P.o_scr), P.bstride,
+        P.bsmem, P.bgrid, 512, s));
+  if (P.nsitems > 0)
+    T3F_CHECK(launch_gram_tile_bwd_table(
+        X->cores, X->dtype, P.dmax, reinterpret_cast<const long long*>(w + P.o_off),
+        reinterpret_cast<const int*>(w + P.o_rk), reinterpret_cast<const int*>(w + P.o_nm),
+        reinterpret_cast<const int*>(w + P.o_sitems), P.nsitems, shead, reinterpret_cast<const int*>(w + P.o_gs),
+        reinterpret_cast<const int*>(w + P.o_gd), reinterpret_cast<const int*>(w + P.o_perm), dout,
+        reinterpret_cast<const long long*>(w + P.o_go), dcores, reinterpret_cast<float*>(w + P.o_sscr), P.sstride,
+        P.ssmem, P.sgrid, 256, s));
+  return T3F_OK;
 }

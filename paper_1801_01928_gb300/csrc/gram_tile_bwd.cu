@@ -699,6 +699,14 @@ bool gram_tile_bwd_fits(int na, int nb, int RA, int RB) {
   return na * RA * RA + nb * RB * RB <= 512 * kGTBMaxPF && gram_tile_bwd_smem(na, nb, RA, RB) <= kGTBMaxSmem;
 }
 
+// A tile for the half-size CTAs (256 threads, two CTAs per SM): at most two 4 x 4 blocks per
+// thread and half of an SM's shared memory.
+constexpr size_t kGTBSmallSmem = 110 * 1024;
+
+bool gram_tile_bwd_fits_small(int na, int nb, int RA, int RB) {
+  return na * (RA / 4) * nb * (RB / 4) <= 512 && gram_tile_bwd_smem(na, nb, RA, RB) <= kGTBSmallSmem;
+}
+
 // Largest balanced tile whose buffers fit one CTA (512 threads, 2 blocks per thread).
 void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB) {
   *TA = 1;
@@ -774,7 +782,7 @@ t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, co
                                       const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
                                       const int* gd, const int* perm, const float* dout, const long long* gout_off,
                                       float* dX, float* scratch, long long scratch_stride, size_t smem, int grid,
-                                      cudaStream_t s) {
+                                      int threads, cudaStream_t s) {
   GramBwdTileArgs g;
   memset(&g, 0, sizeof(g));
   g.mode = 1;
@@ -800,12 +808,12 @@ t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, co
     auto kern = k_gram_tile_bwd<float>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
-    kern<<<grid, 512, smem, s>>>(g);
+    kern<<<grid, threads, smem, s>>>(g);
   } else {
     auto kern = k_gram_tile_bwd<__nv_bfloat16>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
-    kern<<<grid, 512, smem, s>>>(g);
+    kern<<<grid, threads, smem, s>>>(g);
   }
   return launch_status();
 }
