@@ -26,9 +26,9 @@ t3f_status launch_gram_tile_table(const void* cores, int dtype, int dmax, const 
                                   const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
                                   const int* gd, float* out, const long long* gout_off, const int* perm, size_t smem,
                                   cudaStream_t s);
-size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB);
+size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB, bool single);
 bool gram_tile_bwd_fits(int na, int nb, int RA, int RB);
-bool gram_tile_bwd_fits_small(int na, int nb, int RA, int RB);
+bool gram_tile_bwd_fits_small(int na, int nb, int RA, int RB, bool single);
 t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, const long long* off, const int* rk,
                                       const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
                                       const int* gd, const int* perm, const float* dout, const long long* gout_off,
@@ -264,7 +264,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
                 it.v[6] = RB;
                 it.v[7] = sym;
                 its.push_back(it);
-                smem = std::max(smem, bwd ? gram_tile_bwd_smem(na, nb, RA, RB) : gram_tile_smem(na, nb, RA, RB));
+                smem = std::max(smem, bwd ? gram_tile_bwd_smem(na, nb, RA, RB, false) : gram_tile_smem(na, nb, RA, RB));
                 pmax = std::max(pmax, (long long)na * nb * RA * RB);
               }
             }
@@ -336,9 +336,9 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
   // adjoint tiles (seven partial tiles per pair). Runs of rank-sorted objects grow (side at
   // most 16) while their square tile fits a full-size CTA (512 threads, one per SM); a tile
   // that does not fit is halved along b, then along a. Tiles that also fit a half-size CTA
-  // (256 threads, half an SM's shared memory) go to a second list run with two CTAs per SM,
-  // where one CTA's barrier waits overlap the other's work. Sub-tiles of a diagonal square
-  // cover ordered pairs (sym = 0).
+  // (256 threads, half an SM's shared memory), if need be with one staging buffer instead of
+  // two, go to a second list run with two CTAs per SM, where one CTA's barrier and load waits
+  // overlap the other's work. Sub-tiles of a diagonal square cover ordered pairs (sym = 0).
   {
     auto padr = [&](int pos0, int n) {
       int R = 4;
@@ -401,7 +401,9 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
                   continue;
                 }
                 if (!fb) return T3F_ERR_UNSUPPORTED;
-                const bool fs = gram_tile_bwd_fits_small(t.na, t.nb, RA, RB);
+                // half-size CTA with two staging buffers, else with one, else full-size
+                const bool fs2 = gram_tile_bwd_fits_small(t.na, t.nb, RA, RB, false);
+                const bool fs = fs2 || gram_tile_bwd_fits_small(t.na, t.nb, RA, RB, true);
                 It it;
                 it.cost = (double)t.na * t.nb * RA * RB * (3.0 * RA + 4.0 * RB) * slices;
                 it.v[0] = g;
@@ -411,8 +413,8 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
                 it.v[4] = t.nb;
                 it.v[5] = RA;
                 it.v[6] = RB;
-                it.v[7] = sym;
-                const size_t sm = gram_tile_bwd_smem(t.na, t.nb, RA, RB);
+                it.v[7] = sym | (fs && !fs2 ? 2 : 0);  // bit 1: one staging buffer
+                const size_t sm = gram_tile_bwd_smem(t.na, t.nb, RA, RB, fs && !fs2);
                 const long long pe = (long long)t.na * t.nb * RA * RB;
                 if (fs) {
                   small.push_back(it);

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
   const int tid = threadIdx.x, nth = blockDim.x;
   float* scr = g.scratch + (long long)blockIdx.x * g.scratch_stride;
   for (int it = 0;; ++it) {
-    int grp = 0, a0, na, b0, nb, RA, RB, sym = 0, d;
+    int grp = 0, a0, na, b0, nb, RA, RB, sym = 0, single = 0, d;
     if (g.mode == 0) {
       if (it > 0) break;
       const int ntb = (g.B.batch + g.TB - 1) / g.TB;
@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
       nb = s_item[4];
       RA = s_item[5];
       RB = s_item[6];
-      sym = g.items[s_item[7] * 8 + 7];
+      const int fl = g.items[s_item[7] * 8 + 7];  // bit 0: symmetrise, bit 1: one staging buffer
+      sym = fl & 1;
+      single = (fl >> 1) & 1;
       d = g.gd[grp];
     }
     const int P = na * nb, PS = RA * RB, QA = RA / 4, QB = RB / 4;
@@ -109,9 +111,11 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
     float* XT = Xm + P * PS;             // [p][bp][al]    X^T     (K rows bp for R'; the 4-float
                                          // column chunk c of row bp sits at chunk (c + bp/4) mod RA/4)
     float* Ym = XT + P * PS;             // [b][be][a][ap] g Y     (K rows (b, be) for dA)
-    float* Sg = Ym + P * PS;             // staging: [2][AT (na RA RA) + BT (nb RB RB)]
+    float* Sg = Ym + P * PS;             // staging: [2 or 1][AT (na RA RA) + BT (nb RB RB)]
     const int szA = na * RA * RA, szS = szA + nb * RB * RB;
-    float* gsm = Sg + 2 * szS;           // [P] cotangents of the tile's pairs
+    // with one staging buffer (tiles that fit half an SM only that way) the next slice is
+    // issued after the slice's last barrier and waited for at the next slice's start
+    float* gsm = Sg + (single ? 1 : 2) * szS;  // [P] cotangents of the tile's pairs
     // block decode tables (a | qa << 4 | b << 8 | qb << 12), filled once per tile so that the
     // per-slice phases need no integer division: dP = pair-layout 4 x 4 blocks (qb fastest,
     // then b, qa, a), dY = Y-layout blocks (qa fastest, then a, qb, b), d3 = gradient blocks
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           k2 = k + 1;
           i2 = 0;
         }
-        if (k2 < d) {
+        if (k2 < d && !single) {
           stage(k2, i2, Sg + (cur ^ 1) * szS, 0);
           if (sizeof(ST) == 4) asm volatile("cp.async.wait_group 1;\n" ::);
         } else if (sizeof(ST) == 4) {
@@ -342,7 +346,11 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           }
         }
         __syncthreads();
-        cur ^= 1;
+        if (single) {
+          if (k2 < d) stage(k2, i2, Sg, 0);  // every thread is past its last read of the buffer
+        } else {
+          cur ^= 1;
+        }
         if (++i >= nk) {
           // split mode: the second halves hand their partial sums to the first halves
           if (ks == 2) {
@@ -480,7 +488,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
       int cur = 0;
       stage(k, 0, Sg, 1);
       for (int i = 0; i < nk; ++i) {
-        if (i + 1 < nk) {
+        if (i + 1 < nk && !single) {
           stage(k, i + 1, Sg + (cur ^ 1) * szS, 1);
           if (sizeof(ST) == 4) asm volatile("cp.async.wait_group 1;\n" ::);
         } else if (sizeof(ST) == 4) {
@@ -630,7 +638,11 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           }
         }
         __syncthreads();
-        cur ^= 1;
+        if (single) {
+          if (i + 1 < nk) stage(k, i + 1, Sg, 1);  // every thread is past its last read of the buffer
+        } else {
+          cur ^= 1;
+        }
       }
       // R at interface k; with an R' split, parts 1.. hand their sums to part 0 through the
       // free X / X^T / Y buffers (nblk blocks of 16 values each, at most three parts)
@@ -685,26 +697,26 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
 
 static int pad4b(int r) { return (r + 3) & ~3; }
 
-size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB) {
+size_t gram_tile_bwd_smem(int na, int nb, int RA, int RB, bool single) {
   const size_t P = (size_t)na * nb, PS = (size_t)RA * RB;
   const size_t szS = (size_t)na * RA * RA + (size_t)nb * RB * RB;
   const size_t QA = RA / 4, QB = RB / 4;
   const size_t tables = 2 * P * QA * QB + na * QA * QA + nb * QB * QB + 512;  // decode + split tables
-  return sizeof(float) * (7 * P * PS + 2 * szS + P) + sizeof(int) * tables;
+  return sizeof(float) * (7 * P * PS + (single ? 1 : 2) * szS + P) + sizeof(int) * tables;
 }
 
 constexpr size_t kGTBMaxSmem = 220 * 1024;
 
 bool gram_tile_bwd_fits(int na, int nb, int RA, int RB) {
-  return na * RA * RA + nb * RB * RB <= 512 * kGTBMaxPF && gram_tile_bwd_smem(na, nb, RA, RB) <= kGTBMaxSmem;
+  return na * RA * RA + nb * RB * RB <= 512 * kGTBMaxPF && gram_tile_bwd_smem(na, nb, RA, RB, false) <= kGTBMaxSmem;
 }
 
 // A tile for the half-size CTAs (256 threads, two CTAs per SM): at most two 4 x 4 blocks per
 // thread and half of an SM's shared memory.
 constexpr size_t kGTBSmallSmem = 110 * 1024;
 
-bool gram_tile_bwd_fits_small(int na, int nb, int RA, int RB) {
-  return na * (RA / 4) * nb * (RB / 4) <= 512 && gram_tile_bwd_smem(na, nb, RA, RB) <= kGTBSmallSmem;
+bool gram_tile_bwd_fits_small(int na, int nb, int RA, int RB, bool single) {
+  return na * (RA / 4) * nb * (RB / 4) <= 512 && gram_tile_bwd_smem(na, nb, RA, RB, single) <= kGTBSmallSmem;
 }
 
 // Largest balanced tile whose buffers fit one CTA (512 threads, 2 blocks per thread).
@@ -761,7 +773,7 @@ t3f_status run_gram_tile_bwd(const TTV& A, const TTV& B, const float* dG, float*
   g.dtype = A.dtype;
   g.scratch = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeader);
   g.scratch_stride = (long long)(A.d + 1) * g.TA * g.TB * g.RA * g.RB;
-  const size_t smem = gram_tile_bwd_smem(g.TA, g.TB, g.RA, g.RB);
+  const size_t smem = gram_tile_bwd_smem(g.TA, g.TB, g.RA, g.RB, false);
   const long long grid = (long long)((A.batch + g.TA - 1) / g.TA) * ((B.batch + g.TB - 1) / g.TB);
   if (A.dtype == T3F_F32) {
     auto kern = k_gram_tile_bwd<float>;
