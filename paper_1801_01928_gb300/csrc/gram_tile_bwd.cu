@@ -54,7 +54,9 @@ __device__ __forceinline__ void fma44b(float (&acc)[4][4], const float4 a, const
 
 constexpr int kGTBMaxPF = 16;  // staging elements per thread and slice (tiles up to 8192 elements)
 
-template <typename ST>
+// MAXB: 4 x 4 blocks of a partial tile per thread (1 or 2); with one, the accumulators of a
+// second block are not allocated, which leaves registers to the K loops
+template <typename ST, int MAXB>
 __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ GramBwdTileArgs g) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_item[8];
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
     {
       int k = 0, i = 0, cur = 0;
       stage(0, 0, Sg, 0);
-      float acc[2][4][4];
+      float acc[MAXB][4][4];
       // with at most half as many 4 x 4 blocks as threads, two threads share a block and split
       // its K range (T: be, M': al); their partial sums of M' are combined at the end of a core
       const int ks = 2 * nblk <= nth ? 2 : 1;
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         const int nk = nmode(k);
         if (i == 0) {
 #pragma unroll
-          for (int q = 0; q < 2; ++q)
+          for (int q = 0; q < MAXB; ++q)
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
+          for (int q = 0; q < MAXB; ++q) {
             const int blk = tid + q * nth;
             if (blk < nblk) {
               const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             }
           }
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
+          for (int q = 0; q < MAXB; ++q) {
             const int blk = ks == 2 ? (q == 0 && hb == 0 ? bb : nblk) : tid + q * nth;
             if (blk < nblk) {
               const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
@@ -477,10 +479,10 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         *reinterpret_cast<float4*>(mt + (size_t)2 * na * RA) = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
         *reinterpret_cast<float4*>(mt + (size_t)3 * na * RA) = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
       }
-      float racc[2][4][4];
+      float racc[MAXB][4][4];
       const int nr = na * QA * nb * QB;
 #pragma unroll
-      for (int q = 0; q < 2; ++q)
+      for (int q = 0; q < MAXB; ++q)
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -543,7 +545,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         __syncthreads();
         // (2) R'[a][al][b][be] += sum_bp X[al][bp] B[be][bp]  (bp range split s2 ways)
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < MAXB; ++q) {
           int blk, part = 0;
           if (s2 == 1) {
             blk = tid + q * nth;
@@ -673,7 +675,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         }
       }
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < MAXB; ++q) {
         const int blk = s2 == 1 ? tid + q * nth : (q == 0 ? rblk : nr);
         if (blk < nr) {
           const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
@@ -776,12 +778,12 @@ t3f_status run_gram_tile_bwd(const TTV& A, const TTV& B, const float* dG, float*
   const size_t smem = gram_tile_bwd_smem(g.TA, g.TB, g.RA, g.RB, false);
   const long long grid = (long long)((A.batch + g.TA - 1) / g.TA) * ((B.batch + g.TB - 1) / g.TB);
   if (A.dtype == T3F_F32) {
-    auto kern = k_gram_tile_bwd<float>;
+    auto kern = k_gram_tile_bwd<float, 2>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
     kern<<<(unsigned)grid, 512, smem, s>>>(g);
   } else {
-    auto kern = k_gram_tile_bwd<__nv_bfloat16>;
+    auto kern = k_gram_tile_bwd<__nv_bfloat16, 2>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
     kern<<<(unsigned)grid, 512, smem, s>>>(g);
@@ -794,7 +796,7 @@ t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, co
                                       const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
                                       const int* gd, const int* perm, const float* dout, const long long* gout_off,
                                       float* dX, float* scratch, long long scratch_stride, size_t smem, int grid,
-                                      int threads, cudaStream_t s) {
+                                      int threads, int maxb, cudaStream_t s) {
   GramBwdTileArgs g;
   memset(&g, 0, sizeof(g));
   g.mode = 1;
@@ -816,17 +818,17 @@ t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, co
   g.scratch = scratch;
   g.scratch_stride = scratch_stride;
   if (smem > 227 * 1024) return T3F_ERR_UNSUPPORTED;
-  if (dtype == T3F_F32) {
-    auto kern = k_gram_tile_bwd<float>;
+  // a list whose tiles have at most one 4 x 4 block per thread runs the one-block form
+  auto go = [&](auto kern) -> t3f_status {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
     kern<<<grid, threads, smem, s>>>(g);
-  } else {
-    auto kern = k_gram_tile_bwd<__nv_bfloat16>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return T3F_ERR_CUDA;
-    kern<<<grid, threads, smem, s>>>(g);
-  }
+    return T3F_OK;
+  };
+  if (dtype == T3F_F32)
+    T3F_CHECK(maxb == 1 ? go(k_gram_tile_bwd<float, 1>) : go(k_gram_tile_bwd<float, 2>));
+  else
+    T3F_CHECK(maxb == 1 ? go(k_gram_tile_bwd<__nv_bfloat16, 1>) : go(k_gram_tile_bwd<__nv_bfloat16, 2>));
   return launch_status();
 }
 
