@@ -604,6 +604,6 @@ extern "C" t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t n
         reinterpret_cast<const int*>(w + P.o_sitems), P.nsitems, shead, reinterpret_cast<const int*>(w + P.o_gs),
         reinterpret_cast<const int*>(w + P.o_gd), reinterpret_cast<const int*>(w + P.o_perm), dout,
         reinterpret_cast<const long long*>(w + P.o_go), dcores, reinterpret_cast<float*>(w + P.o_sscr), P.sstride,
-        P.ssmem, P.sgrid, 256, 2, s));
+        P.ssmem, P.sgrid, 256, 1, s));
   return T3F_OK;
 }

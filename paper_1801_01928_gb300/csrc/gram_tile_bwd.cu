@@ -713,12 +713,12 @@ bool gram_tile_bwd_fits(int na, int nb, int RA, int RB) {
   return na * RA * RA + nb * RB * RB <= 512 * kGTBMaxPF && gram_tile_bwd_smem(na, nb, RA, RB, false) <= kGTBMaxSmem;
 }
 
-// A tile for the half-size CTAs (256 threads, two CTAs per SM): at most two 4 x 4 blocks per
+// A tile for the half-size CTAs (256 threads, two CTAs per SM): at most one 4 x 4 block per
 // thread and half of an SM's shared memory.
 constexpr size_t kGTBSmallSmem = 110 * 1024;
 
 bool gram_tile_bwd_fits_small(int na, int nb, int RA, int RB, bool single) {
-  return na * (RA / 4) * nb * (RB / 4) <= 512 && gram_tile_bwd_smem(na, nb, RA, RB, single) <= kGTBSmallSmem;
+  return na * (RA / 4) * nb * (RB / 4) <= 256 && gram_tile_bwd_smem(na, nb, RA, RB, single) <= kGTBSmallSmem;
 }
 
 // Largest balanced tile whose buffers fit one CTA (512 threads, 2 blocks per thread).
@@ -777,17 +777,18 @@ t3f_status run_gram_tile_bwd(const TTV& A, const TTV& B, const float* dG, float*
   g.scratch_stride = (long long)(A.d + 1) * g.TA * g.TB * g.RA * g.RB;
   const size_t smem = gram_tile_bwd_smem(g.TA, g.TB, g.RA, g.RB, false);
   const long long grid = (long long)((A.batch + g.TA - 1) / g.TA) * ((B.batch + g.TB - 1) / g.TB);
-  if (A.dtype == T3F_F32) {
-    auto kern = k_gram_tile_bwd<float, 2>;
+  // tiles of at most 512 4 x 4 blocks run the one-block-per-thread form
+  const bool one = g.TA * (g.RA / 4) * g.TB * (g.RB / 4) <= 512;
+  auto go = [&](auto kern) -> t3f_status {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
     kern<<<(unsigned)grid, 512, smem, s>>>(g);
-  } else {
-    auto kern = k_gram_tile_bwd<__nv_bfloat16, 2>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return T3F_ERR_CUDA;
-    kern<<<(unsigned)grid, 512, smem, s>>>(g);
-  }
+    return T3F_OK;
+  };
+  if (A.dtype == T3F_F32)
+    T3F_CHECK(one ? go(k_gram_tile_bwd<float, 1>) : go(k_gram_tile_bwd<float, 2>));
+  else
+    T3F_CHECK(one ? go(k_gram_tile_bwd<__nv_bfloat16, 1>) : go(k_gram_tile_bwd<__nv_bfloat16, 2>));
   return launch_status();
 }
 
