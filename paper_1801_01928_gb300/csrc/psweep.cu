@@ -45,11 +45,23 @@ __device__ __forceinline__ void fma4x4(float (&acc)[4][4], const float4 a, const
 }
 
 // stage slice i of an X-side core (r0 x n x r1) as [K][m] (left: K = row, m = col;
-// right: K = col, m = row), zero-padded to RU x RU, with 4-byte asynchronous copies (the
-// elements outside the ranks are zero-filled); the caller commits and waits
+// right: K = col, m = row), zero-padded to RU x RU, with asynchronous copies (the elements
+// outside the ranks are zero-filled): 16 bytes at a time when the rows are contiguous and
+// aligned (left, r1 a multiple of 4, 16-byte aligned core), else 4 bytes; the caller
+// commits and waits
 template <int RU>
 __device__ __forceinline__ void stage_x_slice_async(float* dst, const float* core, int r0, int n, int r1, int i,
                                                     int dir, bool valid) {
+  if (dir == 0 && (r1 & 3) == 0 && (reinterpret_cast<unsigned long long>(core) & 15) == 0) {
+    for (int e4 = threadIdx.x; e4 < RU * RU / 4; e4 += blockDim.x) {
+      const int K = e4 / (RU / 4), m = 4 * (e4 % (RU / 4));
+      const bool ok = valid && K < r0 && m < r1;
+      const float* src = ok ? core + ((long long)K * n + i) * r1 + m : core;
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + 4 * e4);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(ok ? 16 : 0));
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < RU * RU; e += blockDim.x) {
     const int K = e / RU, m = e % RU;
     const int row = dir == 0 ? K : m, col = dir == 0 ? m : K;
