@@ -33,7 +33,7 @@ t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, co
                                       const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
                                       const int* gd, const int* perm, const float* dout, const long long* gout_off,
                                       float* dX, float* scratch, long long scratch_stride, size_t smem, int grid,
-                                      int threads, int maxb, cudaStream_t s);
+                                      int threads, cudaStream_t s);
 
 t3f_status launch_gram_mma_list(int math, const void* cores, int dtype, int dmax, const long long* off,
                                 const int* rk, const int* nmodes, const int* items, int nitems, int* head,
@@ -596,7 +596,7 @@ extern "C" t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t n
         reinterpret_cast<const int*>(w + P.o_bitems), P.nbitems, head, reinterpret_cast<const int*>(w + P.o_gs),
         reinterpret_cast<const int*>(w + P.o_gd), reinterpret_cast<const int*>(w + P.o_perm), dout,
         reinterpret_cast<const long long*>(w + P.o_go), dcores, reinterpret_cast<float*>(w + P.o_scr), P.bstride,
-        P.bsmem, P.bgrid, 512, 1, s));
+        P.bsmem, P.bgrid, 512, s));
   if (P.nsitems > 0)
     T3F_CHECK(launch_gram_tile_bwd_table(
         X->cores, X->dtype, P.dmax, reinterpret_cast<const long long*>(w + P.o_off),
@@ -604,6 +604,6 @@ extern "C" t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t n
         reinterpret_cast<const int*>(w + P.o_sitems), P.nsitems, shead, reinterpret_cast<const int*>(w + P.o_gs),
         reinterpret_cast<const int*>(w + P.o_gd), reinterpret_cast<const int*>(w + P.o_perm), dout,
         reinterpret_cast<const long long*>(w + P.o_go), dcores, reinterpret_cast<float*>(w + P.o_sscr), P.sstride,
-        P.ssmem, P.sgrid, 256, 1, s));
+        P.ssmem, P.sgrid, 256, s));
   return T3F_OK;
 }

@@ -54,9 +54,11 @@ __device__ __forceinline__ void fma44b(float (&acc)[4][4], const float4 a, const
 
 constexpr int kGTBMaxPF = 16;  // staging elements per thread and slice (tiles up to 8192 elements)
 
-// MAXB: 4 x 4 blocks of a partial tile per thread (1 or 2); with one, the accumulators of a
-// second block are not allocated, which leaves registers to the K loops
-template <typename ST, int MAXB>
+// Every tile has at most as many 4 x 4 blocks of a partial tile as the CTA has threads, so a
+// thread holds the accumulators of one block (a second would cost registers and spills).
+constexpr int MAXB = 1;
+
+template <typename ST>
 __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ GramBwdTileArgs g) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_item[8];
@@ -721,7 +723,7 @@ bool gram_tile_bwd_fits_small(int na, int nb, int RA, int RB, bool single) {
   return na * (RA / 4) * nb * (RB / 4) <= 256 && gram_tile_bwd_smem(na, nb, RA, RB, single) <= kGTBSmallSmem;
 }
 
-// Largest balanced tile whose buffers fit one CTA (512 threads, 2 blocks per thread).
+// Largest balanced tile whose buffers fit one CTA (512 threads, one block per thread).
 void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB) {
   *TA = 1;
   *TB = 1;
@@ -730,7 +732,7 @@ void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   for (int ta = 1; ta <= 16 && ta <= batchA; ++ta)
     for (int tb = 1; tb <= 16 && tb <= batchB; ++tb) {
-      if (ta * (RA / 4) * tb * (RB / 4) > 1024) continue;
+      if (ta * (RA / 4) * tb * (RB / 4) > 512) continue;  // one 4 x 4 block per thread
       if (!gram_tile_bwd_fits(ta, tb, RA, RB)) continue;
       const long long tiles = (long long)((batchA + ta - 1) / ta) * ((batchB + tb - 1) / tb);
       const long long per_sm = (tiles + sms - 1) / sms;
@@ -777,18 +779,13 @@ t3f_status run_gram_tile_bwd(const TTV& A, const TTV& B, const float* dG, float*
   g.scratch_stride = (long long)(A.d + 1) * g.TA * g.TB * g.RA * g.RB;
   const size_t smem = gram_tile_bwd_smem(g.TA, g.TB, g.RA, g.RB, false);
   const long long grid = (long long)((A.batch + g.TA - 1) / g.TA) * ((B.batch + g.TB - 1) / g.TB);
-  // tiles of at most 512 4 x 4 blocks run the one-block-per-thread form
-  const bool one = g.TA * (g.RA / 4) * g.TB * (g.RB / 4) <= 512;
   auto go = [&](auto kern) -> t3f_status {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
     kern<<<(unsigned)grid, 512, smem, s>>>(g);
     return T3F_OK;
   };
-  if (A.dtype == T3F_F32)
-    T3F_CHECK(one ? go(k_gram_tile_bwd<float, 1>) : go(k_gram_tile_bwd<float, 2>));
-  else
-    T3F_CHECK(one ? go(k_gram_tile_bwd<__nv_bfloat16, 1>) : go(k_gram_tile_bwd<__nv_bfloat16, 2>));
+  T3F_CHECK(A.dtype == T3F_F32 ? go(k_gram_tile_bwd<float>) : go(k_gram_tile_bwd<__nv_bfloat16>));
   return launch_status();
 }
 
@@ -797,7 +794,7 @@ t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, co
                                       const int* nmodes, const int* items, int nitems, int* head, const int* gstart,
                                       const int* gd, const int* perm, const float* dout, const long long* gout_off,
                                       float* dX, float* scratch, long long scratch_stride, size_t smem, int grid,
-                                      int threads, int maxb, cudaStream_t s) {
+                                      int threads, cudaStream_t s) {
   GramBwdTileArgs g;
   memset(&g, 0, sizeof(g));
   g.mode = 1;
@@ -819,17 +816,14 @@ t3f_status launch_gram_tile_bwd_table(const void* cores, int dtype, int dmax, co
   g.scratch = scratch;
   g.scratch_stride = scratch_stride;
   if (smem > 227 * 1024) return T3F_ERR_UNSUPPORTED;
-  // a list whose tiles have at most one 4 x 4 block per thread runs the one-block form
+  // the list's tiles have at most one 4 x 4 block per thread
   auto go = [&](auto kern) -> t3f_status {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
     kern<<<grid, threads, smem, s>>>(g);
     return T3F_OK;
   };
-  if (dtype == T3F_F32)
-    T3F_CHECK(maxb == 1 ? go(k_gram_tile_bwd<float, 1>) : go(k_gram_tile_bwd<float, 2>));
-  else
-    T3F_CHECK(maxb == 1 ? go(k_gram_tile_bwd<__nv_bfloat16, 1>) : go(k_gram_tile_bwd<__nv_bfloat16, 2>));
+  T3F_CHECK(dtype == T3F_F32 ? go(k_gram_tile_bwd<float>) : go(k_gram_tile_bwd<__nv_bfloat16>));
   return launch_status();
 }
 
