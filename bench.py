@@ -202,6 +202,28 @@ class Workload:
         for k, v in self.host.items():
             self.devbuf[k].copy_(v, non_blocking=True)
 
+    # inputs in the order the step first reads them (the orthogonalisation chain's X5 group
+    # early, as its stream reaches orth5 after about a millisecond)
+    UPLOAD_GROUPS = (("X2", "idx", "y"), ("X5", "Z5", "c5"), ("A3", "B3", "dG"), ("Am", "xv", "dC"),
+                     ("X4", "dG4"))
+
+    def upload_async(self, copy_stream):
+        """Every input copied from pinned host memory on `copy_stream`, one group at a time;
+        returns input name -> CUDA event recorded after its group, so each operation waits
+        for its own inputs only and the copies of later groups overlap earlier compute."""
+        torch = self.torch
+        ready = {}
+        with torch.cuda.stream(copy_stream):
+            for grp in self.UPLOAD_GROUPS:
+                for k in grp:
+                    self.devbuf[k].copy_(self.host[k], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+                for k in grp:
+                    ready[k] = ev
+        assert set(ready) == set(self.host), "every input belongs to one upload group"
+        return ready
+
     def ragged(self):
         return self.t3f.RaggedTT(self.devbuf["X4"], *self.r4meta)
 
@@ -299,7 +321,7 @@ class Workload:
         return tot
 
 
-def run_step(w, timers=None, stream=None, side=None):
+def run_step(w, timers=None, stream=None, side=None, ready=None):
     """All hot-path operations once; returns the outputs a user reads back.
 
     With `side` (a second CUDA stream) the orthogonalisation chain (orth2 -> Riemannian
@@ -307,10 +329,17 @@ def run_step(w, timers=None, stream=None, side=None):
     operations, is issued first on `side` and runs concurrently with the rest on the main
     stream: the FP64 orthogonalisation is a chain of small QR steps on one 16-CTA cluster, so
     the other SMs take the independent work meanwhile. Without `side` every operation runs
-    in order on the main stream (the per-operation timings come from that form)."""
+    in order on the main stream (the per-operation timings come from that form). With
+    `ready` (input name -> event of its host-to-device copy) each operation first waits for
+    the copies of its own inputs."""
     t3f, torch = w.t3f, w.torch
     out = {}
     main = stream if stream is not None else torch.cuda.current_stream(w.dev)
+
+    def need(st, *keys):
+        if ready is not None:
+            for ev in {id(ready[k]): ready[k] for k in keys}.values():
+                st.wait_event(ev)
 
     def timed(name, fn, st):
         if timers is not None:
@@ -331,8 +360,10 @@ def run_step(w, timers=None, stream=None, side=None):
     res = {}
 
     def orth_chain(st):
+        need(st, "X2", "idx", "y")
         U2, V2 = timed("orth2", lambda: t3f.orthogonalize(X2), st)
         res["dU2"], _ = timed("rgrad", lambda: t3f.gather_backward(None, idx, y=y, riemannian=True, U=U2, V=V2), st)
+        need(st, "X5", "Z5", "c5")
         U5, V5 = timed("orth5", lambda: t3f.orthogonalize(X5), st)
         res["dU5"] = timed("psum", lambda: t3f.project_sum(U5, V5, Z5, c5), st)
         # adjoint of 1/2 ||project_sum||^2: the cotangent of the coordinates is dU5 itself
@@ -342,16 +373,20 @@ def run_step(w, timers=None, stream=None, side=None):
         side.wait_stream(main)
         with torch.cuda.stream(side):
             orth_chain(side)
+    need(main, "X2", "idx", "y")
     dX, loss = timed("completion", lambda: t3f.gather_backward(X2, idx, y=y, want_loss=True), main)
     if side is None:
         orth_chain(main)
     A3, B3 = w.tt("A3"), w.tt("B3")
+    need(main, "A3", "B3", "dG")
     G = timed("gram", lambda: t3f.gram(A3, B3), main)
     dA, dB = timed("gram_bwd", lambda: t3f.gram_backward(A3, B3, w.devbuf["dG"]), main)
     nrm = timed("norm", lambda: t3f.norm(A3), main)
     Am, xv = w.tt("Am"), w.tt("xv")
+    need(main, "Am", "xv", "dC")
     C = timed("matvec", lambda: t3f.matvec(Am, xv), main)
     dAm, dxv = timed("matvec_bwd", lambda: t3f.matvec_backward(Am, xv, w.tt("dC")), main)
+    need(main, "X4", "dG4")
     timed("uneven", lambda: w.graph4f.replay(), main)
     timed("uneven_bwd", lambda: w.graph4b.replay(), main)
     if side is not None:
@@ -605,6 +640,7 @@ def gpu_arm(args):
     step_flops = sum(flops.values())
     stream = torch.cuda.current_stream(dev)
     side = torch.cuda.Stream(dev)
+    copy_stream = torch.cuda.Stream(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     for _ in range(args.warmup):
@@ -660,8 +696,9 @@ def gpu_arm(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        w.upload(stream)
-        out = run_step(w, None, stream, side)
+        copy_stream.wait_stream(stream)
+        ready = w.upload_async(copy_stream)
+        out = run_step(w, None, stream, side, ready)
         host_out = {k: v.to("cpu", non_blocking=True) for k, v in out.items() if k != "_bulk"}
         e1.record(stream)
         e2e_ev.append((e0, e1))
