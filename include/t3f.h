@@ -283,9 +283,10 @@ typedef struct {
  * are concatenated in `out` (device float). norms (device double [count], nullable) receives
  * sqrt(G_g[a][a]) in FP64.
  * Scheduling: the objects of every group are ordered by rank into buckets {<=8, <=16, <=32,
- * <=64}; tiles[b] (host int32[4], NULL = built-in defaults, each in 1..16) is the tile side
- * used for bucket b. The upper triangle of pairs is cut into tiles, sorted by cost and drained
- * by ONE persistent launch.
+ * <=64}; tiles[b] (host int32[4], NULL = built-in defaults, each in 1..16) caps the tile side
+ * for bucket b. Within a bucket pair, runs of rank-sorted objects grow up to that side while
+ * their tile (padded to the run's own largest rank) fits one CTA; the upper triangle of pairs
+ * is cut into such tiles, sorted by cost and drained by ONE persistent launch.
  * math (t3f_math): FP32 = CUDA-core FP32 throughout. TF32 (F32 cores) / BF16 (F32 or BF16
  * cores): every pair runs on the tensor cores (operands rounded to TF32 / BF16, FP32
  * accumulation) in tiles of (128/RA) x (128/RB) pairs, RA and RB = 16, 16, 32, 64 for the
@@ -310,9 +311,11 @@ t3f_status t3f_gram_groups(const t3f_tt_ragged* X, int32_t ngroups, const int32_
  * Adjoint of t3f_gram_groups: dcores (device float, the layout of X's cores with F32
  * elements) receives the cotangent of sum_g sum_ab dout_g[a][b] <X_a, X_b> for the
  * concatenated per-group cotangents dout (device float, like `out`). FP32 CUDA-core
- * arithmetic: one persistent launch of the tiled adjoint over a second work list (tiles sized
- * per bucket so that the adjoint's seven partial tiles fit one CTA); every off-diagonal tile
- * uses the symmetrised cotangent dout[a][b] + dout[b][a]. Requires the same prepared `ws`.
+ * arithmetic: the tiled adjoint drains its own work lists (runs of rank-sorted objects cut so
+ * that a tile's seven partial tiles fit one CTA, side at most 16 whatever `tiles`): tiles that
+ * need more than half an SM's shared memory in one persistent launch of 512-thread CTAs, the
+ * rest in a second of 256-thread CTAs, two per SM. Every off-diagonal tile uses the
+ * symmetrised cotangent dout[a][b] + dout[b][a]. Requires the same prepared `ws`.
  */
 t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t ngroups,
                                     const int32_t* gstart, const int32_t* tiles,
