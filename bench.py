@@ -325,6 +325,20 @@ class Workload:
         return tot
 
 
+def combine_ranks(dev_ms, e2e_ms, world, step_flops, device):
+    """Whole-job numbers of `world` replicas: the per-rank step times are reduced with MAX
+    (the slowest replica sets the step time) and the job processes `world` steps' FLOPs per
+    step. Returns (dev_ms, e2e_ms, value GFLOP/s, e2e GFLOP/s)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms, e2e_ms = float(t[0]), float(t[1])
+    return (dev_ms, e2e_ms, world * step_flops / (dev_ms * 1e-3) / 1e9,
+            world * step_flops / (e2e_ms * 1e-3) / 1e9)
+
+
 def run_step(w, timers=None, stream=None, side=None, ready=None):
     """All hot-path operations once; returns the outputs a user reads back.
 
@@ -712,13 +726,7 @@ def gpu_arm(args):
     barrier()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
 
-    # max over ranks
-    t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms, e2e_ms = float(t[0]), float(t[1])
-    value = world * step_flops / (dev_ms * 1e-3) / 1e9
-    e2e_value = world * step_flops / (e2e_ms * 1e-3) / 1e9
+    dev_ms, e2e_ms, value, e2e_value = combine_ranks(dev_ms, e2e_ms, world, step_flops, dev)
 
     # dominant operation and its roofline (FP32 CUDA-core pipe)
     dom = max(op_ms, key=op_ms.get)
