@@ -12,6 +12,17 @@
 // dA / dB of a slice are added to the global gradients with atomics (other tiles share the
 // objects). Ranks are zero-padded to multiples of 4; the same kernel takes tiles from the
 // block index (uniform batches) or from a work list (grouped ragged collections).
+//
+// Every tile has at most one 4 x 4 block of a partial tile per thread. Block indices come
+// from per-tile decode tables in shared memory; the products of a core stop at the tile's
+// effective ranks on that core (the largest rank of its objects, padded to 4), so the
+// boundary cores (outer rank 1) cost little. Where a phase has fewer blocks than threads,
+// K ranges are split across threads of different warps (left sweep: T and M' halves; right
+// sweep: R' and dA / dB parts chosen per tile by a K-step count). Core slices are staged by
+// lines (rows, or columns when transposed) shared by 4-16 threads with 4-byte asynchronous
+// copies, into two buffers, or into one for tiles that fit half an SM only that way (the next
+// slice is then issued after a slice's last barrier). The kernel runs with 512 threads (one
+// CTA per SM) or 256 (two per SM, tiles of half an SM's shared memory).
 #include "t3f_internal.cuh"
 
 namespace t3f {
