@@ -5,10 +5,12 @@
 // the update M' = sum_i A_i^T (M B_i) is two batched products with 4 x 4 register blocks:
 //   GEMM1  T[a][al][b][bp]   = sum_be M[a][al][b][be] B_b,i[be][bp]     (stacked over a)
 //   GEMM2  M'[a][ap][b][bp] += sum_al A_a,i[al][ap] T[a][al][b][bp]     (stacked over b)
-// Ranks are zero-padded to multiples of 4 (RA, RB). The operands of the next slice are
-// loaded into registers while the current slice computes. The same kernel serves uniform
-// batches (tile from blockIdx) and ragged, rank-bucketed groups of objects (tiles taken from
-// a work list by persistent CTAs, see gram_groups.cu).
+// Ranks are zero-padded to multiples of 4 (RA, RB). The next slice is staged into a second
+// shared-memory buffer with 4-byte asynchronous copies (issued by rows shared by 4-16
+// threads) while the current slice computes, and the products of a core stop at the tile's
+// effective ranks on that core (boundary cores, outer rank 1, cost little). The same kernel
+// serves uniform batches (tile from blockIdx) and ragged, rank-bucketed groups of objects
+// (tiles taken from a work list by persistent CTAs, see gram_groups.cu).
 #include "t3f_internal.cuh"
 
 namespace t3f {
