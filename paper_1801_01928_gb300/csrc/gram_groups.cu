@@ -199,12 +199,10 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
     for (int x = pos0; x < pos0 + n; ++x) R = std::max(R, (rmax[P->sorted[x]] + 3) & ~3);
     return R;
   };
-  auto make_items = [&](const int* cap, bool bwd, std::vector<int>* out, size_t* smem_out,
-                        long long* pmax_out) -> t3f_status {
+  auto make_items = [&](const int* cap, std::vector<int>* out, size_t* smem_out, long long* pmax_out) -> t3f_status {
     // a tile must fit one CTA of 512 threads: at most 2 blocks each, staging and shared memory
     auto tile_ok = [&](int na, int nb, int RA, int RB) {
       if (na * (RA / 4) * nb * (RB / 4) > 1024) return false;
-      if (bwd) return gram_tile_bwd_fits(na, nb, RA, RB);
       return gram_tile_smem(na, nb, RA, RB) <= 200 * 1024 && na * RA * RA + nb * RB * RB <= 512 * 16;
     };
     auto cut = [&](const Range& Rg, int side_max, std::vector<std::pair<int, int>>* runs) {
@@ -254,7 +252,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
                   continue;
                 }
                 It it;
-                it.cost = (double)na * nb * RA * RB * (bwd ? 3.0 * RA + 4.0 * RB : (double)(RA + RB)) * slices;
+                it.cost = (double)na * nb * RA * RB * (RA + RB) * slices;
                 it.v[0] = g;
                 it.v[1] = a0;
                 it.v[2] = na;
@@ -264,7 +262,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
                 it.v[6] = RB;
                 it.v[7] = sym;
                 its.push_back(it);
-                smem = std::max(smem, bwd ? gram_tile_bwd_smem(na, nb, RA, RB, false) : gram_tile_smem(na, nb, RA, RB));
+                smem = std::max(smem, gram_tile_smem(na, nb, RA, RB));
                 pmax = std::max(pmax, (long long)na * nb * RA * RB);
               }
             }
@@ -281,7 +279,7 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
   };
   size_t smem = 0;
   long long pmax = 0;
-  T3F_CHECK(make_items(tl, false, &P->items, &smem, &pmax));
+  T3F_CHECK(make_items(tl, &P->items, &smem, &pmax));
   P->nitems = (int)(P->items.size() / 8);
   // tensor-core tiles for every bucket pair p <= q: the a side pads to RA = 16 / 16 / 32 / 64
   // (bucket p), the b side to RB (bucket q); (128 / RA) x (128 / RB) pairs per tile
