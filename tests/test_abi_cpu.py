@@ -115,3 +115,46 @@ def test_packed_size_and_workspace(clib):
     assert clib.t3f_workspace_size(5, ctypes.byref(X), None, 1000) > clib.t3f_workspace_size(4, ctypes.byref(X), None, 1000)
     assert clib.t3f_workspace_size(10, ctypes.byref(X), ctypes.byref(A), 0) > 0
     assert clib.t3f_workspace_size(99, ctypes.byref(X), None, 0) == 0
+
+
+def _ragged_meta(t3f, shapes):
+    """A RaggedTT descriptor for the given (modes, ranks) per object over a dummy host buffer:
+    the grouped-Gram planner reads shapes only."""
+    torch = pytest.importorskip("torch")
+    dims = [len(m) for m, _ in shapes]
+    modes = [list(m) for m, _ in shapes]
+    ranks = [list(r) for _, r in shapes]
+    offs, o = [], 0
+    for m, r in shapes:
+        offs.append(o)
+        o += sum(r[k] * m[k] * r[k + 1] for k in range(len(m)))
+    return t3f.RaggedTT(torch.zeros(1), dims, modes, ranks, offs)
+
+
+def test_gram_groups_planner_on_host(clib):
+    # the whole work-list planner (rank-adaptive forward tiles, the adjoint's two lists) runs
+    # on the host: the bench-size uneven batch, per-core varying ranks, d = 1 and n = 1 groups,
+    # every tile-side cap; an out-of-range cap is rejected (size 0)
+    import paper_1801_01928_gb300 as t3f
+    cfg = S.config4()
+    shapes, gstart = [], [0]
+    for grp in cfg.groups:
+        for r in grp.ranks:
+            shapes.append(([grp.n] * grp.d, S.tt_ranks(grp.d, int(r))))
+        gstart.append(len(shapes))
+    rng = np.random.default_rng(7)
+    for d, n in ((1, [5]), (2, [1, 3]), (5, [2, 3, 2, 2, 3])):
+        for _ in range(9):
+            shapes.append((n, [1] + [int(rng.integers(1, 65)) for _ in range(d - 1)] + [1]))
+        gstart.append(len(shapes))
+    X = _ragged_meta(t3f, shapes)
+    gs = (ctypes.c_int32 * len(gstart))(*gstart)
+    sizes = []
+    for tiles in (None, (16, 10, 4, 8), (1, 1, 1, 1), (16, 16, 16, 16)):
+        tl = None if tiles is None else (ctypes.c_int32 * 4)(*tiles)
+        ws = clib.t3f_gram_groups_workspace_size(ctypes.byref(X.desc()), len(gstart) - 1, gs, tl)
+        assert ws > 0, tiles
+        sizes.append(ws)
+    assert len(set(sizes)) > 1  # the caps change the forward work list
+    bad = (ctypes.c_int32 * 4)(16, 0, 4, 8)
+    assert clib.t3f_gram_groups_workspace_size(ctypes.byref(X.desc()), len(gstart) - 1, gs, bad) == 0
