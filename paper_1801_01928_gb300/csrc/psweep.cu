@@ -402,7 +402,7 @@ struct PGradFastArgs {
 };
 
 template <int RU>
-__global__ void __launch_bounds__(256) k_pgrad(const __grid_constant__ PGradFastArgs a) {
+__global__ void __launch_bounds__(RU == 32 ? 512 : 256) k_pgrad(const __grid_constant__ PGradFastArgs a) {
   extern __shared__ __align__(16) float sm[];
   constexpr int QB = kRZ / 4, G = (RU / 4) * QB, TS = RU * kRZ;
   const TTV& Z = a.Z;
@@ -642,7 +642,7 @@ static t3f_status launch_pgrad_t(PGradFastArgs& a, cudaStream_t s) {
   const size_t TS = (size_t)RU * kRZ;
   const size_t smem = sizeof(float) * ((size_t)3 * a.SPLIT * RU * RU + (size_t)a.J * 4 * TS + (size_t)a.J * a.SPLIT * 2 * TS);
   const int G = (RU / 4) * (kRZ / 4);
-  if (smem > 227 * 1024 || a.J * a.SPLIT * G > 256) return T3F_ERR_UNSUPPORTED;
+  if (smem > 227 * 1024 || a.J * a.SPLIT * G > (RU == 32 ? 512 : 256)) return T3F_ERR_UNSUPPORTED;
   auto kern = k_pgrad<RU>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return T3F_ERR_CUDA;
@@ -676,7 +676,9 @@ t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V,
   a.SPLIT = 4;
   while (a.SPLIT > 1 && G * a.SPLIT > 512) a.SPLIT /= 2;
   a.J = 512 / (G * a.SPLIT);
-  if (a.J > 4) a.J = 4;
+  // objects per CTA: the X slices a CTA stages serve all of them (8 at RU = 32, where the
+  // kernel's registers allow 512 threads)
+  if (a.J > (RU == 32 ? 8 : 4)) a.J = RU == 32 ? 8 : 4;
   a.ntiles = (Z.batch + a.J - 1) / a.J;
   switch (RU) {
     case 8: return launch_pgrad_t<8>(a, s);
