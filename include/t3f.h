@@ -168,11 +168,18 @@ t3f_status t3f_gather(const t3f_tt* X, const int32_t* idx, int64_t N, const floa
  * partial it reads. Calls whose work overlaps on the GPU (e.g. issued on two streams with no
  * ordering between them) race on the array. Returns T3F_ERR_WORKSPACE when a launch would
  * need more scratch than T3F_NOALLOC_SCRATCH_BYTES (a device with more than about 1000
- * SMs). Calls no allocating routine.
+ * SMs). Calls no allocating routine. An out-of-range index is clamped on the device, as in
+ * t3f_gather, and recorded in the array's error word: read it with
+ * t3f_gather_noalloc_status() after the call (and before the next one on that device).
  */
 #define T3F_NOALLOC_SCRATCH_BYTES 65536
 t3f_status t3f_gather_noalloc(const t3f_tt* X, const int32_t* idx, int64_t N, const float* y,
                               float* vals, double* loss, t3f_stream_t stream);
+
+/* Device-side status of the last t3f_gather_noalloc call on the current device (the error
+ * word of its scratch array): T3F_OK, or T3F_ERR_ARG if an index tuple was out of range.
+ * Synchronises `stream`; allocates nothing. */
+t3f_status t3f_gather_noalloc_status(t3f_stream_t stream);
 
 /*
  * Adjoint of the gather (paper Section 3.2, Riemannian autodiff, for the completion loss).

@@ -55,6 +55,7 @@ _SIGS = {
     "t3f_gram_backward": (ctypes.c_int32, [_P, _P, _VP, _P, _P, _VP, _SZ, _VP]),
     "t3f_gather": (ctypes.c_int32, [_P, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "t3f_gather_noalloc": (ctypes.c_int32, [_P, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
+    "t3f_gather_noalloc_status": (ctypes.c_int32, [_VP]),
     "t3f_gather_backward": (ctypes.c_int32, [_P, _VP, ctypes.c_int64, _VP, _VP, _VP, _P,
                                              ctypes.c_int32, _P, _P, _VP, _SZ, _VP]),
     "t3f_matvec": (ctypes.c_int32, [_P, _P, _P, _VP, _SZ, _VP]),

@@ -11,6 +11,7 @@
 // suffix vectors of its tuple in shared memory, evaluates the residual, then walks the
 // prefix and scatters the outer products into a per-CTA shared accumulator; a second
 // kernel reduces the per-CTA partials in a fixed order.
+#include <atomic>
 #include <mutex>
 
 #include "t3f_internal.cuh"
@@ -537,13 +538,22 @@ static int gather_grid(long long N, int maxCtas) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// SM count of the current device, looked up once per device index.
 static int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 152;
+  }
+  int sms = cache[dev].load(std::memory_order_relaxed);
+  if (sms <= 0) {
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+      cudaGetLastError();
+      return 152;
+    }
+    cache[dev].store(sms, std::memory_order_relaxed);
   }
   return sms;
 }
@@ -825,21 +835,30 @@ namespace t3f {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[T3F_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kNoAllocMaxDevices = 64;
-static std::once_flag g_noalloc_once[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu[kNoAllocMaxDevices];
 static void* g_noalloc_ptr[kNoAllocMaxDevices];
-static cudaError_t g_noalloc_err[kNoAllocMaxDevices];
 
 // Device address of the scratch array on the current device. The array's name in host
-// code is only a host-side stand-in, so the address is looked up once per device (with
-// that device current) and cached.
+// code is only a host-side stand-in, so the address is looked up with that device current
+// and cached per device. Only a successful lookup is cached: a failed one (for example a
+// first call made while a stream is being captured) clears the runtime's pending error and
+// is retried by the next call.
 static t3f_status noalloc_scratch(void** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return T3F_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return T3F_ERR_CUDA;
+  }
   if (dev < 0 || dev >= kNoAllocMaxDevices) return T3F_ERR_UNSUPPORTED;
-  std::call_once(g_noalloc_once[dev], [dev]() {
-    g_noalloc_err[dev] = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
-  });
-  if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_ptr[dev]) return T3F_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu[dev]);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return T3F_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
   *out = g_noalloc_ptr[dev];
   return T3F_OK;
 }
@@ -858,4 +877,13 @@ extern "C" t3f_status t3f_gather_noalloc(const t3f_tt* X, const int32_t* idx, in
   T3F_CHECK(noalloc_scratch(&scratch));
   // the existing entry point clears the error word and overwrites every partial it reads
   return t3f_gather(X, idx, N, y, vals, loss, scratch, T3F_NOALLOC_SCRATCH_BYTES, stream);
+}
+
+// The error word at the start of the shared scratch array: the device-side status of the
+// last t3f_gather_noalloc call on this device (an index tuple out of range reads back as
+// T3F_ERR_ARG). Synchronises `stream`.
+extern "C" t3f_status t3f_gather_noalloc_status(t3f_stream_t stream) {
+  void* scratch = nullptr;
+  T3F_CHECK(noalloc_scratch(&scratch));
+  return t3f_device_status(scratch, stream);
 }

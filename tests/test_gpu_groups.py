@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 import synth as S
-from tests._util import TOL, rel_err, rel_err_cores, round32, round_bf16
+from tests._util import TOL, assert_gram_blocks, rel_err, rel_err_cores, round32, round_bf16, sampled_gram_errs
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -32,6 +32,10 @@ def as_f32(objs):
     return [round32(o) for o in objs]
 
 
+def sizes_of(gstart):
+    return [gstart[g + 1] - gstart[g] for g in range(len(gstart) - 1)]
+
+
 def oracle_groups(objs, gstart):
     out = []
     for g in range(len(gstart) - 1):
@@ -47,7 +51,7 @@ def test_gram_groups_forward_norms_backward(lib):
     ws = lib.gram_groups_prepare(X, gstart)
     G, nrm = lib.gram_groups(X, gstart, ws)
     ref = oracle_groups(objs, gstart)
-    assert rel_err(G.cpu().numpy(), ref) < TOL["fp32"]
+    assert_gram_blocks(G.cpu().numpy(), ref, sizes_of(gstart), TOL["fp32"])
     assert rel_err(nrm.cpu().numpy(), [O.norm(o) for o in objs]) < TOL["fp32"]
     rng = np.random.default_rng(401)
     dout = rng.normal(size=G.numel()).astype(np.float32)
@@ -85,7 +89,7 @@ def test_gram_groups_varying_core_ranks(lib):
     X = lib.RaggedTT.from_objects([[np.asarray(c, np.float32) for c in o] for o in objs])
     ws = lib.gram_groups_prepare(X, gstart)
     G, nrm = lib.gram_groups(X, gstart, ws)
-    assert rel_err(G.cpu().numpy(), oracle_groups(objs, gstart)) < TOL["fp32"]
+    assert_gram_blocks(G.cpu().numpy(), oracle_groups(objs, gstart), sizes_of(gstart), TOL["fp32"])
     assert rel_err(nrm.cpu().numpy(), [O.norm(o) for o in objs]) < TOL["fp32"]
     dout = rng.normal(size=G.numel()).astype(np.float32)
     dX = lib.gram_groups_backward(X, gstart, ws, torch.tensor(dout, device="cuda"))
@@ -108,10 +112,10 @@ def test_gram_groups_bf16_storage(lib):
     X = lib.RaggedTT.from_objects([[torch.tensor(np.asarray(c)) for c in o] for o in objs_b], dtype=torch.bfloat16)
     ws = lib.gram_groups_prepare(X, gstart)
     G, nrm = lib.gram_groups(X, gstart, ws)
-    assert rel_err(G.cpu().numpy(), oracle_groups(objs_b, gstart)) < TOL["bf16"]
+    ref = oracle_groups(objs_b, gstart)
     assert rel_err(nrm.cpu().numpy(), [O.norm(o) for o in objs_b]) < TOL["bf16"]
-    # the arithmetic is FP32 on the rounded inputs: far inside the BF16 tolerance
-    assert rel_err(G.cpu().numpy(), oracle_groups(objs_b, gstart)) < 1e-5
+    # the arithmetic is FP32 on the rounded inputs: inside the FP32 tolerance
+    assert_gram_blocks(G.cpu().numpy(), ref, sizes_of(gstart), TOL["fp32"])
 
 
 def test_gram_groups_autotune_and_graph_replay(lib):
@@ -139,9 +143,27 @@ def test_gram_groups_autotune_and_graph_replay(lib):
     dX.zero_()
     graph.replay()
     torch.cuda.synchronize()
-    assert rel_err(G.cpu().numpy(), G0.cpu().numpy()) < 1e-6
+    assert_gram_blocks(G.cpu().numpy(), G0.cpu().numpy(), sizes_of(gstart), 1e-6)
     assert rel_err(dX.cpu().numpy(), d0.cpu().numpy()) < 1e-5
-    assert rel_err(G.cpu().numpy(), oracle_groups(objs, gstart)) < TOL["fp32"]
+    assert_gram_blocks(G.cpu().numpy(), oracle_groups(objs, gstart), sizes_of(gstart), TOL["fp32"])
+
+
+def _config4_sampled_check(G, objs, gstart, rng, tol):
+    # per group: both end diagonals and 10 distinct-object pairs, scored separately (the
+    # off-diagonal inner products are 1e-8..1e-2 of the diagonal ones)
+    off = 0
+    for g in range(len(gstart) - 1):
+        Sg = gstart[g + 1] - gstart[g]
+        pairs = [(0, 0), (Sg - 1, Sg - 1)]
+        while len(pairs) < 12:
+            a, b = (int(v) for v in rng.integers(0, Sg, 2))
+            if a != b:
+                pairs.append((a, b))
+        got = [G[off + a * Sg + b] for a, b in pairs]
+        want = [O.dot(objs[gstart[g] + a], objs[gstart[g] + b]) for a, b in pairs]
+        ed, eo = sampled_gram_errs(got, want, [a == b for a, b in pairs])
+        assert ed < tol and eo < tol, (g, ed, eo)
+        off += Sg * Sg
 
 
 def test_gram_groups_config4_sampled(lib):
@@ -153,16 +175,7 @@ def test_gram_groups_config4_sampled(lib):
     X = lib.RaggedTT.from_objects([[np.asarray(c, np.float32) for c in o] for o in objs])
     ws = lib.gram_groups_prepare(X, gstart)
     G, nrm = lib.gram_groups(X, gstart, ws)
-    G = G.cpu().numpy()
-    rng = np.random.default_rng(404)
-    got, want, off = [], [], 0
-    for g in range(len(gstart) - 1):
-        Sg = gstart[g + 1] - gstart[g]
-        for a, b in [(0, 0), (Sg - 1, Sg - 1)] + [tuple(rng.integers(0, Sg, 2)) for _ in range(4)]:
-            got.append(G[off + a * Sg + b])
-            want.append(O.dot(objs[gstart[g] + a], objs[gstart[g] + b]))
-        off += Sg * Sg
-    assert rel_err(got, want) < TOL["fp32"]
+    _config4_sampled_check(G.cpu().numpy(), objs, gstart, np.random.default_rng(404), TOL["fp32"])
 
 
 def test_gram_groups_config4_backward_sampled(lib):
@@ -212,7 +225,7 @@ def test_gram_groups_tensor_cores(lib, math_):
     assert lib.device_status(ws) == 0
     ref = oracle_groups(objs, gstart)
     assert np.isfinite(G.cpu().numpy()).all()
-    assert rel_err(G.cpu().numpy(), ref) < TOL[math_]
+    assert_gram_blocks(G.cpu().numpy(), ref, sizes_of(gstart), TOL[math_])
     assert rel_err(nrm.cpu().numpy(), [O.norm(o) for o in objs]) < TOL[math_]
     # each group matrix is symmetric up to the operand rounding
     off = 0
@@ -233,14 +246,5 @@ def test_gram_groups_config4_bf16_sampled(lib):
     X = lib.RaggedTT.from_objects([[torch.tensor(np.asarray(c)) for c in o] for o in objs], dtype=torch.bfloat16)
     ws = lib.gram_groups_prepare(X, gstart)
     G, nrm = lib.gram_groups(X, gstart, ws, math="bf16")
-    G = G.cpu().numpy()
-    rng = np.random.default_rng(406)
-    got, want, off = [], [], 0
-    for g in range(len(gstart) - 1):
-        Sg = gstart[g + 1] - gstart[g]
-        for a, b in [(0, 0), (Sg - 1, Sg - 1)] + [tuple(rng.integers(0, Sg, 2)) for _ in range(4)]:
-            got.append(G[off + a * Sg + b])
-            want.append(O.dot(objs[gstart[g] + a], objs[gstart[g] + b]))
-        off += Sg * Sg
-    assert rel_err(got, want) < TOL["bf16"]
+    _config4_sampled_check(G.cpu().numpy(), objs, gstart, np.random.default_rng(406), TOL["bf16"])
     assert rel_err(nrm.cpu().numpy()[[0, 100, 511]], [O.norm(objs[i]) for i in (0, 100, 511)]) < TOL["bf16"]

@@ -11,7 +11,7 @@ import pytest
 
 import oracle as O
 import synth as S
-from tests._util import TOL, objects, rel_err, round32, round_bf16
+from tests._util import TOL, assert_gram_blocks, objects, rel_err, round32, round_bf16
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -65,3 +65,5 @@ def test_gram_mma_self_gram_diagonal(lib):
     nrm = np.array([O.norm(o) for o in objects(A)])
     assert rel_err(np.diag(G), nrm ** 2) < TOL["tf32"]
     assert rel_err(G, G.T) < TOL["tf32"]
+    # diagonal and off-diagonal entries scored separately against the oracle
+    assert_gram_blocks(G, O.gram(objects(A), objects(A)), [19], TOL["tf32"])

@@ -244,6 +244,28 @@ def test_project_sum_config5_full(lib):
     assert rel_err_cores(host_objects(dU)[0], ref) < TOL["fp32"]
 
 
+def test_project_sum_config5_invariants_on_gpu(lib):
+    # P o P = P and P_X X = X, checked on the library's own outputs: the tangent vector S of
+    # project_sum (its rank-2r TT built from the GPU's U, V and dU) projected again on the GPU
+    # gives back the same coordinates; X itself projects to dU_k = 0 (k < d), dU_d = U_d.
+    cfg = S.config5()
+    X, Z = round32(cfg.X), round32(cfg.Z)
+    c = cfg.c.astype(np.float32)
+    U, V = _orth(lib, X, torch.float32)
+    dU = lib.project_sum(U, V, dev_tt(lib, Z), torch.tensor(c, device="cuda"))
+    Uh, Vh, dUh = host_objects(U)[0], host_objects(V)[0], host_objects(dU)[0]
+    S_tt = O.tangent_to_tt(Uh, Vh, dUh)
+    assert max(O.tt_ranks_of(S_tt)) <= 2 * max(U.ranks)  # tangent rank <= 2r
+    one = torch.ones(1, device="cuda")
+    dU2 = lib.project_sum(U, V, dev_tt(lib, [s_[None] for s_ in S_tt]), one)
+    assert rel_err_cores(host_objects(dU2)[0], dUh) < TOL["fp32"]
+    dUx = host_objects(lib.project_sum(U, V, dev_tt(lib, X), one))[0]
+    d = len(dUx)
+    scale = np.linalg.norm(Uh[-1])
+    assert max(np.linalg.norm(dUx[k]) for k in range(d - 1)) < TOL["fp32"] * scale
+    assert rel_err(dUx[-1], Uh[-1]) < TOL["fp32"]
+
+
 def test_project_sum_backward(lib):
     cfg = S.config5(batch=37, d=6, n=5, rX=6, rZ=3)
     X, Z = round32(cfg.X), round32(cfg.Z)
@@ -317,6 +339,23 @@ def test_matvec_config3b_sampled(lib):
     Ao, xo = objects(A), objects(x)
     for p in (0, 41, 99):
         assert rel_err_cores(hc[p], O.matvec(Ao[p], xo[p])) < TOL["fp32"]
+
+
+def test_matvec_backward_config3b_sampled(lib):
+    # the rank-100 adjoint the benchmark times, full batch, with a random cotangent of the
+    # product's shape; sampled pairs against the oracle's vjp
+    cfg = S.config3b()
+    A, x = round32(cfg.A), round32(cfg.x)
+    rc = [a * b for a, b in zip(S.tt_ranks(10, 10), S.tt_ranks(10, 10))]
+    rng = np.random.default_rng(112)
+    dC = [rng.normal(size=(100, rc[k], 4, rc[k + 1])).astype(np.float32) for k in range(10)]
+    dA, dx = lib.matvec_backward(dev_tt(lib, A), dev_tt(lib, x), dev_tt(lib, dC))
+    hA, hx = host_objects(dA), host_objects(dx)
+    Ao, xo, Co = objects(A), objects(x), objects(round32(dC))
+    for p in (0, 41, 99):
+        rA, rx = O.matvec_vjp(Ao[p], xo[p], Co[p])
+        assert rel_err_cores(hA[p], rA) < TOL["fp32"], p
+        assert rel_err_cores(hx[p], rx) < TOL["fp32"], p
 
 
 def test_riemannian_grad_config2_full(lib):
