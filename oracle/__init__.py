@@ -4,7 +4,9 @@ A plain, slow, obviously correct NumPy (float64) statement of what the library c
 the TT definition, transfer-matrix sweeps for inner products and Gram matrices, element
 gather and the completion loss with its gradient, TT-matrix x TT-vector, Householder
 orthogonalisation and the Riemannian tangent-space projection (project / project_sum) with
-its adjoint. Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+its adjoint, the tailored tangent-space operations (Gram matrix of tangent vectors,
+projected matrix-by-vector product, linearised Riemannian Hessian of the completion loss)
+and TT rounding. Only the tests, the smoke check and the benchmark's CPU-baseline leg may
 import it; the library itself never does, and it shares no code with the CUDA path.
 
 Parity pins (see tests/test_oracle_pins.py) tie every function here to something other than

@@ -33,6 +33,8 @@ __all__ = [
     "tangent_coords", "gauge_project", "project", "project_sum", "tangent_to_tt",
     "project_sum_vjp", "riemannian_grad_completion", "tangent_basis_jacobian",
     "explicit_projector", "manifold_dim", "tt_add", "tt_scale",
+    "project_batch", "tangent_gram", "project_matvec", "tangent_gather",
+    "riemannian_scatter", "completion_hvp", "svd_sign", "round_ranks", "round_tt",
 ]
 
 
@@ -468,6 +470,116 @@ def riemannian_grad_completion(U, V, idx, y):
     Zhat = [_scatter_outer(res, ls[k], rs[k + 2], idx[k],
                            (U[k].shape[0], U[k].shape[1], V[k].shape[2])) for k in range(len(U))]
     return float(0.5 * np.sum(res * res)), gauge_project(U, Zhat)
+
+
+# ---------------------------------------------------------------------------------------
+# Tailored tangent-space operations (Section 3.2: Gram matrix of tangent vectors of one
+# tangent space, projection of a matrix-by-vector product, the linearised Riemannian
+# Hessian) and rounding (Section 3, t3f.round)
+# ---------------------------------------------------------------------------------------
+
+def project_batch(U, V, Zs, c=None):
+    """Coordinates of c_j P_X Z_j for every object of a batch (c_j = 1 when c is None): the
+    'project' operation of Table 1 applied to each object separately, without summing."""
+    out = []
+    for j, Z in enumerate(Zs):
+        cj = 1.0 if c is None else float(c[j])
+        out.append([cj * x for x in project(U, V, Z)])
+    return out
+
+
+def tangent_gram(dAs, dBs) -> np.ndarray:
+    """G[a, b] = <xi_a, eta_b> for tangent vectors of one tangent space given by gauge
+    coordinates: the terms U_1..U_{k-1} dU_k V_{k+1}..V_d of different k are mutually
+    orthogonal (gauge + orthogonality of U and V), so the inner product is the sum over k of
+    the coordinate inner products <dA_k, dB_k>."""
+    G = np.zeros((len(dAs), len(dBs)))
+    for a, dA in enumerate(dAs):
+        for b, dB in enumerate(dBs):
+            G[a, b] = sum(float(np.sum(np.asarray(x, float) * np.asarray(y, float))) for x, y in zip(dA, dB))
+    return G
+
+
+def project_matvec(U, V, Acores, cs):
+    """Coordinates of P_X (A c_j) for a TT-matrix A and every TT-vector c_j of a batch: the
+    projection of the (unrounded, rank r_A r_c) product matvec(A, c_j)."""
+    return [project(U, V, matvec(Acores, c)) for c in cs]
+
+
+def tangent_gather(U, V, dZ, idx) -> np.ndarray:
+    """Entries xi(i_t) of the tangent vector xi = sum_k U_1..U_{k-1} dZ_k V_{k+1}..V_d, one
+    chain per term k and tuple, summed over k (the definition, term by term)."""
+    U, V, dZ = _as_list(U), _as_list(V), _as_list(dZ)
+    idx = np.asarray(idx)
+    d = len(U)
+    N = idx.shape[1]
+    out = np.zeros(N)
+    for k in range(d):
+        chain = [U[j] for j in range(k)] + [dZ[k]] + [V[j] for j in range(k + 1, d)]
+        out += _prefixes(chain, idx)[-1][:, 0]
+    return out
+
+
+def riemannian_scatter(U, V, idx, w):
+    """Coordinates of P_X (sum_t w_t e_{i_t}): the Euclidean scatter with U-prefixes and
+    V-suffixes, then the gauge projection."""
+    U, V = _as_list(U), _as_list(V)
+    idx = np.asarray(idx)
+    w = np.asarray(w, dtype=np.float64)
+    ls = _prefixes(U, idx)
+    rs = _suffixes(V, idx)
+    Zhat = [_scatter_outer(w, ls[k], rs[k + 2], idx[k],
+                           (U[k].shape[0], U[k].shape[1], V[k].shape[2])) for k in range(len(U))]
+    return gauge_project(U, Zhat)
+
+
+def completion_hvp(U, V, idx, dZ):
+    """Linearised Riemannian Hessian of the completion loss f(X) = 1/2 sum_t (X(i_t) - y_t)^2
+    applied to a tangent vector: P_X (grad^2 f) P_X xi, with xi given by its coordinates dZ.
+    grad^2 f = sum_t e_{i_t} e_{i_t}^T (tuples counted with multiplicity, independent of X and
+    y), so the result is P_X (sum_t xi(i_t) e_{i_t})."""
+    return riemannian_scatter(U, V, idx, tangent_gather(U, V, dZ, idx))
+
+
+def svd_sign(Uk, SVt):
+    """Sign convention of the rounding's SVD factors: every left singular vector has its
+    entry of largest magnitude positive (the matching row of S V^T flips with it)."""
+    piv = np.argmax(np.abs(Uk), axis=0)
+    s = np.where(Uk[piv, np.arange(Uk.shape[1])] < 0.0, -1.0, 1.0)
+    return Uk * s[None, :], SVt * s[:, None]
+
+
+def round_ranks(n, ranks, max_rank) -> list[int]:
+    """Ranks of round_tt: the right-to-left reduction r'_{k-1} = min(r_{k-1}, n_k r'_k),
+    then left to right min(r''_{k-1} n_k, r'_k, max_rank)."""
+    d = len(n)
+    r1 = list(ranks)
+    for k in range(d - 1, 0, -1):
+        r1[k] = min(r1[k], n[k] * r1[k + 1])
+    r2 = list(r1)
+    for k in range(1, d):
+        r2[k] = min(r2[k - 1] * n[k - 1], r1[k], int(max_rank))
+    return [int(v) for v in r2]
+
+
+def round_tt(cores, max_rank):
+    """TT rounding to TT-ranks <= max_rank (Section 3, t3f.round; the TT-SVD recompression of
+    Oseledets 2011): a right-to-left orthogonalisation sweep, then left to right the SVD of
+    each (r_{k-1} n_k) x r_k unfolding, truncated to the leading max_rank singular triplets,
+    with S V^T pushed into the next core. Returns (cores, discarded), discarded[k] the sum of
+    the squared singular values dropped at interface k+1; ||X - round(X)||^2 is their sum."""
+    W = right_orth_sweep(cores)
+    d = len(W)
+    discarded = []
+    for k in range(d - 1):
+        r0, n, r1 = W[k].shape
+        Uk, sv, Vt = np.linalg.svd(W[k].reshape(r0 * n, r1), full_matrices=False)
+        keep = min(int(max_rank), len(sv))
+        Uk, SVt = svd_sign(Uk[:, :keep], sv[:keep, None] * Vt[:keep])
+        discarded.append(float(np.sum(sv[keep:] ** 2)))
+        W[k] = Uk.reshape(r0, n, keep)
+        W[k + 1] = np.tensordot(SVt, W[k + 1], axes=([1], [0]))
+    return W, discarded
 
 
 # ---------------------------------------------------------------------------------------

@@ -375,3 +375,140 @@ def test_riemannian_grad_completion():
           - O.completion_loss(O.tt_add(X, O.tt_scale(xi, -h)), cfg.idx, y)) / (2 * h)
     inner = float(np.sum(O.full(O.tangent_to_tt(U, V, dU)) * O.full(xi)))
     assert np.isclose(fd, inner, rtol=1e-7)
+
+
+# ---------------------------------------------------------------------------------------
+# Tangent-space Gram matrices, projected matvec, linearised Hessian, rounding
+# ---------------------------------------------------------------------------------------
+
+def test_tangent_gram_is_the_full_tensor_inner_product():
+    # brute force: the tangent vectors as full tensors (their rank-2r TTs), inner products of
+    # the dense arrays, and the TT inner product of the same rank-2r TTs
+    cfg = S.config1()
+    X = single(cfg.X)
+    U, V, _ = O.orthogonalize(X)
+    dAs = O.project_batch(U, V, [single(cfg.A, b) for b in range(5)], cfg.c[:5])
+    dBs = O.project_batch(U, V, [single(cfg.B, b) for b in range(4)])
+    G = O.tangent_gram(dAs, dBs)
+    FA = [O.full(O.tangent_to_tt(U, V, d)).ravel() for d in dAs]
+    FB = [O.full(O.tangent_to_tt(U, V, d)).ravel() for d in dBs]
+    np.testing.assert_allclose(G, np.array([[a @ b for b in FB] for a in FA]), rtol=1e-10, atol=1e-10)
+    assert np.isclose(G[1, 2], O.dot(O.tangent_to_tt(U, V, dAs[1]), O.tangent_to_tt(U, V, dBs[2])), rtol=1e-10)
+    # without the gauge the coordinate sum is not the inner product (the pin can fail)
+    raw = O.tangent_coords(U, V, single(cfg.A, 0))
+    FR = O.full(O.tangent_to_tt(U, V, raw)).ravel()
+    assert not np.isclose(O.tangent_gram([raw], [raw])[0, 0], FR @ FR, rtol=1e-3)
+
+
+def test_project_batch_scales_and_sums_to_project_sum():
+    cfg = S.config1()
+    X = single(cfg.X)
+    U, V, _ = O.orthogonalize(X)
+    Zs = [single(cfg.B, b) for b in range(8)]
+    P = O.project_batch(U, V, Zs, cfg.c)
+    tot = [sum(p[k] for p in P) for k in range(4)]
+    for a, b in zip(tot, O.project_sum(U, V, Zs, cfg.c)):
+        np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-12)
+    # each coordinate set is the explicit projector applied to c_j Z_j
+    Pm = O.explicit_projector(X)
+    np.testing.assert_allclose(O.full(O.tangent_to_tt(U, V, P[3])).ravel(),
+                               cfg.c[3] * (Pm @ O.full(Zs[3]).ravel()), rtol=1e-9, atol=1e-10)
+
+
+def test_project_matvec_is_projected_dense_product():
+    rng = np.random.default_rng(41)
+    m, n = [2, 3, 2], [3, 2, 2]
+    A = single(S.random_ttm(rng, 1, m, n, [1, 2, 3, 1]))
+    cs = [rand_tt(rng, n, [1, 2, 2, 1]) for _ in range(3)]
+    X = rand_tt(rng, m, [1, 2, 2, 1])
+    U, V, _ = O.orthogonalize(X)
+    Pm = O.explicit_projector(X)
+    M = O.full_matrix(A)
+    for c, dU in zip(cs, O.project_matvec(U, V, A, cs)):
+        np.testing.assert_allclose(O.full(O.tangent_to_tt(U, V, dU)).ravel(), Pm @ (M @ O.full(c).ravel()),
+                                   rtol=1e-9, atol=1e-10)
+
+
+def test_tangent_gather_is_the_full_tensor_entry():
+    cfg = S.config1()
+    X = single(cfg.X)
+    U, V, _ = O.orthogonalize(X)
+    dZ = O.project(U, V, single(cfg.B, 2))
+    F = O.full(O.tangent_to_tt(U, V, dZ))
+    np.testing.assert_allclose(O.tangent_gather(U, V, dZ, cfg.idx), F[tuple(cfg.idx)], rtol=1e-10, atol=1e-12)
+    # d = 1: the tangent vector is dZ itself
+    x1 = rand_tt(np.random.default_rng(5), [6], [1, 1])
+    U1, V1, _ = O.orthogonalize(x1)
+    z = [np.arange(6.0).reshape(1, 6, 1)]
+    np.testing.assert_allclose(O.tangent_gather(U1, V1, z, np.array([[0, 3, 5]])), [0.0, 3.0, 5.0])
+
+
+def test_completion_hvp_is_projected_sampling_operator():
+    # dense: P diag(counts) P applied to the dense tangent vector; symmetric; and the second
+    # derivative of the (quadratic) loss along xi equals sum_t xi(i_t)^2
+    cfg = S.config1()
+    X = single(cfg.X)
+    U, V, _ = O.orthogonalize(X)
+    xi = O.project(U, V, single(cfg.B, 4))
+    eta = O.project(U, V, single(cfg.B, 5))
+    H = O.completion_hvp(U, V, cfg.idx, xi)
+    Pm = O.explicit_projector(X)
+    counts = np.zeros(O.full(X).shape)
+    np.add.at(counts, tuple(cfg.idx), 1.0)
+    xf = O.full(O.tangent_to_tt(U, V, xi)).ravel()
+    np.testing.assert_allclose(O.full(O.tangent_to_tt(U, V, H)).ravel(), Pm @ (counts.ravel() * (Pm @ xf)),
+                               rtol=1e-9, atol=1e-9)
+    He = O.completion_hvp(U, V, cfg.idx, eta)
+    assert np.isclose(O.tangent_gram([eta], [H])[0, 0], O.tangent_gram([He], [xi])[0, 0], rtol=1e-10)
+    y = O.gather(single(cfg.A, 0), cfg.idx)
+    T = O.tangent_to_tt(U, V, xi)
+    h = 1e-4
+    f = lambda t: O.completion_loss(O.tt_add(X, O.tt_scale(T, t)), cfg.idx, y)
+    fd2 = (f(h) - 2 * f(0.0) + f(-h)) / h ** 2
+    assert np.isclose(fd2, O.tangent_gram([xi], [H])[0, 0], rtol=1e-5)
+    assert np.isclose(fd2, np.sum(O.tangent_gather(U, V, xi, cfg.idx) ** 2), rtol=1e-5)
+
+
+def test_riemannian_scatter_matches_gradient():
+    cfg = S.config1()
+    X = single(cfg.X)
+    U, V, _ = O.orthogonalize(X)
+    y = O.gather(single(cfg.A, 0), cfg.idx) + cfg.noise
+    _, dU = O.riemannian_grad_completion(U, V, cfg.idx, y)
+    res = O.gather(U, cfg.idx) - y
+    for a, b in zip(O.riemannian_scatter(U, V, cfg.idx, res), dU):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_round_d2_is_truncated_matrix_svd():
+    # Eckart-Young: for d = 2 the rounding is the best rank-r approximation of the matrix
+    rng = np.random.default_rng(42)
+    X = rand_tt(rng, [7, 6], [1, 6, 1])
+    Y, disc = O.round_tt(X, 3)
+    Mx = O.full(X)
+    u, s, vt = np.linalg.svd(Mx)
+    np.testing.assert_allclose(O.full(Y), (u[:, :3] * s[:3]) @ vt[:3], rtol=1e-10, atol=1e-10)
+    assert np.isclose(disc[0], np.sum(s[3:] ** 2), rtol=1e-10)
+
+
+def test_round_exact_recompression_and_error_identity():
+    rng = np.random.default_rng(43)
+    n = [3, 4, 2, 3]
+    X = rand_tt(rng, n, [1, 2, 3, 2, 1])
+    XX = O.tt_add(X, X)                       # rank 2r, true rank r
+    Y, disc = O.round_tt(XX, 3)
+    np.testing.assert_allclose(O.full(Y), 2 * O.full(X), rtol=1e-10, atol=1e-10)
+    assert O.tt_ranks_of(Y) == O.round_ranks(n, O.tt_ranks_of(XX), 3)
+    assert max(disc) < 1e-20 * O.dot(XX, XX) + 1e-24
+    # truncation below the true rank: the squared error is the sum of the dropped sigma^2
+    Z = rand_tt(rng, n, [1, 3, 5, 3, 1])
+    Y2, disc2 = O.round_tt(Z, 2)
+    err2 = np.sum((O.full(Z) - O.full(Y2)) ** 2)
+    assert np.isclose(err2, sum(disc2), rtol=1e-9)
+    # result cores 1..d-1 are left-orthogonal and signs follow the convention
+    for k in range(3):
+        Ul = Y2[k].reshape(-1, Y2[k].shape[2])
+        np.testing.assert_allclose(Ul.T @ Ul, np.eye(Ul.shape[1]), atol=1e-12)
+        piv = np.argmax(np.abs(Ul), axis=0)
+        assert (Ul[piv, np.arange(Ul.shape[1])] > 0).all()
+    assert O.tt_ranks_of(Y2) == O.round_ranks(n, O.tt_ranks_of(Z), 2) == [1, 2, 2, 2, 1]
