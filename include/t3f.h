@@ -79,7 +79,8 @@ typedef enum {
   T3F_OP_GRAM = 1, T3F_OP_GRAM_BWD = 2, T3F_OP_NORM = 3,
   T3F_OP_GATHER = 4, T3F_OP_GATHER_BWD = 5, T3F_OP_RGATHER_BWD = 6,
   T3F_OP_MATVEC = 7, T3F_OP_MATVEC_BWD = 8,
-  T3F_OP_ORTH = 9, T3F_OP_PSUM = 10, T3F_OP_PSUM_BWD = 11
+  T3F_OP_ORTH = 9, T3F_OP_PSUM = 10, T3F_OP_PSUM_BWD = 11,
+  T3F_OP_PROJECT = 12, T3F_OP_TANGENT_GRAM = 13, T3F_OP_COMPLETION_HVP = 14
 } t3f_op;
 
 /* Name of a status code (static string). */
@@ -101,7 +102,8 @@ int64_t t3f_packed_size(const t3f_tt* t);
  *   GATHER, GATHER_BWD: a = X, n_items = N tuples.
  *   RGATHER_BWD: a = U (left-orthogonal form), b = V, n_items = N.
  *   MATVEC, MATVEC_BWD: a = A (TT-matrix), b = x.
- *   ORTH: a = X.    PSUM, PSUM_BWD: a = U, b = Z (the batch being projected).
+ *   ORTH: a = X.    PSUM, PSUM_BWD, PROJECT: a = U, b = Z (the batch being projected).
+ *   TANGENT_GRAM: a = dA, b = dB.   COMPLETION_HVP: a = U, b = V, n_items = N.
  * Returns 0 for an invalid request (check with the call itself for the status).
  */
 size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* b, int64_t n_items);
@@ -264,6 +266,57 @@ t3f_status t3f_project_sum_backward(const t3f_tt* U, const t3f_tt* V, const t3f_
                                     const float* c, const t3f_tt* dUbar, t3f_tt* dZ,
                                     float* dc, void* ws, size_t ws_bytes,
                                     t3f_stream_t stream);
+
+/*
+ * Batched projection ('project' of the paper's Table 1, Section 3.2, for every object of a
+ * batch): dU_j = tangent coordinates of c_j P_X Z_j, without summing over j (c NULL: c_j = 1).
+ *   Zhat_j,k[:,i,:] = c_j L^{(j)}_{k-1} Z_j^k[:,i,:] (R^{(j)}_{k+1})^T,
+ *   dU_j,k = (I - U_k U_k^T) Zhat_j,k for k < d, dU_j,d = Zhat_j,d.
+ * U, V: F32 orthogonal forms (batch 1, ranks <= T3F_MAX_RANK); Z: F32 batch with U's modes;
+ * dU: F32 descriptor of batch Z->batch with U's ranks. Summing dU_j over j gives
+ * t3f_project_sum's result.
+ */
+t3f_status t3f_project(const t3f_tt* U, const t3f_tt* V, const t3f_tt* Z, const float* c,
+                       t3f_tt* dU, void* ws, size_t ws_bytes, t3f_stream_t stream);
+
+/*
+ * Gram matrix of tangent vectors of one tangent space (paper Section 3.2, tailored
+ * operations): G[a * dB->batch + b] = <xi_a, eta_b> = sum_k <dA_a,k, dB_b,k>, with xi_a, eta_b
+ * given by gauge coordinates (outputs of t3f_project / t3f_project_sum at the same X, so the
+ * terms of different k are orthogonal). dA, dB: F32 batches of one shape (U's); G: device float
+ * [dA->batch][dB->batch]. math: T3F_MATH_FP32 (FP32 CUDA cores, split-K, deterministic
+ * reduction) or T3F_MATH_TF32 (tcgen05 TF32 tensor cores fed by TMA, FP32 accumulation; every
+ * core block 16-byte aligned with 16-byte-multiple rows, else T3F_ERR_UNSUPPORTED).
+ */
+t3f_status t3f_tangent_gram(const t3f_tt* dA, const t3f_tt* dB, float* G, int32_t math, void* ws,
+                            size_t ws_bytes, t3f_stream_t stream);
+
+/*
+ * Projected matrix-by-vector product (paper Section 3.2, P_b(A c)): dU_j = tangent
+ * coordinates of P_X (A x_j) for the TT-matrix A (batch 1, or zip with x) and every TT-vector
+ * x_j, computed from the Kronecker cores of the product on the fly (the rank r_A r_x TT of
+ * A x_j is never formed): left partials of U and right partials of V against A x_j, then
+ * Zhat_k = L_{k-1} (A x)_k R_{k+1}^T and the gauge projection. A's row modes equal U's modes,
+ * its column modes x's. dU: F32, batch x->batch, U's ranks. Workspace:
+ * t3f_project_matvec_workspace_size(U, A, x) bytes.
+ */
+size_t t3f_project_matvec_workspace_size(const t3f_tt* U, const t3f_tt* A, const t3f_tt* x);
+t3f_status t3f_project_matvec(const t3f_tt* U, const t3f_tt* V, const t3f_tt* A, const t3f_tt* x,
+                              t3f_tt* dU, void* ws, size_t ws_bytes, t3f_stream_t stream);
+
+/*
+ * Linearised Riemannian Hessian of the completion loss applied to a tangent vector (paper
+ * Section 3.2, P_X (grad^2 f) P_X Z): for f(X) = 1/2 sum_t (X(i_t) - y_t)^2 the Euclidean
+ * Hessian is sum_t e_{i_t} e_{i_t}^T, so out = coordinates of P_X (sum_t xi(i_t) e_{i_t}) for
+ * the tangent vector xi with gauge coordinates dZ. xi(i_t) comes from the block recurrence
+ * q_k = q_{k-1} V_k + p_{k-1} dZ_k, p_k = p_{k-1} U_k; the scatter is t3f_gather_backward's
+ * Riemannian form with those weights. U, V: orthogonal forms (ranks <= 16); idx: device int32
+ * [d][N]; dZ, out: F32, U's shape. An out-of-range index is clamped and recorded in the
+ * workspace error word.
+ */
+t3f_status t3f_completion_hvp(const t3f_tt* U, const t3f_tt* V, const int32_t* idx, int64_t N,
+                              const t3f_tt* dZ, t3f_tt* out, void* ws, size_t ws_bytes,
+                              t3f_stream_t stream);
 
 /*
  * A ragged collection of TT-vectors: object o has d[o] cores, modes

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libt3f.so")
 F32, F64, BF16 = 0, 1, 2
 MATH = {"fp32": 0, "tf32": 1, "bf16": 2}
 OP = dict(gram=1, gram_bwd=2, norm=3, gather=4, gather_bwd=5, rgather_bwd=6, matvec=7,
-          matvec_bwd=8, orth=9, psum=10, psum_bwd=11)
+          matvec_bwd=8, orth=9, psum=10, psum_bwd=11, project=12, tangent_gram=13, completion_hvp=14)
 _TORCH_DTYPE = {F32: torch.float32, F64: torch.float64, BF16: torch.bfloat16}
 _CODE = {v: k for k, v in _TORCH_DTYPE.items()}
 
@@ -66,6 +66,11 @@ _SIGS = {
     "t3f_project_sum": (ctypes.c_int32, [_P, _P, _P, _VP, _P, ctypes.c_int32, _VP, _SZ, _VP]),
     "t3f_project_sum_backward": (ctypes.c_int32, [_P, _P, _P, _VP, _P, _P, _VP, _VP, _SZ, _VP]),
     "t3f_device_status": (ctypes.c_int32, [_VP, _VP]),
+    "t3f_project": (ctypes.c_int32, [_P, _P, _P, _VP, _P, _VP, _SZ, _VP]),
+    "t3f_tangent_gram": (ctypes.c_int32, [_P, _P, _VP, ctypes.c_int32, _VP, _SZ, _VP]),
+    "t3f_project_matvec_workspace_size": (ctypes.c_size_t, [_P, _P, _P]),
+    "t3f_project_matvec": (ctypes.c_int32, [_P, _P, _P, _P, _P, _VP, _SZ, _VP]),
+    "t3f_completion_hvp": (ctypes.c_int32, [_P, _P, _VP, ctypes.c_int64, _P, _P, _VP, _SZ, _VP]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -309,6 +314,49 @@ def project_sum_backward(U: TT, V: TT, Z: TT, c: torch.Tensor, dUbar: TT, need_Z
                                            _ptr(dc), _ptr(ws), ws.numel(), _stream(dev)),
            "t3f_project_sum_backward")
     return dZ, dc
+
+
+def project(U: TT, V: TT, Z: TT, c: Optional[torch.Tensor] = None) -> TT:
+    """Tangent coordinates of c_j P_X Z_j for every object of Z (batch Z.batch, U's shape)."""
+    dev = U.data.device
+    dU = TT.empty(U.n, U.ranks, Z.batch, None, torch.float32, dev)
+    ws = _ws("project", U, Z, 0, dev)
+    c = None if c is None else c.contiguous().to(torch.float32)
+    _check(_lib().t3f_project(_ref(U), _ref(V), _ref(Z), _ptr(c), _ref(dU), _ptr(ws), ws.numel(), _stream(dev)),
+           "t3f_project")
+    return dU
+
+
+def tangent_gram(dA: TT, dB: TT, math: str = "fp32") -> torch.Tensor:
+    """G[a, b] = <xi_a, eta_b> for tangent vectors of one tangent space (gauge coordinates)."""
+    dev = dA.data.device
+    G = torch.empty(dA.batch, dB.batch, dtype=torch.float32, device=dev)
+    ws = _ws("tangent_gram", dA, dB, 0, dev)
+    _check(_lib().t3f_tangent_gram(_ref(dA), _ref(dB), _ptr(G), MATH[math], _ptr(ws), ws.numel(), _stream(dev)),
+           "t3f_tangent_gram")
+    return G
+
+
+def project_matvec(U: TT, V: TT, A: TT, x: TT) -> TT:
+    """Tangent coordinates of P_X (A x_j) for every x_j (the product is never formed)."""
+    dev = U.data.device
+    dU = TT.empty(U.n, U.ranks, x.batch, None, torch.float32, dev)
+    nbytes = _lib().t3f_project_matvec_workspace_size(_ref(U), _ref(A), _ref(x))
+    ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+    _check(_lib().t3f_project_matvec(_ref(U), _ref(V), _ref(A), _ref(x), _ref(dU), _ptr(ws), ws.numel(),
+                                     _stream(dev)), "t3f_project_matvec")
+    return dU
+
+
+def completion_hvp(U: TT, V: TT, idx: torch.Tensor, dZ: TT, return_ws: bool = False):
+    """Coordinates of P_X (sum_t xi(i_t) e_{i_t}) for the tangent vector with coordinates dZ."""
+    dev = U.data.device
+    N = idx.shape[1]
+    out = U.empty_like(torch.float32)
+    ws = _ws("completion_hvp", U, V, N, dev)
+    _check(_lib().t3f_completion_hvp(_ref(U), _ref(V), _ptr(idx), N, _ref(dZ), _ref(out), _ptr(ws), ws.numel(),
+                                     _stream(dev)), "t3f_completion_hvp")
+    return (out, ws) if return_ws else out
 
 
 def device_status(ws: torch.Tensor) -> int:

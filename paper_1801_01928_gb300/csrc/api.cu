@@ -129,7 +129,8 @@ extern "C" size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* 
   if (!a || make_view(a, &va, -1, a->m != nullptr) != T3F_OK) return 0;
   const bool need_b = op == T3F_OP_GRAM || op == T3F_OP_GRAM_BWD || op == T3F_OP_RGATHER_BWD ||
                       op == T3F_OP_MATVEC || op == T3F_OP_MATVEC_BWD || op == T3F_OP_PSUM ||
-                      op == T3F_OP_PSUM_BWD;
+                      op == T3F_OP_PSUM_BWD || op == T3F_OP_PROJECT || op == T3F_OP_TANGENT_GRAM ||
+                      op == T3F_OP_COMPLETION_HVP;
   if (need_b && (!b || make_view(b, &vb, -1, b->m != nullptr) != T3F_OK)) return 0;
   switch (op) {
     case T3F_OP_GRAM: return kWsHeader;
@@ -143,6 +144,9 @@ extern "C" size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* 
     case T3F_OP_ORTH: return ws_orth(va);
     case T3F_OP_PSUM: return ws_psum(va, vb, false);
     case T3F_OP_PSUM_BWD: return ws_psum(va, vb, true);
+    case T3F_OP_PROJECT: return ws_project(va, vb);
+    case T3F_OP_TANGENT_GRAM: return ws_tangent_gram(va, vb);
+    case T3F_OP_COMPLETION_HVP: return ws_completion_hvp(va, vb, n_items);
     default: return 0;
   }
 }

@@ -104,6 +104,9 @@ size_t ws_gather(const TTV& X, long long N, bool bwd);
 size_t ws_rgather(const TTV& U, const TTV& V, long long N);
 size_t ws_orth(const TTV& X);
 size_t ws_psum(const TTV& U, const TTV& Z, bool bwd);
+size_t ws_project(const TTV& U, const TTV& Z);
+size_t ws_tangent_gram(const TTV& A, const TTV& B);
+size_t ws_completion_hvp(const TTV& U, const TTV& V, long long N);
 
 }  // namespace t3f
 
