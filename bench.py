@@ -134,6 +134,32 @@ def f_psum_bwd(n, ru, rz, batch):
     return batch * (f_left_sweep(n, ru, rz) + f_right_sweep(n, ru, rz) + P + Q + G) + f_gauge(n, ru)
 
 
+def f_project_batch(n, ru, rz, batch):
+    """per object: both sweeps, the per-slice assembly and the per-object gauge projection."""
+    asm = sum(2 * n[k] * ru[k] * rz[k + 1] * (rz[k] + ru[k + 1]) for k in range(len(n)))
+    return batch * (f_left_sweep(n, ru, rz) + f_right_sweep(n, ru, rz) + asm + f_gauge(n, ru))
+
+
+def f_project_matvec(m, n, rx, ra, rc, batch):
+    """per object: left and right Kronecker sweeps (c-step, A-step, X-step) and the assembly."""
+    d = len(n)
+    tot = 0.0
+    for k in range(d):
+        x0, x1, a0, a1, b0, b1 = rx[k], rx[k + 1], ra[k], ra[k + 1], rc[k], rc[k + 1]
+        left = 2 * x0 * a0 * n[k] * b1 * b0 + 2 * x0 * m[k] * a1 * b1 * a0 * n[k] + 2 * x1 * a1 * b1 * x0 * m[k]
+        right = 2 * x1 * a1 * n[k] * b0 * b1 + 2 * x1 * m[k] * a0 * b0 * a1 * n[k] + 2 * x0 * a0 * b0 * x1 * m[k]
+        asm = 2 * x0 * a0 * n[k] * b1 * b0 + 2 * x0 * m[k] * a1 * b1 * a0 * n[k] + 2 * x0 * m[k] * x1 * a1 * b1
+        tot += left + right + asm
+    return batch * (tot + f_gauge(m, rx))
+
+
+def f_hvp(r, n, N):
+    """tangent-vector gather (three chains of r x r products per core) + the Riemannian scatter."""
+    d = len(r) - 1
+    gather = sum(3 * 2 * r[k] * r[k + 1] for k in range(d))
+    return N * (gather + f_completion(r)) + f_gauge(n, r)
+
+
 # ---------------------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------------------
@@ -193,6 +219,16 @@ class Workload:
         ntot = sum((self.gstart[g + 1] - self.gstart[g]) ** 2 for g in range(len(self.gstart) - 1))
         host["dG4"] = rng.normal(size=ntot).astype(np.float32)
         self.host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+        # inputs of the tangent-space rows measured beside the step: the first 100 TTs of the
+        # projection batch, the first TT-matrix of the matvec batch and a rank-10 point (d=10, n=4)
+        Z100 = [np.asarray(cz[:100], np.float32) for cz in c5.Z]
+        A1 = [np.asarray(ca[:1], np.float32) for ca in c3b.A]
+        Xp = S.random_tt(np.random.default_rng(7 + seed_offset), 1, 4, S.tt_ranks(10, 10), 1 / math.sqrt(10))
+        self.next_dev = {
+            "Z100": torch.tensor(np.concatenate([c.ravel() for c in Z100]), device=dev),
+            "A1": torch.tensor(np.concatenate([c.ravel() for c in A1]), device=dev),
+            "Xp": torch.tensor(np.concatenate([np.asarray(c, np.float32).ravel() for c in Xp]), device=dev),
+        }
         self.h2d_bytes = sum(v.numel() * v.element_size() for v in self.host.values())
         self.devbuf = {k: torch.empty_like(v, device=dev) for k, v in self.host.items()}
         self.upload(torch.cuda.current_stream(dev))
@@ -255,33 +291,6 @@ class Workload:
             t3f.gram_groups_backward(X4, self.gstart, self.ws4, self.devbuf["dG4"], self.tiles4, dcores=self.dX4)
         self.graph_kernels = (n1 - n0) + (t3f.launch_count() - n1)
         torch.cuda.synchronize(self.dev)
-
-    def plain_uneven(self):
-        """The single-shape FP32 comparator for the uneven batch: every group zero-padded to
-        its largest rank (inner products unchanged) and run as one uniform Gram + adjoint
-        launch sequence per group, without the work queue or graph."""
-        t3f, torch = self.t3f, self.torch
-        dims, modes, ranks, _ = self.r4meta
-        rg = self.t3f.RaggedTT(self.host["X4"], dims, modes, ranks, self.r4meta[3])
-        groups, off = [], 0
-        for g in range(len(self.gstart) - 1):
-            objs = list(range(self.gstart[g], self.gstart[g + 1]))
-            d, n = dims[objs[0]], modes[objs[0]]
-            R = max(max(ranks[o][1:-1], default=1) for o in objs)
-            rk = [1] + [R] * (d - 1) + [1]
-            cores = []
-            for k in range(d):
-                blk = np.zeros((len(objs), rk[k], n[k], rk[k + 1]), np.float32)
-                for j, o in enumerate(objs):
-                    c = rg.object_cores(o)[k].numpy()
-                    blk[j, :c.shape[0], :, :c.shape[2]] = c
-                cores.append(blk)
-            A = t3f.TT.from_cores(cores, device=self.dev)
-            S_ = len(objs)
-            dG = self.devbuf["dG4"][off:off + S_ * S_].view(S_, S_)
-            off += S_ * S_
-            groups.append((A, dG))
-        return groups
 
     def tt(self, key):
         n, r, b, m = self.meta[key]
@@ -467,9 +476,11 @@ def reduced_precision(w, flops, flush, stream, reps=5):
                 "unit": "TFLOP/s", "frac": round(gflops / 1e3 / peaks[kind], 5), "peak_source": psrc,
                 "flops": "algorithmic (unpadded ranks)"}
 
+    keep = {}
     for math_ in ("tf32", "bf16"):
         ms = timed(lambda: t3f.gram(A3, B3, math=math_))
         G = t3f.gram(A3, B3, math=math_)
+        keep[f"gram_{math_}"] = (G, 5e-3 if math_ == "tf32" else 2e-2)
         gf = flops["gram"] / (ms * 1e-3) / 1e9
         out[f"gram_{math_}"] = {"ms": round(ms, 4), "gflops": round(gf, 1),
                                 "diff_vs_fp32": round(rel(G, G32), 6), "roofline": roof(gf, math_),
@@ -480,12 +491,160 @@ def reduced_precision(w, flops, flush, stream, reps=5):
             ("uneven_bf16_tc", X4b, ws4b, "bf16", "BF16 cores; tcgen05 BF16 tiles, FP32 accumulation")):
         ms = timed(lambda: t3f.gram_groups(X_, w.gstart, ws_, w.tiles4, math=math_))
         Gx, _ = t3f.gram_groups(X_, w.gstart, ws_, w.tiles4, math=math_)
+        keep[key] = (Gx, {"fp32": 2e-2, "tf32": 5e-3, "bf16": 2e-2}[math_])
         gf = flops["uneven"] / (ms * 1e-3) / 1e9
         out[key] = {"ms": round(ms, 4), "gflops": round(gf, 1), "diff_vs_fp32": round(rel(Gx, G4_32), 6),
                     "path": path}
         if math_ != "fp32":
             out[key]["roofline"] = roof(gf, math_)
+    return out, keep
+
+
+def event_time(torch, fn, flush, stream, reps=5):
+    """Mean CUDA-event time (ms) of fn on `stream`, L2 flushed (untimed) before each rep."""
+    fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps
+
+
+def measured_fp32_peak(t3f, torch, dev, gpu_index):
+    """FP32 FMA rate of this GPU from the library's FMA probe (8 independent chains per
+    thread, 4 CTAs of 256 threads per SM), with the SM clock sampled while it runs."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    grid, iters = sms * 4, 20000
+    t3f.fma_probe(grid, iters, dev)
+    torch.cuda.synchronize(dev)
+    reps = 8
+    with ClockSampler(gpu_index) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            flops, _ = t3f.fma_probe(grid, iters, dev)
+        e1.record()
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    c = clk.summary()
+    return {"tflops": round(flops / (ms * 1e-3) / 1e12, 2), "ms_per_launch": round(ms, 3),
+            "sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"], "reasons": c["reasons"],
+            "derived_at_max_clock": round(FP32_PEAK_TFLOPS, 2),
+            "how": f"t3f_fma_probe: {grid} CTAs x 256 threads x 8 FMA chains, CUDA events"}
+
+
+def next_rows(w, flush, stream, fp32_peak):
+    """The tangent-space rows beyond the step (Section 3.2), each timed on its own:
+    batched projection of 100 config-5 TTs + the Gram matrix of their tangent vectors (FP32
+    CUDA cores and TF32 tensor cores via TMA), the projected matvec P_X(A x_j) at config-3b
+    shapes, and the completion loss's linearised Riemannian Hessian applied to its Riemannian
+    gradient (config 2)."""
+    t3f, torch = w.t3f, w.torch
+    out = {}
+    hbm = hbm_peak()
+    X5 = w.tt("X5")
+    U5, V5 = t3f.orthogonalize(X5)
+    Z = t3f.TT(w.next_dev["Z100"], [16] * 20, S.tt_ranks(20, 8), 100)
+    c100 = w.devbuf["c5"][:100]
+    ru5 = t3f.orth_ranks([16] * 20, S.tt_ranks(20, 32))
+    rz5 = S.tt_ranks(20, 8)
+
+    def row(name, ms, flops, extra=None):
+        gf = flops / (ms * 1e-3) / 1e9
+        out[name] = {"ms": round(ms, 4), "gflop": round(flops / 1e9, 4), "gflops": round(gf, 1),
+                     "roofline": {"bound": "alu", "achieved": round(gf / 1e3, 3), "peak": fp32_peak, "unit": "TFLOP/s",
+                                  "frac": round(gf / 1e3 / fp32_peak, 4), "peak_source": "measured FMA probe"}}
+        if extra:
+            out[name].update(extra)
+
+    ms = event_time(torch, lambda: t3f.project(U5, V5, Z, c100), flush, stream)
+    row("project_batch", ms, f_project_batch([16] * 20, ru5, rz5, 100))
+    dU = t3f.project(U5, V5, Z, c100)
+    K = dU.data.numel() // 100
+    gflop = 2 * 100 * 100 * K
+    ms = event_time(torch, lambda: t3f.tangent_gram(dU, dU), flush, stream)
+    row("tangent_gram_fp32", ms, gflop)
+    ms = event_time(torch, lambda: t3f.tangent_gram(dU, dU, math="tf32"), flush, stream)
+    G32 = t3f.tangent_gram(dU, dU).double()
+    Gtf = t3f.tangent_gram(dU, dU, math="tf32").double()
+    nbytes = dU.data.numel() * 4
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    out["tangent_gram_tf32"] = {
+        "ms": round(ms, 4), "gflops": round(gflop / (ms * 1e-3) / 1e9, 1),
+        "diff_vs_fp32": round(float((Gtf - G32).norm() / G32.norm()), 6),
+        "path": "TMA (2D, 128-byte swizzle) + tcgen05 kind::tf32, FP32 accumulation in TMEM, split-K",
+        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                     "traffic": None, "bytes": "coordinates read once (self Gram: one operand per diagonal tile)"}}
+    # projected matvec at config-3b shapes: A = the first TT-matrix, 100 TT-vectors, X rank 10
+    A1 = t3f.TT(w.next_dev["A1"], [4] * 10, S.tt_ranks(10, 10), 1, [4] * 10)
+    xv = w.tt("xv")
+    Xp = t3f.TT(w.next_dev["Xp"], [4] * 10, S.tt_ranks(10, 10), 1)
+    Up, Vp = t3f.orthogonalize(Xp)
+    rxp = t3f.orth_ranks([4] * 10, S.tt_ranks(10, 10))
+    ms = event_time(torch, lambda: t3f.project_matvec(Up, Vp, A1, xv), flush, stream)
+    row("project_matvec", ms, f_project_matvec([4] * 10, [4] * 10, rxp, S.tt_ranks(10, 10), S.tt_ranks(10, 10), 100))
+    # linearised Riemannian Hessian of the completion loss along its Riemannian gradient
+    X2 = w.tt("X2")
+    U2, V2 = t3f.orthogonalize(X2)
+    idx, y = w.devbuf["idx"], w.devbuf["y"]
+    g2, _ = t3f.gather_backward(None, idx, y=y, riemannian=True, U=U2, V=V2)
+    ms = event_time(torch, lambda: t3f.completion_hvp(U2, V2, idx, g2), flush, stream)
+    ru2 = t3f.orth_ranks([10] * 10, S.tt_ranks(10, 8))
+    row("completion_hvp", ms, f_hvp(ru2, [10] * 10, idx.shape[1]))
     return out
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+def bucket_comparator(w):
+    """The single-shape FP32 comparator of the uneven batch without cubic padding: within each
+    group the objects are split by rank bucket (<= 8, 16, 32, 64), each bucket padded to its
+    own largest rank, and every bucket pair runs as one uniform Gram + adjoint launch pair
+    (per-group sequential launches, no work queue, no graph)."""
+    t3f, torch = w.t3f, w.torch
+    dims, modes, ranks, offs = w.r4meta
+    rg = t3f.RaggedTT(w.host["X4"], dims, modes, ranks, offs)
+    launches = []
+    for g in range(len(w.gstart) - 1):
+        objs = list(range(w.gstart[g], w.gstart[g + 1]))
+        d, n = dims[objs[0]], modes[objs[0]]
+        buckets = {}
+        for o in objs:
+            r = max(ranks[o][1:-1], default=1)
+            b = 0 if r <= 8 else 1 if r <= 16 else 2 if r <= 32 else 3
+            buckets.setdefault(b, []).append(o)
+        tts = {}
+        for b, os_ in buckets.items():
+            R = max(max(ranks[o][1:-1], default=1) for o in os_)
+            rk = [1] + [R] * (d - 1) + [1]
+            cores = []
+            for k in range(d):
+                blk = np.zeros((len(os_), rk[k], n[k], rk[k + 1]), np.float32)
+                for j, o in enumerate(os_):
+                    cc = rg.object_cores(o)[k].numpy()
+                    blk[j, :cc.shape[0], :, :cc.shape[2]] = cc
+                cores.append(blk)
+            tts[b] = t3f.TT.from_cores(cores, device=w.dev)
+        keys = sorted(tts)
+        for i, p in enumerate(keys):
+            for q in keys[i:]:
+                dG = torch.randn(tts[p].batch, tts[q].batch, device=w.dev)
+                launches.append((tts[p], tts[q], dG))
+    return launches
 
 
 # ---------------------------------------------------------------------------------------
@@ -597,6 +756,145 @@ def oracle_sample(frac: float, seed: int = 0):
     desc = (f"FP64 NumPy oracle, 1 thread: completion+rgrad on {N} tuples, gram+bwd {nA}x100 pairs, "
             f"matvec+bwd {nm} pairs, orth+project_sum+bwd of {nz} TTs (fraction {frac:g} of the step)")
     return flops, secs, desc, tcomp
+
+
+def oracle_errors(w, out, extra=None):
+    """Error of every output of one step against the FP64 oracle on the same (FP32-rounded)
+    inputs, on sampled objects / rows / pairs the oracle computes one by one (the loss, the
+    completion gradient, the Riemannian gradient and project_sum in full). Each entry gives
+    the max and median over its samples of the normwise relative error (Gram matrices of one
+    collection: diagonal and off-diagonal entries separately) and the stated tolerance."""
+    import oracle as O
+    t3f = w.t3f
+    t0 = time.perf_counter()
+    res = {}
+
+    def rel(a, b):
+        a = np.concatenate([np.asarray(x, np.float64).ravel() for x in a]) if isinstance(a, list) else np.ravel(a)
+        b = np.concatenate([np.asarray(x, np.float64).ravel() for x in b]) if isinstance(b, list) else np.ravel(b)
+        nb = np.linalg.norm(b)
+        return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))
+
+    def rec(name, errs, tol):
+        res[name] = {"max": float(max(errs)), "median": float(np.median(errs)), "samples": len(errs), "tol": tol}
+
+    def objs(key, data=None, ranks=None):
+        n, r, b, m = w.meta[key]
+        r = ranks or r
+        src = w.host[key] if data is None else data.detach().cpu()
+        tt = t3f.TT(src.double(), n, r, b, m)
+        cores = [c.numpy() for c in tt.cores()]
+        return [[c[i] for c in cores] for i in range(b)]
+
+    # completion loss and gradient, Riemannian gradient (all 10^6 tuples)
+    X2 = objs("X2")[0]
+    idx = w.host["idx"].numpy()
+    y = w.host["y"].double().numpy()
+    L, g = O.completion_loss_grad(X2, idx, y)
+    rec("completion.loss", [abs(float(out["loss"].item()) - L) / abs(L)], 1e-5)
+    rec("completion.dX", [rel(objs("X2", out["dX"])[0], g)], 1e-5)
+    U2, V2, ru2 = O.orthogonalize(X2)
+    _, dU2 = O.riemannian_grad_completion(U2, V2, idx, y)
+    rec("rgrad.dU", [rel(objs("X2", out["dU2"], ranks=ru2)[0], dU2)], 1e-5)
+    # Gram, adjoint, norms (sampled rows and objects)
+    A, B = objs("A3"), objs("B3")
+    dG = w.host["dG"].double().numpy()
+    G = out["G"].double().cpu().numpy()
+    rec("gram.G", [rel(G[a], [O.dot(A[a], Bb) for Bb in B]) for a in (0, 57, 99)], 1e-5)
+    dA, dB = objs("A3", out["dA"]), objs("B3", out["dB"])
+    rec("gram_bwd.dA", [rel(dA[a], O.gram_vjp([A[a]], B, dG[a:a + 1])[0][0]) for a in (0, 99)], 1e-5)
+    rec("gram_bwd.dB", [rel(dB[b], O.gram_vjp(A, [B[b]], dG[:, b:b + 1])[1][0]) for b in (3,)], 1e-5)
+    nrm = out["norm"].double().cpu().numpy()
+    rec("norm", [abs(nrm[a] - O.norm(A[a])) / O.norm(A[a]) for a in range(0, 100, 11)], 1e-5)
+    # matvec and its adjoint (sampled pairs)
+    Am, xv = objs("Am"), objs("xv")
+    C = w.t3f.TT(out["_bulk"][0].data.detach().cpu().double(), [4] * 10,
+                 [a * b for a, b in zip(S.tt_ranks(10, 10), S.tt_ranks(10, 10))], 100)
+    Cc = [c.numpy() for c in C.cores()]
+    rec("matvec.C", [rel([c[p] for c in Cc], O.matvec(Am[p], xv[p])) for p in (0, 99)], 1e-5)
+    dC = objs("dC")
+    dAm, dxv = objs("Am", out["dAm"]), objs("xv", out["dxv"])
+    ea, ex = [], []
+    for p in (0, 99):
+        ra, rx = O.matvec_vjp(Am[p], xv[p], dC[p])
+        ea.append(rel(dAm[p], ra))
+        ex.append(rel(dxv[p], rx))
+    rec("matvec_bwd.dA", ea, 1e-5)
+    rec("matvec_bwd.dx", ex, 1e-5)
+    # project_sum (all 1000 TTs) and its adjoint (sampled TTs, the step's own cotangent)
+    X5 = objs("X5")[0]
+    Z5 = objs("Z5")
+    c5 = w.host["c5"].double().numpy()
+    U5, V5, ru5 = O.orthogonalize(X5)
+    dU5 = objs("X5", out["dU5"], ranks=ru5)[0]
+    rec("psum.dU", [rel(dU5, O.project_sum(U5, V5, Z5, c5))], 1e-5)
+    dZ = w.t3f.TT(out["_bulk"][1].data.detach().cpu().double(), [16] * 20, S.tt_ranks(20, 8), 1000)
+    dZc = [c.numpy() for c in dZ.cores()]
+    dc = out["dc"].double().cpu().numpy()
+    ez, ec = [], []
+    for j in (0, 500, 999):
+        rz, rc = O.project_sum_vjp(U5, V5, [Z5[j]], [c5[j]], dU5)
+        ez.append(rel([c[j] for c in dZc], rz[0]))
+        ec.append(abs(dc[j] - rc[0]) / abs(rc[0]))
+    rec("psum_bwd.dZ", ez, 1e-5)
+    rec("psum_bwd.dc", ec, 1e-5)
+    # uneven batch: sampled pairs of every group, first norm of every group, one adjoint object
+    dims, modes, ranks, offs = w.r4meta
+    rg = t3f.RaggedTT(w.host["X4"], dims, modes, ranks, offs)
+    ob = lambda o, src=rg: [c.double().numpy() for c in src.object_cores(o)]
+    G4 = out["G4"].double().cpu().numpy()
+    n4 = out["n4"].double().cpu().numpy()
+    gd = t3f.RaggedTT(out["dX4"].detach().cpu(), dims, modes, ranks, offs)
+    dG4 = w.host["dG4"].double().numpy()
+    rng = np.random.default_rng(77)
+    ediag, eoff, enorm, ebwd = [], [], [], []
+    off = 0
+    for gi in range(len(w.gstart) - 1):
+        g0, Sg = w.gstart[gi], w.gstart[gi + 1] - w.gstart[gi]
+        pairs = [(0, 0), (Sg - 1, Sg - 1)]
+        while len(pairs) < 12:
+            a, b = (int(v) for v in rng.integers(0, Sg, 2))
+            if a != b:
+                pairs.append((a, b))
+        got = np.array([G4[off + a * Sg + b] for a, b in pairs])
+        want = np.array([O.dot(ob(g0 + a), ob(g0 + b)) for a, b in pairs])
+        ediag.append(rel(got[:2], want[:2]))
+        eoff.append(rel(got[2:], want[2:]))
+        enorm.append(abs(n4[g0] - O.norm(ob(g0))) / O.norm(ob(g0)))
+        a = int(rng.integers(0, Sg))
+        M = dG4[off:off + Sg * Sg].reshape(Sg, Sg)
+        grp = [ob(g0 + j) for j in range(Sg)]
+        ref = O.gram_vjp([grp[a]], grp, (M[a, :] + M[:, a])[None, :])[0][0]
+        ebwd.append(rel(ob(g0 + a, gd), ref))
+        off += Sg * Sg
+    rec("uneven.G.diag", ediag, 1e-5)
+    rec("uneven.G.offdiag", eoff, 1e-5)
+    rec("uneven.norms", enorm, 1e-5)
+    rec("uneven_bwd.dX", ebwd, 1e-5)
+    for key, (G_, tol) in (extra or {}).items():
+        if key.startswith("gram_"):
+            Gx = G_.double().cpu().numpy()
+            rec(key + ".G", [rel(Gx[a], [O.dot(A[a], Bb) for Bb in B]) for a in (0, 57, 99)], tol)
+        elif key.startswith("uneven_"):
+            Gx = G_.double().cpu().numpy()
+            rg_x = rg
+            if "bf16" in key:
+                import torch as _t
+                rg_x = t3f.RaggedTT(w.host["X4"].to(_t.bfloat16).to(_t.float64), dims, modes, ranks, offs)
+            obx = lambda o: [c.double().numpy() for c in rg_x.object_cores(o)]
+            ed, eo, off = [], [], 0
+            for gi in range(len(w.gstart) - 1):
+                g0, Sg = w.gstart[gi], w.gstart[gi + 1] - w.gstart[gi]
+                pairs = [(0, 0), (Sg - 1, Sg - 1), (0, Sg - 1), (1, 2), (3, Sg - 2), (Sg // 2, 5)]
+                got = np.array([Gx[off + a * Sg + b] for a, b in pairs])
+                want = np.array([O.dot(obx(g0 + a), obx(g0 + b)) for a, b in pairs])
+                ed.append(rel(got[:2], want[:2]))
+                eo.append(rel(got[2:], want[2:]))
+                off += Sg * Sg
+            rec(key + ".G.diag", ed, tol)
+            rec(key + ".G.offdiag", eo, tol)
+    res["_seconds"] = round(time.perf_counter() - t0, 2)
+    return res
 
 
 def reference_arm(args):
@@ -728,12 +1026,15 @@ def gpu_arm(args):
 
     dev_ms, e2e_ms, value, e2e_value = combine_ranks(dev_ms, e2e_ms, world, step_flops, dev)
 
+    # FP32 FMA peak measured on this GPU (the ALU roofline's denominator)
+    fp32 = measured_fp32_peak(t3f, torch, dev, local)
+    peak32 = fp32["tflops"]
     # dominant operation and its roofline (FP32 CUDA-core pipe)
     dom = max(op_ms, key=op_ms.get)
     ach = flops[dom] / (op_ms[dom] * 1e-3) / 1e12
     per_op = {k: {"ms": round(op_ms[k], 4), "gflop": round(flops[k] / 1e9, 4),
                   "gflops": round(flops[k] / (op_ms[k] * 1e-3) / 1e9, 1),
-                  "frac_fp32": round(flops[k] / (op_ms[k] * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, 4)}
+                  "frac_fp32": round(flops[k] / (op_ms[k] * 1e-3) / 1e12 / peak32, 4)}
               for k in op_ms}
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
@@ -755,9 +1056,11 @@ def gpu_arm(args):
                    "ms_per_step_one_stream": round(seq_ms, 4),
                    "uneven_tiles": list(w.tiles4)},
         "roofline": {"bound": "alu", "kernel_op": dom, "achieved": round(ach, 3),
-                     "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-                     "frac": round(ach / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
-                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (derived)"},
+                     "peak": peak32, "unit": "TFLOP/s",
+                     "frac": round(ach / peak32, 4), "traffic": traffic,
+                     "peak_source": "measured: FP32 FMA probe on this GPU (fp32_peak)",
+                     "frac_of_derived": round(ach / FP32_PEAK_TFLOPS, 4)},
+        "fp32_peak": fp32,
         "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": w.h2d_bytes,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
         "gpu_launches": launches,
@@ -766,11 +1069,11 @@ def gpu_arm(args):
     }
     # single-shape FP32 comparator for the uneven batch (outside the timed step)
     if not args.no_comparator:
-        groups = w.plain_uneven()
+        groups = bucket_comparator(w)
         def plain():
-            for A, dG in groups:
-                t3f.gram(A, A)
-                t3f.gram_backward(A, A, dG)
+            for A, B, dG in groups:
+                t3f.gram(A, B)
+                t3f.gram_backward(A, B, dG)
         plain()
         torch.cuda.synchronize(dev)
         reps = 2
@@ -785,12 +1088,21 @@ def gpu_arm(args):
         um = op_ms["uneven"] + op_ms["uneven_bwd"]
         uf = flops["uneven"] + flops["uneven_bwd"]
         line["comparators"] = {"uneven_plain_fp32": {
-            "what": "per-group uniform Gram + adjoint launches, ranks zero-padded to the group maximum",
+            "what": "per group and rank-bucket pair (<= 8, 16, 32, 64) one uniform FP32 Gram + adjoint "
+                    "launch pair, each bucket padded to its own largest rank; no work queue, no graph",
+            "launches": 2 * len(groups),
             "ms": round(pm, 3), "gflops_same_work": round(uf / (pm * 1e-3) / 1e9, 1),
             "uneven_ms": round(um, 3), "uneven_speedup": round(pm / um, 2)}}
         del groups
     # reduced-precision forms of the same work (outside the timed step; FP32 step above)
-    line["reduced_precision"] = reduced_precision(w, flops, flush, stream)
+    line["reduced_precision"], rp_out = reduced_precision(w, flops, flush, stream)
+    # tangent-space rows measured beside the step
+    line["next_rows"] = next_rows(w, flush, stream, peak32)
+    # error of every output against the FP64 oracle (one step's outputs, sampled)
+    if rank == 0 and not args.no_oracle_check:
+        out = run_step(w, None, stream, side)
+        torch.cuda.synchronize(dev)
+        line["oracle_err"] = oracle_errors(w, out, rp_out)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f, s, desc, _ = oracle_sample(args.cpu_fraction)
         line["cpu_baseline"] = {"value": round(f / s / 1e9, 4), "unit": "GFLOP/s", "cores": 1,
@@ -811,6 +1123,7 @@ def main():
     ap.add_argument("--cpu-fraction", type=float, default=0.15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

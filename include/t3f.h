@@ -383,6 +383,14 @@ t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t ngroups,
                                     size_t ws_bytes, t3f_stream_t stream);
 
 /*
+ * FP32 FMA throughput probe (no counterpart in the paper; a measurement aid for the CUDA-core
+ * roofline): `grid` CTAs of 256 threads each run 8 independent FMA chains for iters * 16
+ * steps; t3f_fma_probe_flops() gives the FLOPs of one launch. out: device float [grid * 256].
+ */
+t3f_status t3f_fma_probe(int32_t grid, int64_t iters, float* out, t3f_stream_t stream);
+double t3f_fma_probe_flops(int32_t grid, int64_t iters);
+
+/*
  * Device-side error word of the last call that used `ws` (enqueued on `stream`, read after
  * a synchronisation): 0 = none, T3F_ERR_ARG = an index tuple was out of range,
  * T3F_ERR_TIMEOUT = a bounded wait ran out. Synchronises `stream`.

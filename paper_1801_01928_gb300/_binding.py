@@ -71,6 +71,8 @@ _SIGS = {
     "t3f_project_matvec_workspace_size": (ctypes.c_size_t, [_P, _P, _P]),
     "t3f_project_matvec": (ctypes.c_int32, [_P, _P, _P, _P, _P, _VP, _SZ, _VP]),
     "t3f_completion_hvp": (ctypes.c_int32, [_P, _P, _VP, ctypes.c_int64, _P, _P, _VP, _SZ, _VP]),
+    "t3f_fma_probe": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int64, _VP, _VP]),
+    "t3f_fma_probe_flops": (ctypes.c_double, [ctypes.c_int32, ctypes.c_int64]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -357,6 +359,13 @@ def completion_hvp(U: TT, V: TT, idx: torch.Tensor, dZ: TT, return_ws: bool = Fa
     _check(_lib().t3f_completion_hvp(_ref(U), _ref(V), _ptr(idx), N, _ref(dZ), _ref(out), _ptr(ws), ws.numel(),
                                      _stream(dev)), "t3f_completion_hvp")
     return (out, ws) if return_ws else out
+
+
+def fma_probe(grid: int, iters: int, device="cuda"):
+    """Launch the FP32 FMA probe once; returns (FLOPs of the launch, its output buffer)."""
+    out = torch.empty(grid * 256, dtype=torch.float32, device=device)
+    _check(_lib().t3f_fma_probe(grid, iters, _ptr(out), _stream(torch.device(device))), "t3f_fma_probe")
+    return float(_lib().t3f_fma_probe_flops(grid, iters)), out
 
 
 def device_status(ws: torch.Tensor) -> int:

@@ -31,6 +31,7 @@ struct GatherArgs {
   long long Loff[T3F_MAX_D];
   const float* Rg;           // suffix cores, packed, batch 1
   long long Roff[T3F_MAX_D];
+  long long Lnfl, Rnfl;      // floats of the packed prefix / suffix object
   int same;                  // L and R are the same cores
   const int* idx;            // [d][N]
   const float* y;            // nullable
@@ -43,17 +44,84 @@ struct GatherArgs {
   int* err;                  // device error word
 };
 
+// ---- whole-object staging through the TMA unit -------------------------------------------
+// One cp.async.bulk copies the packed cores of a batch-1 TT (rounded out to 16-byte
+// boundaries: the copy may start up to 12 bytes before the object and end up to 15 bytes
+// after it, always inside the same 16-byte block, hence the same page) into a landing zone
+// of shared memory; stage_from_raw then lays the slices out on chip. The landing zone is
+// the first core rounded down by delta floats: raw[delta + element offset].
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;  // about one second
+  }
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+__host__ __device__ __forceinline__ uint32_t raw_bytes(const float* src, long long nfl) {
+  const uintptr_t s = reinterpret_cast<uintptr_t>(src);
+  return (uint32_t)(((s & 15) + (uintptr_t)nfl * 4 + 15) & ~uintptr_t(15));
+}
+
+__device__ __forceinline__ int raw_delta(const float* src) { return (int)((reinterpret_cast<uintptr_t>(src) & 15) >> 2); }
+
+// thread 0: one bulk copy of [src, src + nfl) (rounded out) into raw, completing on bar
+__device__ __forceinline__ void tma_copy(float* raw, const float* src, long long nfl, uint64_t* bar) {
+  const uintptr_t s0 = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(raw)),
+               "l"(s0), "r"(raw_bytes(src, nfl)), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// zero-padded R x R slices with slice stride SS from the landed object
 template <int R>
-__device__ __forceinline__ void stage_padded(float* dst, const float* src, const long long* off,
-                                             const int* r, const int* n, int d, int nmax) {
-  const int total = d * nmax * R * R;
+__device__ __forceinline__ void stage_from_raw(float* dst, int SS, const float* raw, const long long* off,
+                                               const int* r, const int* n, int d, int nmax) {
+  const int total = d * nmax * SS;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int b = e % R, a = (e / R) % R, i = (e / (R * R)) % nmax, k = e / (R * R * nmax);
+    const int q = e % SS, i = (e / SS) % nmax, k = e / (SS * nmax);
+    const int a = q / R, b = q % R;
     float v = 0.0f;
-    if (i < n[k] && a < r[k] && b < r[k + 1])
-      v = __ldg(src + off[k] + ((long long)a * n[k] + i) * r[k + 1] + b);
+    if (q < R * R && i < n[k] && a < r[k] && b < r[k + 1]) v = raw[off[k] + ((long long)a * n[k] + i) * r[k + 1] + b];
     dst[e] = v;
   }
+}
+
+// land one object and stage it (every thread; bar used at `parity`); false on a timeout
+template <int R>
+__device__ bool stage_object_tma(float* dst, int SS, float* landing, const float* src, long long nfl,
+                                 const long long* off, const int* r, const int* n, int d, int nmax, uint64_t* bar,
+                                 uint32_t parity) {
+  if (threadIdx.x == 0) {
+    tma_expect(bar, raw_bytes(src, nfl));
+    tma_copy(landing, src, nfl, bar);
+  }
+  const bool ok = bar_wait(smem_u32(bar), parity);
+  stage_from_raw<R>(dst, SS, landing + raw_delta(src), off, r, n, d, nmax);
+  return ok;
 }
 
 __device__ __forceinline__ int load_index(const GatherArgs& g, int k, long long t) {
@@ -80,10 +148,15 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Forward: values and / or loss partials.
 template <int R>
 __global__ void __launch_bounds__(kGatherThreads) k_gather_fwd(const __grid_constant__ GatherArgs g) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   __shared__ double red[kGatherThreads / 32];
+  __shared__ __align__(8) uint64_t bar;
   float* Ls = sm;
-  stage_padded<R>(Ls, g.L, g.Loff, g.rl, g.n, g.d, g.nmax);
+  float* landing = sm + g.d * g.nmax * R * R;  // 16-byte aligned (R * R is a multiple of 16)
+  bar_init(&bar);
+  if (!stage_object_tma<R>(Ls, R * R, landing, g.L, g.Lnfl, g.Loff, g.rl, g.n, g.d, g.nmax, &bar, 0u) &&
+      threadIdx.x == 0)
+    atomicExch(g.err, (int)T3F_ERR_TIMEOUT);
   __syncthreads();
   double lsum = 0.0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < g.N;
@@ -135,8 +208,16 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_bwd(const __grid_cons
   float* Rs = g.same ? Ls : Ls + SL;
   float* acc = Ls + (g.same ? SL : 2 * SL);  // d * nmax * GS
   float* sfx = acc + g.d * g.nmax * GS;      // [d][R][blockDim]: suffix at interface k+1
-  stage_padded<R>(Ls, g.L, g.Loff, g.rl, g.n, g.d, g.nmax);
-  if (!g.same) stage_padded<R>(Rs, g.Rg, g.Roff, g.rr, g.n, g.d, g.nmax);
+  // both objects land in the accumulator region (zeroed afterwards), one after the other
+  __shared__ __align__(8) uint64_t bar;
+  bar_init(&bar);
+  bool ok = stage_object_tma<R>(Ls, R * R, acc, g.L, g.Lnfl, g.Loff, g.rl, g.n, g.d, g.nmax, &bar, 0u);
+  __syncthreads();
+  if (!g.same) {
+    ok &= stage_object_tma<R>(Rs, R * R, acc, g.Rg, g.Rnfl, g.Roff, g.rr, g.n, g.d, g.nmax, &bar, 1u);
+    __syncthreads();
+  }
+  if (!ok && threadIdx.x == 0) atomicExch(g.err, (int)T3F_ERR_TIMEOUT);
   for (int e = threadIdx.x; e < g.d * g.nmax * GS; e += blockDim.x) acc[e] = 0.0f;
   __syncthreads();
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -281,19 +362,21 @@ __global__ void __launch_bounds__(256, 1) k_completion(const __grid_constant__ C
   int* CNT = WC + (size_t)d * NB * NW;                                              // [d][NB]
   int* BO = CNT + (size_t)d * NB;                                                   // [d][NB+1]
 
-  // stage the cores as zero-padded R x R slices with stride SS
-  for (int e = tid; e < d * nmax * SS; e += blockDim.x) {
-    const int q = e % SS, i = (e / SS) % nmax, k = e / (SS * nmax);
-    const int a = q / R, b = q % R;
-    float vl = 0.0f, vr = 0.0f;
-    if (q < R * R && i < g.n[k]) {
-      if (a < g.rl[k] && b < g.rl[k + 1]) vl = __ldg(g.L + g.Loff[k] + ((long long)a * g.n[k] + i) * g.rl[k + 1] + b);
-      if (!g.same && a < g.rr[k] && b < g.rr[k + 1])
-        vr = __ldg(g.Rg + g.Roff[k] + ((long long)a * g.n[k] + i) * g.rr[k + 1] + b);
-    }
-    Ls[e] = vl;
-    if (!g.same) Rs[e] = vr;
+  // stage the cores as zero-padded R x R slices with stride SS: the whole object(s) land in
+  // the RH / LW region (not used before the first chunk) through one TMA bulk copy each
+  __shared__ __align__(8) uint64_t bar;
+  bar_init(&bar);
+  float* landL = reinterpret_cast<float*>(RH);
+  float* landR = landL + ((raw_bytes(g.L, g.Lnfl) + 15) / 16) * 4;
+  if (tid == 0) {
+    tma_expect(&bar, raw_bytes(g.L, g.Lnfl) + (g.same ? 0u : raw_bytes(g.Rg, g.Rnfl)));
+    tma_copy(landL, g.L, g.Lnfl, &bar);
+    if (!g.same) tma_copy(landR, g.Rg, g.Rnfl, &bar);
   }
+  if (!bar_wait(smem_u32(&bar), 0u) && tid == 0) atomicExch(g.err, (int)T3F_ERR_TIMEOUT);
+  stage_from_raw<R>(Ls, SS, landL + raw_delta(g.L), g.Loff, g.rl, g.n, d, nmax);
+  if (!g.same) stage_from_raw<R>(Rs, SS, landR + raw_delta(g.Rg), g.Roff, g.rr, g.n, d, nmax);
+  __syncthreads();
   // this thread's item (core ik, slice is, part ip) of the accumulation phase
   int ik = -1, is = 0, ip = 0, np = 1;
   for (int k = 0; k < d; ++k)
@@ -618,7 +701,9 @@ static GatherLayout gather_layout(const TTV& L, const TTV& Rv, long long N, bool
   const int nmax = L.nmax;
   const size_t SL = (size_t)L.d * nmax * R * R;
   if (!bwd) {
-    lay.smem = sizeof(float) * SL;
+    // padded slices + the TMA landing zone of the packed object (rounded out to 16 bytes)
+    const long long nfl = L.off[L.d - 1] + L.osz[L.d - 1];
+    lay.smem = sizeof(float) * SL + (size_t)((nfl * 4 + 12 + 15) / 16) * 16;
     lay.grid = gather_grid(N, num_sms() * 8);
   } else if (lay.R && plan_completion(L, same, R, &lay)) {
     long long g = (N + lay.T - 1) / lay.T;
@@ -662,6 +747,8 @@ static void fill_args(GatherArgs* g, const TTV& L, const TTV& Rv) {
   g->gsize = go;
   g->L = static_cast<const float*>(L.p);
   g->Rg = static_cast<const float*>(Rv.p);
+  g->Lnfl = L.off[L.d - 1] + L.osz[L.d - 1];
+  g->Rnfl = Rv.off[Rv.d - 1] + Rv.osz[Rv.d - 1];
 }
 
 template <int R>

@@ -108,6 +108,10 @@ size_t ws_project(const TTV& U, const TTV& Z);
 size_t ws_tangent_gram(const TTV& A, const TTV& B);
 size_t ws_completion_hvp(const TTV& U, const TTV& V, long long N);
 
+// TF32 tensor-core Gram of tangent coordinates fed by TMA (tgram_tc.cu).
+size_t ws_tangent_gram_tc(const TTV& A, const TTV& B);
+t3f_status run_tangent_gram_tc(const TTV& A, const TTV& B, float* G, void* ws, size_t ws_bytes, cudaStream_t s);
+
 }  // namespace t3f
 
 #define T3F_CHECK(x)                       \

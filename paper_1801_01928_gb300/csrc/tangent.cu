@@ -555,7 +555,9 @@ ProjectLayout project_layout(const TTV& U, const TTV& Z) {
 }  // namespace
 
 size_t ws_project(const TTV& U, const TTV& Z) { return project_layout(U, Z).total; }
-size_t ws_tangent_gram(const TTV& A, const TTV& B) { return tgram_plan(A, B).total; }
+size_t ws_tangent_gram(const TTV& A, const TTV& B) {
+  return std::max(tgram_plan(A, B).total, ws_tangent_gram_tc(A, B));
+}
 size_t ws_completion_hvp(const TTV& U, const TTV& V, long long N) {
   return align256(ws_rgather(U, V, N)) + align256(sizeof(float) * (size_t)std::max(N, 1LL));
 }
@@ -617,6 +619,7 @@ extern "C" t3f_status t3f_tangent_gram(const t3f_tt* dA, const t3f_tt* dB, float
   if (va.d != vb.d) return T3F_ERR_SHAPE;
   for (int k = 0; k <= va.d; ++k)
     if (va.r[k] != vb.r[k] || (k < va.d && va.n[k] != vb.n[k])) return T3F_ERR_SHAPE;
+  if (math == T3F_MATH_TF32) return run_tangent_gram_tc(va, vb, G, ws, ws_bytes, (cudaStream_t)stream);
   if (math != T3F_MATH_FP32) return T3F_ERR_UNSUPPORTED;
   const TGramPlan p = tgram_plan(va, vb);
   T3F_CHECK(check_ws(ws, ws_bytes, p.total));

@@ -143,3 +143,38 @@ def test_completion_hvp_out_of_range_index(lib):
     xi = [np.zeros((1,) + c.shape) for c in Uh]
     _, ws = lib.completion_hvp(U, V, torch.tensor(bad, device="cuda"), dev_tt(lib, xi), return_ws=True)
     assert lib.device_status(ws) == -1
+
+
+def test_tangent_gram_tf32_projected_config5_shape(lib):
+    # TMA + tcgen05 TF32 path on the self Gram matrix of 48 projected rank-8 TTs (one operand
+    # per diagonal tile), diagonal and off-diagonal entries within the TF32 tolerance
+    cfg = S.config5(batch=48)
+    X, Z, c = round32(cfg.X), round32(cfg.Z), cfg.c.astype(np.float32)
+    U, V, Uh, Vh = _uv(lib, X)
+    dU = lib.project(U, V, dev_tt(lib, Z), torch.tensor(c, device="cuda"))
+    G = lib.tangent_gram(dU, dU, math="tf32").double().cpu().numpy()
+    coords = host_objects(dU)
+    assert_gram_blocks(G, O.tangent_gram(coords, coords), [48], TOL["tf32"])
+
+
+def test_tangent_gram_tf32_two_operands_several_tiles(lib):
+    # 200 x 130 pairs: 2 x 2 tiles of 128, both operands loaded, ragged tile edges
+    rng = np.random.default_rng(701)
+    n, r = [4, 4, 4, 4, 4], [1, 4, 8, 8, 4, 1]
+    dA = round32(S.random_tt(rng, 200, n, r))
+    dB = round32(S.random_tt(rng, 130, n, r))
+    G = lib.tangent_gram(dev_tt(lib, dA), dev_tt(lib, dB), math="tf32").double().cpu().numpy()
+    Gref = O.tangent_gram(objects(dA), objects(dB))
+    assert G.shape == (200, 130)
+    assert rel_err(G, Gref) < TOL["tf32"]
+    # the FP32 path on the same inputs
+    G32 = lib.tangent_gram(dev_tt(lib, dA), dev_tt(lib, dB)).double().cpu().numpy()
+    assert rel_err(G32, Gref) < TOL["fp32"]
+
+
+def test_tangent_gram_tf32_rejects_unaligned_rows(lib):
+    rng = np.random.default_rng(702)
+    dA = round32(S.random_tt(rng, 5, [3, 3], [1, 3, 1]))  # 9 floats per core row
+    with pytest.raises(lib.T3FError) as e:
+        lib.tangent_gram(dev_tt(lib, dA), dev_tt(lib, dA), math="tf32")
+    assert e.value.status == -7
