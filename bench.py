@@ -153,6 +153,29 @@ def f_project_matvec(m, n, rx, ra, rc, batch):
     return batch * (tot + f_gauge(m, rx))
 
 
+def f_round(n, ranks, maxr):
+    """TT rounding, non-iterative part: the right-to-left Householder QRs (factor + form Q)
+    with the R products, then per interface the Gram matrix of the smaller side, the left
+    singular vectors (when formed from M V) and the S V^T product into the next core (the
+    Jacobi sweeps, an iteration, are not counted)."""
+    d = len(n)
+    r = list(ranks)
+    tot = 0.0
+    for k in range(d - 1, 0, -1):
+        m, c = n[k] * r[k + 1], r[k]
+        q = min(m, c)
+        tot += f_qr(m, c) + 2 * r[k - 1] * n[k - 1] * c * q
+        r[k] = q
+    rr = [1] + [0] * d
+    for k in range(d - 1):
+        m, c = rr[k] * n[k], r[k + 1]
+        s = min(m, c)
+        p = min(maxr, s)
+        tot += 2 * s * s * max(m, c) + (2 * m * c * p if m > c else 2 * p * m * c) + 2 * p * c * n[k + 1] * r[k + 2]
+        rr[k + 1] = p
+    return tot
+
+
 def f_hvp(r, n, N):
     """tangent-vector gather (three chains of r x r products per core) + the Riemannian scatter."""
     d = len(r) - 1
@@ -485,6 +508,25 @@ def reduced_precision(w, flops, flush, stream, reps=5):
         out[f"gram_{math_}"] = {"ms": round(ms, 4), "gflops": round(gf, 1),
                                 "diff_vs_fp32": round(rel(G, G32), 6), "roofline": roof(gf, math_),
                                 "path": "tcgen05 " + math_ + " products, FP32 accumulation in TMEM"}
+    # the uneven adjoint on BF16-stored cores (FP32 arithmetic) next to the FP32 one
+    dX32 = w.dX4.double()
+    ms = timed(lambda: t3f.gram_groups_backward(X4b, w.gstart, ws4b, w.devbuf["dG4"], w.tiles4))
+    dXb = t3f.gram_groups_backward(X4b, w.gstart, ws4b, w.devbuf["dG4"], w.tiles4)
+    gf = flops["uneven_bwd"] / (ms * 1e-3) / 1e9
+    out["uneven_bwd_bf16_cores"] = {"ms": round(ms, 4), "gflops": round(gf, 1), "diff_vs_fp32": round(rel(dXb, dX32), 6),
+                                    "path": "BF16 cores, FP32 CUDA-core arithmetic (adjoint work lists)"}
+    # project_sum of config 5 with the U- and V-side sweep contractions on the tensor cores
+    X5, Z5, c5 = w.tt("X5"), w.tt("Z5"), w.devbuf["c5"]
+    U5, V5 = t3f.orthogonalize(X5)
+    P32 = t3f.project_sum(U5, V5, Z5, c5).data.double()
+    ms = timed(lambda: t3f.project_sum(U5, V5, Z5, c5, math="tf32"))
+    Ptf = t3f.project_sum(U5, V5, Z5, c5, math="tf32")
+    keep["psum_tf32"] = (Ptf.data, 5e-3)
+    gf = flops["psum"] / (ms * 1e-3) / 1e9
+    out["psum_tf32"] = {"ms": round(ms, 4), "gflops": round(gf, 1), "diff_vs_fp32": round(rel(Ptf.data, P32), 6),
+                        "roofline": roof(gf, "tf32"),
+                        "path": "sweeps: CUDA-core L Z_i factor + tcgen05 TF32 products against U_k / V_k "
+                                "(M = 128, N = 32, K = r n), TMA bulk Z staging; FP32 assembly and gauge"}
     for key, X_, ws_, math_, path in (
             ("uneven_bf16_cores", X4b, ws4b, "fp32", "BF16 cores, FP32 CUDA-core arithmetic (grouped work list)"),
             ("uneven_tf32", X4, w.ws4, "tf32", "F32 cores; tcgen05 TF32 tiles, FP32 accumulation"),
@@ -517,6 +559,24 @@ def event_time(torch, fn, flush, stream, reps=5):
     return tot / reps
 
 
+def measured_fp64_peak(t3f, torch, dev):
+    """FP64 FMA rate of this GPU from the library's FP64 probe (same shape as the FP32 one)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    grid, iters = sms * 4, 400
+    t3f.fma_probe(grid, iters, dev, fp64=True)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        flops, _ = t3f.fma_probe(grid, iters, dev, fp64=True)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / 3
+    return {"tflops": round(flops / (ms * 1e-3) / 1e12, 3), "ms_per_launch": round(ms, 3),
+            "how": f"t3f_fma_probe_f64: {grid} CTAs x 256 threads x 8 DFMA chains, CUDA events"}
+
+
 def measured_fp32_peak(t3f, torch, dev, gpu_index):
     """FP32 FMA rate of this GPU from the library's FMA probe (8 independent chains per
     thread, 4 CTAs of 256 threads per SM), with the SM clock sampled while it runs."""
@@ -541,7 +601,7 @@ def measured_fp32_peak(t3f, torch, dev, gpu_index):
             "how": f"t3f_fma_probe: {grid} CTAs x 256 threads x 8 FMA chains, CUDA events"}
 
 
-def next_rows(w, flush, stream, fp32_peak):
+def next_rows(w, flush, stream, fp32_peak, fp64_peak=None):
     """The tangent-space rows beyond the step (Section 3.2), each timed on its own:
     batched projection of 100 config-5 TTs + the Gram matrix of their tangent vectors (FP32
     CUDA cores and TF32 tensor cores via TMA), the projected matvec P_X(A x_j) at config-3b
@@ -599,6 +659,18 @@ def next_rows(w, flush, stream, fp32_peak):
     ms = event_time(torch, lambda: t3f.completion_hvp(U2, V2, idx, g2), flush, stream)
     ru2 = t3f.orth_ranks([10] * 10, S.tt_ranks(10, 8))
     row("completion_hvp", ms, f_hvp(ru2, [10] * 10, idx.shape[1]))
+    # TT rounding (FP64 TT-SVD) of the 100 rank-100 matvec products of config 3b to rank 10
+    C = t3f.matvec(w.tt("Am"), xv)
+    ms = event_time(torch, lambda: t3f.round_tt(C, 10), flush, stream, reps=3)
+    fl = 100 * f_round([4] * 10, C.ranks, 10)
+    gf = fl / (ms * 1e-3) / 1e9
+    out["round"] = {"ms": round(ms, 4), "gflop": round(fl / 1e9, 4), "gflops": round(gf, 2),
+                    "what": "100 TT-vectors of rank 100 (d=10, n=4) rounded to rank 10, FP64",
+                    "roofline": {"bound": "alu", "achieved": round(gf / 1e3, 4),
+                                 "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
+                                 "frac": round(gf / 1e3 / fp64_peak, 4) if fp64_peak else None,
+                                 "peak_source": "measured FP64 FMA probe",
+                                 "flops": "QR, Gram, singular-vector and S V^T products; Jacobi sweeps not counted"}}
     return out
 
 
@@ -827,7 +899,10 @@ def oracle_errors(w, out, extra=None):
     c5 = w.host["c5"].double().numpy()
     U5, V5, ru5 = O.orthogonalize(X5)
     dU5 = objs("X5", out["dU5"], ranks=ru5)[0]
-    rec("psum.dU", [rel(dU5, O.project_sum(U5, V5, Z5, c5))], 1e-5)
+    psum_ref = O.project_sum(U5, V5, Z5, c5)
+    rec("psum.dU", [rel(dU5, psum_ref)], 1e-5)
+    if extra and "psum_tf32" in extra:
+        rec("psum_tf32.dU", [rel(objs("X5", extra["psum_tf32"][0], ranks=ru5)[0], psum_ref)], extra["psum_tf32"][1])
     dZ = w.t3f.TT(out["_bulk"][1].data.detach().cpu().double(), [16] * 20, S.tt_ranks(20, 8), 1000)
     dZc = [c.numpy() for c in dZ.cores()]
     dc = out["dc"].double().cpu().numpy()
@@ -872,6 +947,8 @@ def oracle_errors(w, out, extra=None):
     rec("uneven.norms", enorm, 1e-5)
     rec("uneven_bwd.dX", ebwd, 1e-5)
     for key, (G_, tol) in (extra or {}).items():
+        if key == "psum_tf32":
+            continue
         if key.startswith("gram_"):
             Gx = G_.double().cpu().numpy()
             rec(key + ".G", [rel(Gx[a], [O.dot(A[a], Bb) for Bb in B]) for a in (0, 57, 99)], tol)
@@ -1097,7 +1174,9 @@ def gpu_arm(args):
     # reduced-precision forms of the same work (outside the timed step; FP32 step above)
     line["reduced_precision"], rp_out = reduced_precision(w, flops, flush, stream)
     # tangent-space rows measured beside the step
-    line["next_rows"] = next_rows(w, flush, stream, peak32)
+    fp64 = measured_fp64_peak(t3f, torch, dev)
+    line["fp64_peak"] = fp64
+    line["next_rows"] = next_rows(w, flush, stream, peak32, fp64["tflops"])
     # error of every output against the FP64 oracle (one step's outputs, sampled)
     if rank == 0 and not args.no_oracle_check:
         out = run_step(w, None, stream, side)

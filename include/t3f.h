@@ -80,7 +80,8 @@ typedef enum {
   T3F_OP_GATHER = 4, T3F_OP_GATHER_BWD = 5, T3F_OP_RGATHER_BWD = 6,
   T3F_OP_MATVEC = 7, T3F_OP_MATVEC_BWD = 8,
   T3F_OP_ORTH = 9, T3F_OP_PSUM = 10, T3F_OP_PSUM_BWD = 11,
-  T3F_OP_PROJECT = 12, T3F_OP_TANGENT_GRAM = 13, T3F_OP_COMPLETION_HVP = 14
+  T3F_OP_PROJECT = 12, T3F_OP_TANGENT_GRAM = 13, T3F_OP_COMPLETION_HVP = 14,
+  T3F_OP_ROUND = 15
 } t3f_op;
 
 /* Name of a status code (static string). */
@@ -104,6 +105,7 @@ int64_t t3f_packed_size(const t3f_tt* t);
  *   MATVEC, MATVEC_BWD: a = A (TT-matrix), b = x.
  *   ORTH: a = X.    PSUM, PSUM_BWD, PROJECT: a = U, b = Z (the batch being projected).
  *   TANGENT_GRAM: a = dA, b = dB.   COMPLETION_HVP: a = U, b = V, n_items = N.
+ *   ROUND: a = X.
  * Returns 0 for an invalid request (check with the call itself for the status).
  */
 size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* b, int64_t n_items);
@@ -212,7 +214,7 @@ t3f_status t3f_matvec(const t3f_tt* A, const t3f_tt* x, t3f_tt* C, void* ws,
 
 /* Adjoint of t3f_matvec: dA^k[a,i,j,a'] = sum_{b,b'} dC^k[(a,b),i,(a',b')] x^k[b,j,b'],
  * dx^k[b,j,b'] = sum_{a,a',i} dC^k[(a,b),i,(a',b')] A^k[a,i,j,a'] (summed over the batch on
- * a broadcast side). dA or dx may be NULL. */
+ * a broadcast side). dA or dx may be NULL. ws is not used (may be NULL). */
 t3f_status t3f_matvec_backward(const t3f_tt* A, const t3f_tt* x, const t3f_tt* dC,
                                t3f_tt* dA, t3f_tt* dx, void* ws, size_t ws_bytes,
                                t3f_stream_t stream);
@@ -247,9 +249,12 @@ t3f_status t3f_orthogonalize(const t3f_tt* X, t3f_tt* U, t3f_tt* V, void* ws,
  * [Z->batch]; dU: F32 descriptor with U's shape. With Z->batch = 1 and c = 1 this is the
  * projection P_X Z ('project' in Table 1). The TT of S has cores [dU_1, U_1],
  * [[V_k, 0], [dU_k, U_k]], [[V_d], [dU_d]] (ranks <= 2 r).
- * math: FP32; TF32 and BF16 are accepted when Z's ranks are < 16 (every contraction then has
- * one side below the tensor-core threshold, and the FP32 CUDA-core sweeps run), else
- * T3F_ERR_UNSUPPORTED.
+ * math: FP32 (CUDA cores), or TF32: the U- and V-side contractions of both sweeps
+ * (L'_j = sum_i U_i^T (L_j Z_j,i), M = 128 rows of 16 objects x 8, N = r_X, K = r_X n) run on
+ * the tensor cores (tcgen05, TF32 operands, FP32 accumulation), the assembly and the gauge
+ * projection in FP32; X ranks <= 32, Z ranks <= 8, modes <= 16 and multiples of 8, else
+ * T3F_ERR_UNSUPPORTED (also for BF16). A tensor-core wait that runs out writes T3F_ERR_TIMEOUT
+ * into the workspace's error word.
  */
 t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3f_tt* Z,
                            const float* c, t3f_tt* dU, int32_t math, void* ws,
@@ -317,6 +322,22 @@ t3f_status t3f_project_matvec(const t3f_tt* U, const t3f_tt* V, const t3f_tt* A,
 t3f_status t3f_completion_hvp(const t3f_tt* U, const t3f_tt* V, const int32_t* idx, int64_t N,
                               const t3f_tt* dZ, t3f_tt* out, void* ws, size_t ws_bytes,
                               t3f_stream_t stream);
+
+/*
+ * TT rounding (paper Section 3, t3f.round: the approximation of X by a TT of ranks
+ * <= max_rank), the TT-SVD recompression in FP64 for every object of the batch: a
+ * right-to-left Householder orthogonalisation sweep (diag(R) >= 0), then left to right the
+ * SVD of each (r_{k-1} n_k) x r_k unfolding truncated to its leading min(max_rank, .)
+ * singular triplets, S V^T pushed into the next core. Every kept left singular vector has its
+ * entry of largest magnitude positive (this fixes the cores element by element where the
+ * singular values are distinct). X: F32 batch (ranks up to 164 on each QR, every truncated
+ * unfolding with min(rows, cols) <= 100, else T3F_ERR_UNSUPPORTED); Y: F32 batch of X's modes
+ * with ranks t3f_round_ranks(X, max_rank). ws: t3f_workspace_size(T3F_OP_ROUND, X) bytes.
+ */
+t3f_status t3f_round_ranks(int32_t d, const int32_t* n, const int32_t* ranks, int32_t max_rank,
+                           int32_t* out_ranks);
+t3f_status t3f_round(const t3f_tt* X, int32_t max_rank, t3f_tt* Y, void* ws, size_t ws_bytes,
+                     t3f_stream_t stream);
 
 /*
  * A ragged collection of TT-vectors: object o has d[o] cores, modes
@@ -389,6 +410,9 @@ t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t ngroups,
  */
 t3f_status t3f_fma_probe(int32_t grid, int64_t iters, float* out, t3f_stream_t stream);
 double t3f_fma_probe_flops(int32_t grid, int64_t iters);
+/* The same probe in FP64 (the denominator of the FP64 rounding and orthogonalisation);
+ * out: device double [grid * 256]. */
+t3f_status t3f_fma_probe_f64(int32_t grid, int64_t iters, double* out, t3f_stream_t stream);
 
 /*
  * Device-side error word of the last call that used `ws` (enqueued on `stream`, read after

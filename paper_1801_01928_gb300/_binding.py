@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_PKG, "libt3f.so")
 F32, F64, BF16 = 0, 1, 2
 MATH = {"fp32": 0, "tf32": 1, "bf16": 2}
 OP = dict(gram=1, gram_bwd=2, norm=3, gather=4, gather_bwd=5, rgather_bwd=6, matvec=7,
-          matvec_bwd=8, orth=9, psum=10, psum_bwd=11, project=12, tangent_gram=13, completion_hvp=14)
+          matvec_bwd=8, orth=9, psum=10, psum_bwd=11, project=12, tangent_gram=13, completion_hvp=14,
+          round=15)
 _TORCH_DTYPE = {F32: torch.float32, F64: torch.float64, BF16: torch.bfloat16}
 _CODE = {v: k for k, v in _TORCH_DTYPE.items()}
 
@@ -73,6 +74,11 @@ _SIGS = {
     "t3f_completion_hvp": (ctypes.c_int32, [_P, _P, _VP, ctypes.c_int64, _P, _P, _VP, _SZ, _VP]),
     "t3f_fma_probe": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int64, _VP, _VP]),
     "t3f_fma_probe_flops": (ctypes.c_double, [ctypes.c_int32, ctypes.c_int64]),
+    "t3f_fma_probe_f64": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int64, _VP, _VP]),
+    "t3f_round_ranks": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32)]),
+    "t3f_round": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _VP, _SZ, _VP]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -361,10 +367,26 @@ def completion_hvp(U: TT, V: TT, idx: torch.Tensor, dZ: TT, return_ws: bool = Fa
     return (out, ws) if return_ws else out
 
 
-def fma_probe(grid: int, iters: int, device="cuda"):
-    """Launch the FP32 FMA probe once; returns (FLOPs of the launch, its output buffer)."""
-    out = torch.empty(grid * 256, dtype=torch.float32, device=device)
-    _check(_lib().t3f_fma_probe(grid, iters, _ptr(out), _stream(torch.device(device))), "t3f_fma_probe")
+def round_ranks(n, ranks, max_rank):
+    out = (ctypes.c_int32 * (len(n) + 1))()
+    _check(_lib().t3f_round_ranks(len(n), _i32(n), _i32(ranks), int(max_rank), out), "t3f_round_ranks")
+    return [int(v) for v in out]
+
+
+def round_tt(X: TT, max_rank: int) -> TT:
+    """TT rounding of every object of X to ranks <= max_rank (FP64 TT-SVD, F32 output)."""
+    dev = X.data.device
+    Y = TT.empty(X.n, round_ranks(X.n, X.ranks, max_rank), X.batch, None, torch.float32, dev)
+    ws = _ws("round", X, None, 0, dev)
+    _check(_lib().t3f_round(_ref(X), int(max_rank), _ref(Y), _ptr(ws), ws.numel(), _stream(dev)), "t3f_round")
+    return Y
+
+
+def fma_probe(grid: int, iters: int, device="cuda", fp64: bool = False):
+    """Launch the FP32 (or FP64) FMA probe once; returns (FLOPs of the launch, its output)."""
+    out = torch.empty(grid * 256, dtype=torch.float64 if fp64 else torch.float32, device=device)
+    fn = _lib().t3f_fma_probe_f64 if fp64 else _lib().t3f_fma_probe
+    _check(fn(grid, iters, _ptr(out), _stream(torch.device(device))), "t3f_fma_probe")
     return float(_lib().t3f_fma_probe_flops(grid, iters)), out
 
 

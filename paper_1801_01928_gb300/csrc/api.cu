@@ -147,6 +147,7 @@ extern "C" size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* 
     case T3F_OP_PROJECT: return ws_project(va, vb);
     case T3F_OP_TANGENT_GRAM: return ws_tangent_gram(va, vb);
     case T3F_OP_COMPLETION_HVP: return ws_completion_hvp(va, vb, n_items);
+    case T3F_OP_ROUND: return ws_round(va);
     default: return 0;
   }
 }

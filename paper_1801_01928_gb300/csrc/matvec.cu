@@ -67,6 +67,55 @@ __global__ void __launch_bounds__(256) k_matvec(const __grid_constant__ MatvecAr
   }
 }
 
+// Forward for column modes n = N and x's left rank r_x <= RB (the common shapes): a thread
+// owns positions q = (i, a', b') of the row block, keeps x[b, :, b'] for every b in registers,
+// and for every row a loads A[a, i, :, a'] once to write the r_x outputs (a, b), b < r_x:
+// about N + 2 instructions per output instead of a division chain per output.
+template <int N, int RB>
+__global__ void __launch_bounds__(256) k_matvec_n(const __grid_constant__ MatvecArgs a) {
+  extern __shared__ float sm[];
+  const int p = blockIdx.x / a.A.d, k = blockIdx.x % a.A.d;
+  const TTV& A = a.A;
+  const TTV& X = a.x;
+  const int ra0 = A.r[k], ra1 = A.r[k + 1], rx0 = X.r[k], rx1 = X.r[k + 1];
+  const int m = A.m[k];
+  float* As = sm;             // [ra0][m][N][ra1]
+  float* Xs = sm + a.maxA;    // [rx0][N][rx1]
+  const float* Ap = static_cast<const float*>(A.p) + core_base(A, k, a.bA == 1 ? 0 : p);
+  const float* Xp = static_cast<const float*>(X.p) + core_base(X, k, a.bx == 1 ? 0 : p);
+  const int sa = ra0 * m * N * ra1, sx = rx0 * N * rx1;
+  for (int e = threadIdx.x; e < sa; e += blockDim.x) As[e] = __ldg(Ap + e);
+  for (int e = threadIdx.x; e < sx; e += blockDim.x) Xs[e] = __ldg(Xp + e);
+  __syncthreads();
+  float* Cp = static_cast<float*>(a.C.p) + core_base(a.C, k, p);
+  const int rowlen = m * ra1 * rx1;
+  for (int q = threadIdx.x; q < rowlen; q += blockDim.x) {
+    const int i = q / (ra1 * rx1), c1 = q - i * (ra1 * rx1);
+    const int ap = c1 / rx1, bp = c1 - ap * rx1;
+    float xr[RB][N];
+#pragma unroll
+    for (int be = 0; be < RB; ++be)
+#pragma unroll
+      for (int j = 0; j < N; ++j) xr[be][j] = be < rx0 ? Xs[(be * N + j) * rx1 + bp] : 0.0f;
+    const float* Ar = As + (i * N) * ra1 + ap;  // A[al, i, j, ap] at al * m * N * ra1 + j * ra1
+    float* cq = Cp + q;
+    for (int al = 0; al < ra0; ++al) {
+      float av[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) av[j] = Ar[(al * m * N + j) * ra1];
+#pragma unroll
+      for (int be = 0; be < RB; ++be) {
+        if (be < rx0) {
+          float s = 0.0f;
+#pragma unroll
+          for (int j = 0; j < N; ++j) s = fmaf(av[j], xr[be][j], s);
+          cq[(long long)(al * rx0 + be) * rowlen] = s;
+        }
+      }
+    }
+  }
+}
+
 // Adjoint: one CTA per (pair, core). Rows a of dC are staged in shared memory in turn.
 struct MatvecBwdArgs {
   TTV A, x, dC;
@@ -193,10 +242,24 @@ extern "C" t3f_status t3f_matvec(const t3f_tt* A, const t3f_tt* x, t3f_tt* C, vo
   const long long grid = (long long)P * va.d;
   if (grid > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaFuncSetAttribute(k_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return T3F_ERR_CUDA;
-  k_matvec<<<(unsigned)grid, 256, smem, s>>>(args);
-  return launch_status();
+  // the specialised kernels need one column mode for every core and r_x <= 16 on the left
+  int nall = va.n[0], rxmax = 0;
+  for (int k = 0; k < va.d; ++k) {
+    if (va.n[k] != nall) nall = -1;
+    if (vx.r[k] > rxmax) rxmax = vx.r[k];
+  }
+  auto run = [&](auto kern) -> t3f_status {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<(unsigned)grid, 256, smem, s>>>(args);
+    return launch_status();
+  };
+  if (rxmax <= 16) {
+    if (nall == 2) return run(k_matvec_n<2, 16>);
+    if (nall == 4) return run(k_matvec_n<4, 16>);
+    if (nall == 8) return run(k_matvec_n<8, 16>);
+  }
+  return run(k_matvec);
 }
 
 extern "C" t3f_status t3f_matvec_backward(const t3f_tt* A, const t3f_tt* x, const t3f_tt* dC,

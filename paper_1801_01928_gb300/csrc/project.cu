@@ -423,9 +423,10 @@ extern "C" t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3
   T3F_CHECK(check_like(dU, vu, &vd));
   if (!c) return T3F_ERR_ARG;
   if (math != T3F_MATH_FP32 && math != T3F_MATH_TF32 && math != T3F_MATH_BF16) return T3F_ERR_ARG;
-  // tensor cores only pay off when both ranks of a contraction are >= 16; below that the
-  // reduced-precision modes run the FP32 CUDA-core sweeps (at least as accurate)
-  if (math != T3F_MATH_FP32 && vz.rmax >= 16) return T3F_ERR_UNSUPPORTED;
+  // TF32: the U- and V-side contractions of both sweeps on the tensor cores; BF16 has no
+  // tensor-core form here
+  if (math == T3F_MATH_BF16) return T3F_ERR_UNSUPPORTED;
+  if (math == T3F_MATH_TF32 && (!psweep_tc_supported(vu, vz) || !psweep_supported(vu, vz))) return T3F_ERR_UNSUPPORTED;
   PsumLayout l = psum_layout(vu, vz, false);
   T3F_CHECK(check_ws(ws, ws_bytes, l.total));
   cudaStream_t s = (cudaStream_t)stream;
@@ -433,6 +434,16 @@ extern "C" t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3
   float* Lst = reinterpret_cast<float*>(w + l.offL);
   float* Rst = reinterpret_cast<float*>(w + l.offR);
   float* part = reinterpret_cast<float*>(w + l.offPart);
+  if (math == T3F_MATH_TF32) {
+    int* err = static_cast<int*>(ws);
+    if (cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
+    T3F_CHECK(run_psweep_tc(vu, vz, 0, Lst, l.ioffL, err, s));
+    T3F_CHECK(run_psweep_tc(vv, vz, 1, Rst, l.ioffR, err, s));
+    T3F_CHECK(run_passemble(vu, vz, Lst, Rst, l.ioffL, c, part, l.nchunks, s));
+    k_reduce_chunks<<<256, 256, 0, s>>>(part, l.nchunks, l.gsize, part);
+    T3F_CHECK(launch_status());
+    return run_gauge_project(vu, part, static_cast<float*>(vd.p), s);
+  }
   if (psweep_supported(vu, vz)) {
     T3F_CHECK(run_psweep(vu, vz, 0, static_cast<const float*>(vu.p), nullptr, nullptr, Lst, nullptr, l.ioffL, s));
     T3F_CHECK(run_psweep(vv, vz, 1, static_cast<const float*>(vv.p), nullptr, nullptr, Rst, nullptr, l.ioffR, s));

@@ -76,6 +76,11 @@ bool psweep_supported(const TTV& X, const TTV& Z);
 t3f_status run_psweep(const TTV& X, const TTV& Z, int dir, const float* A, const float* B1, const float* B2,
                       float* st1, float* st2, const long long* ioff, cudaStream_t s);
 int passemble_ranges(const TTV& Z);
+// Tensor-core (TF32) form of the project_sum sweeps (psweep_tc.cu): X ranks <= 32, Z ranks
+// <= 8, modes <= 16 and multiples of 8.
+bool psweep_tc_supported(const TTV& X, const TTV& Z);
+t3f_status run_psweep_tc(const TTV& X, const TTV& Z, int dir, float* st, const long long* ioff, int* err,
+                         cudaStream_t s);
 t3f_status run_passemble(const TTV& X, const TTV& Z, const float* L, const float* R, const long long* ioff,
                          const float* c, float* part, int nranges, cudaStream_t s);
 t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V, const float* W, const float* L,
@@ -107,6 +112,13 @@ size_t ws_psum(const TTV& U, const TTV& Z, bool bwd);
 size_t ws_project(const TTV& U, const TTV& Z);
 size_t ws_tangent_gram(const TTV& A, const TTV& B);
 size_t ws_completion_hvp(const TTV& U, const TTV& V, long long N);
+
+size_t ws_round(const TTV& X);
+
+// Deterministic two-level sum of nsplit partial arrays of `size` floats (tangent.cu); mid
+// holds ws_split_reduce(size) bytes.
+t3f_status run_split_reduce(const float* part, int nsplit, long long size, float* mid, float* G, cudaStream_t s);
+size_t ws_split_reduce(long long size);
 
 // TF32 tensor-core Gram of tangent coordinates fed by TMA (tgram_tc.cu).
 size_t ws_tangent_gram_tc(const TTV& A, const TTV& B);

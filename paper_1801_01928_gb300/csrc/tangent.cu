@@ -146,7 +146,7 @@ __device__ void stage_slices(float* dst, const float* src, const TGatherArgs& g)
 }
 
 template <int R>
-__global__ void __launch_bounds__(128) k_tangent_gather(const __grid_constant__ TGatherArgs g) {
+__global__ void __launch_bounds__(256) k_tangent_gather(const __grid_constant__ TGatherArgs g) {
   extern __shared__ float sm[];
   const int SL = g.d * g.nmax * R * R;
   float* Us = sm;
@@ -278,18 +278,52 @@ __global__ void __launch_bounds__(kThreads) k_tgram(const __grid_constant__ TGra
     }
 }
 
-__global__ void k_tgram_reduce(const float* part, int nsplit, long long size, float* G) {
+// Sum of split partials in a fixed order, in two levels so that every SM takes part:
+// level 1 sums the splits g, g + G1, g + 2 G1, ... of each element into mid[g] (grid
+// elements / 256 x G1), level 2 sums the G1 groups.
+constexpr int kReduceGroups = 16;
+
+__global__ void k_split_reduce1(const float* part, int nsplit, long long size, float* mid) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y, G1 = gridDim.y;
+  if (e >= size) return;
+  float s = 0.0f;
+#pragma unroll 4
+  for (int p = g; p < nsplit; p += G1) s += __ldg(part + (long long)p * size + e);
+  mid[(long long)g * size + e] = s;
+}
+
+__global__ void k_split_reduce2(const float* mid, int groups, long long size, float* G) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < size; e += (long long)gridDim.x * blockDim.x) {
     float s = 0.0f;
-    for (int p = 0; p < nsplit; ++p) s += part[(long long)p * size + e];
+    for (int g = 0; g < groups; ++g) s += mid[(long long)g * size + e];
     G[e] = s;
   }
+}
+
+// SM count of the current device (looked up once per device index).
+int dev_sms() {
+  static int cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (cache[dev] <= 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      return 152;
+    }
+    cache[dev] = v;
+  }
+  return cache[dev];
 }
 
 struct TGramPlan {
   int tilesA, tilesB, nsplit;
   long long Ktot, kper;
-  size_t part_off, total;
+  size_t part_off, mid_off, total;
 };
 
 TGramPlan tgram_plan(const TTV& A, const TTV& B) {
@@ -299,14 +333,15 @@ TGramPlan tgram_plan(const TTV& A, const TTV& B) {
   p.tilesA = (A.batch + kTM - 1) / kTM;
   p.tilesB = (B.batch + kTM - 1) / kTM;
   const long long tiles = (long long)p.tilesA * p.tilesB;
-  long long ns = (152LL * 4 + tiles - 1) / tiles;       // about four CTAs per SM in all
+  long long ns = ((long long)dev_sms() * 4 + tiles - 1) / tiles;  // about four CTAs per SM in all
   ns = std::min(ns, (p.Ktot + 255) / 256);              // at least 256 coordinates per split
   ns = std::max(ns, 1LL);
   p.kper = (p.Ktot + ns - 1) / ns;
   p.kper = (p.kper + kKC - 1) / kKC * kKC;
   p.nsplit = (int)((p.Ktot + p.kper - 1) / p.kper);
   p.part_off = kWsHeader;
-  p.total = p.part_off + align256(sizeof(float) * (size_t)p.nsplit * A.batch * B.batch);
+  p.mid_off = p.part_off + align256(sizeof(float) * (size_t)p.nsplit * A.batch * B.batch);
+  p.total = p.mid_off + align256(sizeof(float) * (size_t)kReduceGroups * A.batch * B.batch);
   return p;
 }
 
@@ -554,6 +589,18 @@ ProjectLayout project_layout(const TTV& U, const TTV& Z) {
 
 }  // namespace
 
+t3f_status run_split_reduce(const float* part, int nsplit, long long size, float* mid, float* G, cudaStream_t s) {
+  const int G1 = std::min(nsplit, kReduceGroups);
+  const long long bx = (size + 255) / 256;
+  if (bx > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
+  k_split_reduce1<<<dim3((unsigned)bx, (unsigned)G1), 256, 0, s>>>(part, nsplit, size, mid);
+  T3F_CHECK(launch_status());
+  k_split_reduce2<<<(unsigned)std::min<long long>(std::max<long long>(bx, 1), 1024), 256, 0, s>>>(mid, G1, size, G);
+  return launch_status();
+}
+
+size_t ws_split_reduce(long long size) { return align256(sizeof(float) * (size_t)kReduceGroups * size); }
+
 size_t ws_project(const TTV& U, const TTV& Z) { return project_layout(U, Z).total; }
 size_t ws_tangent_gram(const TTV& A, const TTV& B) {
   return std::max(tgram_plan(A, B).total, ws_tangent_gram_tc(A, B));
@@ -639,9 +686,7 @@ extern "C" t3f_status t3f_tangent_gram(const t3f_tt* dA, const t3f_tt* dB, float
   k_tgram<<<(unsigned)grid, kThreads, 0, s>>>(g);
   T3F_CHECK(launch_status());
   const long long size = (long long)va.batch * vb.batch;
-  k_tgram_reduce<<<(unsigned)std::min<long long>(std::max<long long>((size + 255) / 256, 1), 1024), 256, 0, s>>>(
-      g.part, p.nsplit, size, G);
-  return launch_status();
+  return run_split_reduce(g.part, p.nsplit, size, reinterpret_cast<float*>(static_cast<char*>(ws) + p.mid_off), G, s);
 }
 
 extern "C" size_t t3f_project_matvec_workspace_size(const t3f_tt* U, const t3f_tt* A, const t3f_tt* x) {
@@ -735,19 +780,19 @@ extern "C" t3f_status t3f_completion_hvp(const t3f_tt* U, const t3f_tt* V, const
     g.err = static_cast<int*>(ws);
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)std::min<long long>((N + 127) / 128, (long long)sms * 8);
+    const int grid = (int)std::min<long long>((N + 255) / 256, (long long)sms * 4);
     switch (R) {
       case 4:
         cudaFuncSetAttribute(k_tangent_gather<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_tangent_gather<4><<<grid, 128, smem, s>>>(g);
+        k_tangent_gather<4><<<grid, 256, smem, s>>>(g);
         break;
       case 8:
         cudaFuncSetAttribute(k_tangent_gather<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_tangent_gather<8><<<grid, 128, smem, s>>>(g);
+        k_tangent_gather<8><<<grid, 256, smem, s>>>(g);
         break;
       default:
         cudaFuncSetAttribute(k_tangent_gather<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_tangent_gather<16><<<grid, 128, smem, s>>>(g);
+        k_tangent_gather<16><<<grid, 256, smem, s>>>(g);
         break;
     }
     T3F_CHECK(launch_status());

@@ -132,7 +132,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tgram_tc(const __grid_constan
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
 
-  if (tid == 0) {
+  // warp 0 lane 0: producer; warp 1 lane 0: MMA issuer. The other lanes of these two warps
+  // park at __syncwarp (not in a divergent spin beside the working lane).
+  if (warp == 0 && lane == 0) {
     // ---- producer: TMA loads into the stage ring
     const uint32_t bytes = one_operand ? kTileBytes : 2 * kTileBytes;
     bool ok = true;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tgram_tc(const __grid_constan
     });
     s_issued = issued;
     if (!ok) atomicExch(&s_bad, 1);
-  } else if (tid == 32) {
+  } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     bool ok = true;
     for_chunks(g, e0, e1, [&](int c, int, int) {
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tgram_tc(const __grid_constan
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(&accb))
                  : "memory");
   }
+  if (warp < 2) __syncwarp();
   // ---- epilogue: all four warps
   const bool acc_ok = mbar_wait(su32(&accb), 0u);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -228,14 +231,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tgram_tc(const __grid_constan
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-__global__ void k_tgram_tc_reduce(const float* part, int nsplit, long long size, float* G) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < size; e += (long long)gridDim.x * blockDim.x) {
-    float s = 0.0f;
-    for (int p = 0; p < nsplit; ++p) s += part[(long long)p * size + e];
-    G[e] = s;
-  }
-}
-
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
                               const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -272,10 +267,29 @@ bool encode_core(CUtensorMap* m, const TTV& v, int k) {
          CUDA_SUCCESS;
 }
 
+// SM count of the current device (looked up once per device index).
+int dev_sms() {
+  static int cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (cache[dev] <= 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      return 152;
+    }
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
 struct TcPlan {
   int tilesA, tilesB, nsplit;
   long long nchunks, cper;
-  size_t part_off, total;
+  size_t part_off, mid_off, total;
 };
 
 TcPlan tc_plan(const TTV& A, const TTV& B) {
@@ -285,13 +299,14 @@ TcPlan tc_plan(const TTV& A, const TTV& B) {
   p.tilesA = (A.batch + kTile - 1) / kTile;
   p.tilesB = (B.batch + kTile - 1) / kTile;
   const long long tiles = (long long)p.tilesA * p.tilesB;
-  long long ns = (152LL + tiles - 1) / tiles;       // one CTA per SM in all
+  long long ns = ((long long)dev_sms() + tiles - 1) / tiles;  // one CTA per SM in all
   ns = std::min(ns, (p.nchunks + 3) / 4);           // at least four chunks per split
   ns = std::max(ns, 1LL);
   p.cper = (p.nchunks + ns - 1) / ns;
   p.nsplit = (int)((p.nchunks + p.cper - 1) / p.cper);
   p.part_off = kWsHeader;
-  p.total = p.part_off + align256(sizeof(float) * (size_t)p.nsplit * A.batch * B.batch);
+  p.mid_off = p.part_off + align256(sizeof(float) * (size_t)p.nsplit * A.batch * B.batch);
+  p.total = p.mid_off + ws_split_reduce((long long)A.batch * B.batch);
   return p;
 }
 
@@ -305,13 +320,41 @@ t3f_status run_tangent_gram_tc(const TTV& A, const TTV& B, float* G, void* ws, s
   if (A.d > kMaxCoresTc) return T3F_ERR_UNSUPPORTED;
   const TcPlan p = tc_plan(A, B);
   T3F_CHECK(check_ws(ws, ws_bytes, p.total));
-  static TGramTcArgs g;  // large (8 KB of tensor maps): built on the host, passed by value
+  // Large (8 KB of tensor maps): built on the host and passed by value. The maps of the last
+  // pair of operands are kept, so a repeated call on the same buffers and shapes (the usual
+  // case in an iteration) encodes nothing.
+  static TGramTcArgs g;
+  static struct {
+    const void *pA, *pB;
+    int d, bA, bB, dev;
+    long long osz[kMaxCoresTc];
+    bool valid;
+  } key;
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
-  memset(&g, 0, sizeof(g));
-  for (int k = 0; k < A.d; ++k) {
-    if (!encode_core(&g.mapA[k], A, k) || !encode_core(&g.mapB[k], B, k)) return T3F_ERR_UNSUPPORTED;
-    g.ksz[k] = A.osz[k];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return T3F_ERR_CUDA;
+  }
+  bool same = key.valid && key.pA == A.p && key.pB == B.p && key.d == A.d && key.bA == A.batch && key.bB == B.batch &&
+              key.dev == dev;
+  for (int k = 0; same && k < A.d; ++k) same = key.osz[k] == A.osz[k];
+  if (!same) {
+    key.valid = false;
+    memset(&g, 0, sizeof(g));
+    for (int k = 0; k < A.d; ++k) {
+      if (!encode_core(&g.mapA[k], A, k) || !encode_core(&g.mapB[k], B, k)) return T3F_ERR_UNSUPPORTED;
+      g.ksz[k] = A.osz[k];
+      key.osz[k] = A.osz[k];
+    }
+    key.pA = A.p;
+    key.pB = B.p;
+    key.d = A.d;
+    key.bA = A.batch;
+    key.bB = B.batch;
+    key.dev = dev;
+    key.valid = true;
   }
   g.nchunks = p.nchunks;
   g.cper = p.cper;
@@ -330,10 +373,8 @@ t3f_status run_tangent_gram_tc(const TTV& A, const TTV& B, float* G, void* ws, s
   if (grid > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
   k_tgram_tc<<<(unsigned)grid, kTcThreads, kTcSmem, s>>>(g);
   T3F_CHECK(launch_status());
-  const long long size = (long long)A.batch * B.batch;
-  k_tgram_tc_reduce<<<(unsigned)std::min<long long>(std::max<long long>((size + 255) / 256, 1), 1024), 256, 0, s>>>(
-      g.part, p.nsplit, size, G);
-  return launch_status();
+  return run_split_reduce(g.part, p.nsplit, (long long)A.batch * B.batch,
+                          reinterpret_cast<float*>(static_cast<char*>(ws) + p.mid_off), G, s);
 }
 
 }  // namespace t3f

@@ -248,3 +248,30 @@ def test_gram_groups_config4_bf16_sampled(lib):
     G, nrm = lib.gram_groups(X, gstart, ws, math="bf16")
     _config4_sampled_check(G.cpu().numpy(), objs, gstart, np.random.default_rng(406), TOL["bf16"])
     assert rel_err(nrm.cpu().numpy()[[0, 100, 511]], [O.norm(objs[i]) for i in (0, 100, 511)]) < TOL["bf16"]
+
+
+def test_gram_groups_config4_bf16_backward_sampled(lib):
+    # the uneven adjoint on BF16-stored cores (FP32 arithmetic): sampled objects of every group
+    # against the oracle's cotangent on the same BF16-rounded cores
+    cfg = S.config4()
+    objs, gstart = [], [0]
+    for grp in cfg.groups:
+        objs += [round_bf16(o) for o in grp.cores]
+        gstart.append(len(objs))
+    X = lib.RaggedTT.from_objects([[torch.tensor(np.asarray(c)) for c in o] for o in objs], dtype=torch.bfloat16)
+    ws = lib.gram_groups_prepare(X, gstart)
+    G, _ = lib.gram_groups(X, gstart, ws)
+    rng = np.random.default_rng(407)
+    dout = rng.normal(size=G.numel()).astype(np.float32)
+    dX = lib.gram_groups_backward(X, gstart, ws, torch.tensor(dout, device="cuda"))
+    view = lib.RaggedTT(dX, X.dims, X.modes, X.ranks, X.offsets)
+    off = 0
+    for g in range(len(gstart) - 1):
+        grp = objs[gstart[g]:gstart[g + 1]]
+        Sg = len(grp)
+        dG = dout[off:off + Sg * Sg].reshape(Sg, Sg).astype(np.float64)
+        off += Sg * Sg
+        a = int(rng.integers(0, Sg))
+        dA, _ = O.gram_vjp([grp[a]], grp, (dG[a, :] + dG[:, a])[None, :])
+        got = [c.double().cpu().numpy() for c in view.object_cores(gstart[g] + a)]
+        assert rel_err_cores(got, dA[0]) < TOL["bf16"], (g, a)

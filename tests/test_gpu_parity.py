@@ -392,12 +392,40 @@ def test_project_sum_fwd_bwd_shapes(lib, shape):
     assert rel_err(dc.cpu().numpy(), rc) < TOL["fp32"]
 
 
-def test_project_sum_reduced_precision_modes_below_threshold(lib):
-    # Z rank 2 < 16: the TF32 / BF16 modes run the FP32 sweeps and agree with FP32 exactly
+def test_project_sum_tf32_config5_full(lib):
+    # the U- and V-side contractions of both sweeps on the tensor cores (TF32), at config 5
+    cfg = S.config5()
+    X, Z = round32(cfg.X), round32(cfg.Z)
+    c = cfg.c.astype(np.float32)
+    U, V = _orth(lib, X, torch.float32)
+    Zt, ct = dev_tt(lib, Z), torch.tensor(c, device="cuda")
+    dU = lib.project_sum(U, V, Zt, ct, math="tf32")
+    Uo, Vo, _ = O.orthogonalize(objects(X)[0])
+    ref = O.project_sum(Uo, Vo, objects(Z), c.astype(np.float64))
+    err = rel_err_cores(host_objects(dU)[0], ref)
+    assert err < TOL["tf32"]
+    assert err > 1e-7  # the reduced-precision path really ran
+
+
+def test_project_sum_tf32_ragged_batch(lib):
+    # 37 objects (the last CTA holds 5), X ranks 1..12, Z ranks 5, modes 8
+    cfg = S.config5(batch=37, d=6, n=8, rX=12, rZ=5)
+    X, Z = round32(cfg.X), round32(cfg.Z)
+    c = cfg.c.astype(np.float32)
+    U, V = _orth(lib, X, torch.float32)
+    dU = lib.project_sum(U, V, dev_tt(lib, Z), torch.tensor(c, device="cuda"), math="tf32")
+    Uo, Vo, _ = O.orthogonalize(objects(X)[0])
+    ref = O.project_sum(Uo, Vo, objects(Z), c.astype(np.float64))
+    assert rel_err_cores(host_objects(dU)[0], ref) < TOL["tf32"]
+
+
+def test_project_sum_reduced_precision_limits(lib):
+    # modes that are not multiples of 8 have no tensor-core form, nor has BF16: both refused
     cfg = S.config1()
     X, Z = round32(cfg.X), round32(cfg.B)
     U, V = _orth(lib, X, torch.float32)
     Zt, c = dev_tt(lib, Z), torch.tensor(cfg.c.astype(np.float32), device="cuda")
-    ref = lib.project_sum(U, V, Zt, c).data
     for m in ("tf32", "bf16"):
-        assert torch.equal(lib.project_sum(U, V, Zt, c, math=m).data, ref)
+        with pytest.raises(lib.T3FError) as e:
+            lib.project_sum(U, V, Zt, c, math=m)
+        assert e.value.status == -7
