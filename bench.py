@@ -371,6 +371,38 @@ def combine_ranks(dev_ms, e2e_ms, world, step_flops, device):
             world * step_flops / (e2e_ms * 1e-3) / 1e9)
 
 
+def op_graph_times(w, flush, stream):
+    """Device time of every operation of the step on its own: each one (with the inputs the
+    step gives it) captured as a CUDA graph and timed by replay with L2 flushed before every
+    replay, so operations shorter than their host-side call are timed on the device. The
+    uneven batch is already a graph and is replayed as it stands."""
+    t3f, torch = w.t3f, w.torch
+    X2, idx, y = w.tt("X2"), w.devbuf["idx"], w.devbuf["y"]
+    U2, V2 = t3f.orthogonalize(X2)
+    X5, Z5, c5 = w.tt("X5"), w.tt("Z5"), w.devbuf["c5"]
+    U5, V5 = t3f.orthogonalize(X5)
+    dU5 = t3f.project_sum(U5, V5, Z5, c5)
+    A3, B3, dG = w.tt("A3"), w.tt("B3"), w.devbuf["dG"]
+    Am, xv, dC = w.tt("Am"), w.tt("xv"), w.tt("dC")
+    fns = {
+        "completion": lambda: t3f.gather_backward(X2, idx, y=y, want_loss=True),
+        "orth2": lambda: t3f.orthogonalize(X2),
+        "rgrad": lambda: t3f.gather_backward(None, idx, y=y, riemannian=True, U=U2, V=V2),
+        "orth5": lambda: t3f.orthogonalize(X5),
+        "psum": lambda: t3f.project_sum(U5, V5, Z5, c5),
+        "psum_bwd": lambda: t3f.project_sum_backward(U5, V5, Z5, c5, dU5),
+        "gram": lambda: t3f.gram(A3, B3),
+        "gram_bwd": lambda: t3f.gram_backward(A3, B3, dG),
+        "norm": lambda: t3f.norm(A3),
+        "matvec": lambda: t3f.matvec(Am, xv),
+        "matvec_bwd": lambda: t3f.matvec_backward(Am, xv, dC),
+    }
+    out = {k: graph_time(torch, f, flush, stream, reps=5) for k, f in fns.items()}
+    for key, g in (("uneven", w.graph4f), ("uneven_bwd", w.graph4b)):
+        out[key] = event_time(torch, g.replay, flush, stream)
+    return out
+
+
 def run_step(w, timers=None, stream=None, side=None, ready=None):
     """All hot-path operations once; returns the outputs a user reads back.
 
@@ -559,6 +591,35 @@ def event_time(torch, fn, flush, stream, reps=5):
     return tot / reps
 
 
+def graph_time(torch, fn, flush, stream, reps=10):
+    """Mean CUDA-event time (ms) of one replay of fn captured as a CUDA graph, L2 flushed
+    (untimed) before each replay: the device time of operations whose host-side call would
+    otherwise be longer than their kernels."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    del g
+    return tot / reps
+
+
 def measured_fp64_peak(t3f, torch, dev):
     """FP64 FMA rate of this GPU from the library's FP64 probe (same shape as the FP32 one)."""
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -602,7 +663,8 @@ def measured_fp32_peak(t3f, torch, dev, gpu_index):
 
 
 def next_rows(w, flush, stream, fp32_peak, fp64_peak=None):
-    """The tangent-space rows beyond the step (Section 3.2), each timed on its own:
+    """The tangent-space rows beyond the step (Section 3.2), each timed on its own (CUDA-graph
+    replay, L2 flushed before each):
     batched projection of 100 config-5 TTs + the Gram matrix of their tangent vectors (FP32
     CUDA cores and TF32 tensor cores via TMA), the projected matvec P_X(A x_j) at config-3b
     shapes, and the completion loss's linearised Riemannian Hessian applied to its Riemannian
@@ -625,14 +687,14 @@ def next_rows(w, flush, stream, fp32_peak, fp64_peak=None):
         if extra:
             out[name].update(extra)
 
-    ms = event_time(torch, lambda: t3f.project(U5, V5, Z, c100), flush, stream)
+    ms = graph_time(torch, lambda: t3f.project(U5, V5, Z, c100), flush, stream)
     row("project_batch", ms, f_project_batch([16] * 20, ru5, rz5, 100))
     dU = t3f.project(U5, V5, Z, c100)
     K = dU.data.numel() // 100
     gflop = 2 * 100 * 100 * K
-    ms = event_time(torch, lambda: t3f.tangent_gram(dU, dU), flush, stream)
+    ms = graph_time(torch, lambda: t3f.tangent_gram(dU, dU), flush, stream)
     row("tangent_gram_fp32", ms, gflop)
-    ms = event_time(torch, lambda: t3f.tangent_gram(dU, dU, math="tf32"), flush, stream)
+    ms = graph_time(torch, lambda: t3f.tangent_gram(dU, dU, math="tf32"), flush, stream)
     G32 = t3f.tangent_gram(dU, dU).double()
     Gtf = t3f.tangent_gram(dU, dU, math="tf32").double()
     nbytes = dU.data.numel() * 4
@@ -649,14 +711,14 @@ def next_rows(w, flush, stream, fp32_peak, fp64_peak=None):
     Xp = t3f.TT(w.next_dev["Xp"], [4] * 10, S.tt_ranks(10, 10), 1)
     Up, Vp = t3f.orthogonalize(Xp)
     rxp = t3f.orth_ranks([4] * 10, S.tt_ranks(10, 10))
-    ms = event_time(torch, lambda: t3f.project_matvec(Up, Vp, A1, xv), flush, stream)
+    ms = graph_time(torch, lambda: t3f.project_matvec(Up, Vp, A1, xv), flush, stream)
     row("project_matvec", ms, f_project_matvec([4] * 10, [4] * 10, rxp, S.tt_ranks(10, 10), S.tt_ranks(10, 10), 100))
     # linearised Riemannian Hessian of the completion loss along its Riemannian gradient
     X2 = w.tt("X2")
     U2, V2 = t3f.orthogonalize(X2)
     idx, y = w.devbuf["idx"], w.devbuf["y"]
     g2, _ = t3f.gather_backward(None, idx, y=y, riemannian=True, U=U2, V=V2)
-    ms = event_time(torch, lambda: t3f.completion_hvp(U2, V2, idx, g2), flush, stream)
+    ms = graph_time(torch, lambda: t3f.completion_hvp(U2, V2, idx, g2), flush, stream)
     ru2 = t3f.orth_ranks([10] * 10, S.tt_ranks(10, 8))
     row("completion_hvp", ms, f_hvp(ru2, [10] * 10, idx.shape[1]))
     # TT rounding (FP64 TT-SVD) of the 100 rank-100 matvec products of config 3b to rank 10
@@ -1063,9 +1125,7 @@ def gpu_arm(args):
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     dev_ms = sum(step_ms) / args.steps
 
-    # per-operation device times: the same K steps with every operation in order on one
-    # stream (no overlap), each operation bracketed by events
-    timers = {}
+    # the same K steps with every operation in order on one stream (no overlap)
     seq_ev = []
     torch.cuda.synchronize(dev)
     for _ in range(args.steps):
@@ -1073,12 +1133,13 @@ def gpu_arm(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        run_step(w, timers, stream)
+        run_step(w, None, stream)
         e1.record(stream)
         seq_ev.append((e0, e1))
     torch.cuda.synchronize(dev)
     seq_ms = sum(a.elapsed_time(b) for a, b in seq_ev) / args.steps
-    op_ms = {k: sum(a.elapsed_time(b) for a, b in v) / args.steps for k, v in timers.items()}
+    # per-operation device times (each operation replayed as its own CUDA graph)
+    op_ms = op_graph_times(w, flush, stream)
 
     # end-to-end: pinned host inputs copied in, results read back, every step
     d2h = 0

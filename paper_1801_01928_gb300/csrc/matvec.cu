@@ -6,6 +6,8 @@
 // One CTA per (pair, core): both cores are staged in shared memory and the product core is
 // streamed out row by row; for a fixed output row (a, b) the (i, a', b') block is
 // contiguous, so consecutive threads write consecutive addresses.
+#include <algorithm>
+
 #include "t3f_internal.cuh"
 
 namespace t3f {
@@ -16,7 +18,12 @@ struct MatvecArgs {
   TTV A, x, C;
   int bA, bx, P;       // batches; P = number of products
   int maxA, maxX;      // staged floats per core (max over k)
+  // specialised kernels: CTA units (pair, core k, rows a in [u * kMvRows, ...)); units of core
+  // k are ucum[k] .. ucum[k + 1] - 1 within a pair
+  int ucum[T3F_MAX_D + 1];
 };
+
+constexpr int kMvRows = 5;  // rows a of A's left rank per CTA of the specialised kernels
 
 __global__ void __launch_bounds__(256) k_matvec(const __grid_constant__ MatvecArgs a) {
   extern __shared__ float sm[];
@@ -74,7 +81,11 @@ __global__ void __launch_bounds__(256) k_matvec(const __grid_constant__ MatvecAr
 template <int N, int RB>
 __global__ void __launch_bounds__(256) k_matvec_n(const __grid_constant__ MatvecArgs a) {
   extern __shared__ float sm[];
-  const int p = blockIdx.x / a.A.d, k = blockIdx.x % a.A.d;
+  const int per = a.ucum[a.A.d];
+  const int p = blockIdx.x / per, u = blockIdx.x % per;
+  int k = 0;
+  while (u >= a.ucum[k + 1]) ++k;
+  const int al0 = (u - a.ucum[k]) * kMvRows;
   const TTV& A = a.A;
   const TTV& X = a.x;
   const int ra0 = A.r[k], ra1 = A.r[k + 1], rx0 = X.r[k], rx1 = X.r[k + 1];
@@ -99,7 +110,8 @@ __global__ void __launch_bounds__(256) k_matvec_n(const __grid_constant__ Matvec
       for (int j = 0; j < N; ++j) xr[be][j] = be < rx0 ? Xs[(be * N + j) * rx1 + bp] : 0.0f;
     const float* Ar = As + (i * N) * ra1 + ap;  // A[al, i, j, ap] at al * m * N * ra1 + j * ra1
     float* cq = Cp + q;
-    for (int al = 0; al < ra0; ++al) {
+    const int al1 = min(ra0, al0 + kMvRows);
+    for (int al = al0; al < al1; ++al) {
       float av[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) av[j] = Ar[(al * m * N + j) * ra1];
@@ -190,6 +202,163 @@ __global__ void __launch_bounds__(256) k_matvec_bwd(const __grid_constant__ Matv
   }
 }
 
+// Adjoint for column modes n = N (2, 4, 8): one CTA per (pair, core). The dC row blocks a
+// (rows (a, b), b < r_x: contiguous) are staged by 16-byte asynchronous copies into two
+// buffers, one block ahead of the products; A and x are staged with j innermost
+// (At[a][i][a'][j], xt[b][b'][j]) so that every K step of the two products reads its N
+// values of j with one vector load:
+//   dx[b, j, b'] += sum_{i, a'} G[b][i][a'][b'] At[a][i][a'][j]   thread per (b, b'), kept in
+//                                                                 registers across all a
+//   dA[a, i, j, a'] = sum_{b, b'} G[b][i][a'][b'] xt[b][b'][j]    thread per (i, a') and part of
+//                                                                 the b range, parts summed
+//                                                                 in shared memory
+template <int N>
+__global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ MatvecBwdArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const int p = blockIdx.x / a.A.d, k = blockIdx.x % a.A.d;
+  const TTV& A = a.A;
+  const TTV& X = a.x;
+  const int ra0 = A.r[k], ra1 = A.r[k + 1], rx0 = X.r[k], rx1 = X.r[k + 1];
+  const int m = A.m[k];
+  const int tid = threadIdx.x;
+  float* At = sm;                      // [ra0][m][ra1][N]
+  float* Xt = At + a.maxA;             // [rx0][rx1][N]
+  float* Gb = Xt + a.maxX;             // [2][maxRow]
+  float* Red = Gb + 2 * a.maxRow;      // dA partial sums [parts][m * ra1][N]
+  const int oa = a.bA == 1 ? 0 : p, ox = a.bx == 1 ? 0 : p;
+  const float* Ap = static_cast<const float*>(A.p) + core_base(A, k, oa);
+  const float* Xp = static_cast<const float*>(X.p) + core_base(X, k, ox);
+  const float* Gp = static_cast<const float*>(a.dC.p) + core_base(a.dC, k, p);
+  const int sa = ra0 * m * N * ra1, sx = rx0 * N * rx1;
+  for (int e = tid; e < sa; e += blockDim.x) {  // A[al][i][j][ap] -> At[al][i][ap][j]
+    const int ap = e % ra1, j = (e / ra1) % N, ali = e / (ra1 * N);
+    At[(ali * ra1 + ap) * N + j] = __ldg(Ap + e);
+  }
+  for (int e = tid; e < sx; e += blockDim.x) {  // x[b][j][bp] -> Xt[b][bp][j]
+    const int bp = e % rx1, j = (e / rx1) % N, b = e / (rx1 * N);
+    Xt[(b * rx1 + bp) * N + j] = __ldg(Xp + e);
+  }
+  const int rowlen = m * ra1 * rx1;
+  const int blk = rx0 * rowlen;
+  const bool vec = ((reinterpret_cast<uintptr_t>(Gp) & 15) == 0) && (blk & 3) == 0;
+  auto stage = [&](int al) {
+    float* dst = Gb + (al & 1) * a.maxRow;
+    const float* src = Gp + (long long)al * blk;
+    if (vec) {
+      for (int e4 = tid; e4 < blk / 4; e4 += blockDim.x) {
+        const unsigned sa_ = (unsigned)__cvta_generic_to_shared(dst + 4 * e4);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa_), "l"(src + 4 * e4));
+      }
+    } else {
+      for (int e = tid; e < blk; e += blockDim.x) {
+        const unsigned sa_ = (unsigned)__cvta_generic_to_shared(dst + e);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa_), "l"(src + e));
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  // dx: thread per (b, bp) with N accumulators
+  const int nbb = rx0 * rx1;
+  float dxa[2][N];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int j = 0; j < N; ++j) dxa[u][j] = 0.0f;
+  // dA: items (i, ap) x parts of the b range
+  const int nia = m * ra1;
+  const int parts = max(1, min(rx0, (int)blockDim.x / max(nia, 1)));
+  stage(0);
+  for (int al = 0; al < ra0; ++al) {
+    if (al + 1 < ra0) {
+      stage(al + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::);
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::);
+    }
+    __syncthreads();
+    const float* G = Gb + (al & 1) * a.maxRow;  // [b][i][ap][bp]
+    if (a.dx) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = tid + u * (int)blockDim.x;
+        if (e < nbb) {
+          const int b = e / rx1, bp = e % rx1;
+          const float* g = G + (long long)b * rowlen + bp;
+          const float* at = At + (long long)al * m * ra1 * N;
+          for (int q = 0; q < nia; ++q) {  // q = i * ra1 + ap
+            const float gv = g[q * rx1];
+            if constexpr (N == 4) {
+              const float4 v = *reinterpret_cast<const float4*>(at + q * 4);
+              dxa[u][0] = fmaf(gv, v.x, dxa[u][0]);
+              dxa[u][1] = fmaf(gv, v.y, dxa[u][1]);
+              dxa[u][2] = fmaf(gv, v.z, dxa[u][2]);
+              dxa[u][3] = fmaf(gv, v.w, dxa[u][3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < N; ++j) dxa[u][j] = fmaf(gv, at[q * N + j], dxa[u][j]);
+            }
+          }
+        }
+      }
+    }
+    if (a.dA) {
+      const int it = tid % max(nia, 1), part = tid / max(nia, 1);
+      float acc[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc[j] = 0.0f;
+      if (part < parts && it < nia) {
+        const int b0 = part * rx0 / parts, b1 = (part + 1) * rx0 / parts;
+        for (int b = b0; b < b1; ++b) {
+          const float* g = G + (long long)b * rowlen + it * rx1;
+          const float* xt = Xt + (long long)b * rx1 * N;
+          for (int bp = 0; bp < rx1; ++bp) {
+            const float gv = g[bp];
+            if constexpr (N == 4) {
+              const float4 v = *reinterpret_cast<const float4*>(xt + bp * 4);
+              acc[0] = fmaf(gv, v.x, acc[0]);
+              acc[1] = fmaf(gv, v.y, acc[1]);
+              acc[2] = fmaf(gv, v.z, acc[2]);
+              acc[3] = fmaf(gv, v.w, acc[3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < N; ++j) acc[j] = fmaf(gv, xt[bp * N + j], acc[j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) Red[(part * nia + it) * N + j] = acc[j];
+      }
+      __syncthreads();
+      // dA[al, i, j, ap] from the parts
+      float* dAp = a.dA + core_base(A, k, oa);
+      for (int e = tid; e < nia * N; e += blockDim.x) {
+        const int ap = e % ra1, j = (e / ra1) % N, i = e / (ra1 * N);
+        const int q = i * ra1 + ap;
+        float s = 0.0f;
+        for (int pp = 0; pp < parts; ++pp) s += Red[(pp * nia + q) * N + j];
+        float* dst = dAp + ((al * m + i) * N + j) * ra1 + ap;
+        if (a.atomicA) atomicAdd(dst, s); else *dst = s;
+      }
+    }
+    __syncthreads();  // this buffer is restaged two blocks later
+  }
+  if (a.dx) {
+    float* dXp = a.dx + core_base(X, k, ox);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * (int)blockDim.x;
+      if (e < nbb) {
+        const int b = e / rx1, bp = e % rx1;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          float* dst = dXp + (b * N + j) * rx1 + bp;
+          if (a.atomicX) atomicAdd(dst, dxa[u][j]); else *dst = dxa[u][j];
+        }
+      }
+    }
+  }
+}
+
 static t3f_status matvec_views(const t3f_tt* A, const t3f_tt* x, TTV* va, TTV* vx, int* P) {
   T3F_CHECK(make_view(A, va, T3F_F32, true));
   T3F_CHECK(make_view(x, vx, T3F_F32, false));
@@ -242,24 +411,42 @@ extern "C" t3f_status t3f_matvec(const t3f_tt* A, const t3f_tt* x, t3f_tt* C, vo
   const long long grid = (long long)P * va.d;
   if (grid > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
-  // the specialised kernels need one column mode for every core and r_x <= 16 on the left
+  // the specialised kernels need one column mode for every core and r_x <= 16 on the left;
+  // their CTAs take kMvRows rows a of one core each, so the boundary cores (left rank 1) do
+  // not leave most of the grid with a tenth of the work
   int nall = va.n[0], rxmax = 0;
+  args.ucum[0] = 0;
   for (int k = 0; k < va.d; ++k) {
     if (va.n[k] != nall) nall = -1;
     if (vx.r[k] > rxmax) rxmax = vx.r[k];
+    args.ucum[k + 1] = args.ucum[k] + (va.r[k] + kMvRows - 1) / kMvRows;
   }
-  auto run = [&](auto kern) -> t3f_status {
+  const long long ugrid = (long long)P * args.ucum[va.d];
+  auto run = [&](auto kern, long long g) -> t3f_status {
+    if (g > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
-    kern<<<(unsigned)grid, 256, smem, s>>>(args);
+    kern<<<(unsigned)g, 256, smem, s>>>(args);
     return launch_status();
   };
-  if (rxmax <= 16) {
-    if (nall == 2) return run(k_matvec_n<2, 16>);
-    if (nall == 4) return run(k_matvec_n<4, 16>);
-    if (nall == 8) return run(k_matvec_n<8, 16>);
+  if (rxmax <= 16 && (nall == 2 || nall == 4 || nall == 8)) {
+    const int RB = rxmax <= 4 ? 4 : (rxmax <= 8 ? 8 : (rxmax <= 12 ? 12 : 16));
+    switch (nall * 100 + RB) {
+      case 204: return run(k_matvec_n<2, 4>, ugrid);
+      case 208: return run(k_matvec_n<2, 8>, ugrid);
+      case 212: return run(k_matvec_n<2, 12>, ugrid);
+      case 216: return run(k_matvec_n<2, 16>, ugrid);
+      case 404: return run(k_matvec_n<4, 4>, ugrid);
+      case 408: return run(k_matvec_n<4, 8>, ugrid);
+      case 412: return run(k_matvec_n<4, 12>, ugrid);
+      case 416: return run(k_matvec_n<4, 16>, ugrid);
+      case 804: return run(k_matvec_n<8, 4>, ugrid);
+      case 808: return run(k_matvec_n<8, 8>, ugrid);
+      case 812: return run(k_matvec_n<8, 12>, ugrid);
+      default: return run(k_matvec_n<8, 16>, ugrid);
+    }
   }
-  return run(k_matvec);
+  return run(k_matvec, grid);
 }
 
 extern "C" t3f_status t3f_matvec_backward(const t3f_tt* A, const t3f_tt* x, const t3f_tt* dC,
@@ -305,11 +492,40 @@ extern "C" t3f_status t3f_matvec_backward(const t3f_tt* A, const t3f_tt* x, cons
   }
   const size_t smem = sizeof(float) * ((size_t)args.maxA + 2 * (size_t)args.maxX + args.maxRow);
   if (smem > 200 * 1024) return T3F_ERR_UNSUPPORTED;
+  // the specialised adjoint: one column mode for every core, at most 512 (b, b') pairs and
+  // 256 (i, a') items per core
+  int nall = va.n[0];
+  bool spec = true;
+  int maxIA = 0;
+  for (int k = 0; k < va.d; ++k) {
+    if (va.n[k] != nall) nall = -1;
+    if (vx.r[k] * vx.r[k + 1] > 512) spec = false;
+    maxIA = std::max(maxIA, va.m[k] * va.r[k + 1]);
+  }
+  if (maxIA > 256) spec = false;
   if (args.atomicA && cudaMemsetAsync(args.dA, 0, sizeof(float) * t3f_packed_size(dA), s) != cudaSuccess)
     return T3F_ERR_CUDA;
   if (args.atomicX && cudaMemsetAsync(args.dx, 0, sizeof(float) * t3f_packed_size(dx), s) != cudaSuccess)
     return T3F_ERR_CUDA;
   const long long grid = (long long)P * va.d;
+  if (spec && (nall == 2 || nall == 4 || nall == 8)) {
+    MatvecBwdArgs b2 = args;
+    b2.maxA = (args.maxA + 3) & ~3;
+    b2.maxX = (args.maxX + 3) & ~3;
+    b2.maxRow = (args.maxRow + 3) & ~3;
+    const size_t sm2 = sizeof(float) * ((size_t)b2.maxA + b2.maxX + 2 * (size_t)b2.maxRow + 256 * 8);
+    if (sm2 <= 200 * 1024) {
+      auto go = [&](auto kern) -> t3f_status {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2) != cudaSuccess)
+          return T3F_ERR_CUDA;
+        kern<<<(unsigned)grid, 256, sm2, s>>>(b2);
+        return launch_status();
+      };
+      if (nall == 2) return go(k_matvec_bwd_n<2>);
+      if (nall == 4) return go(k_matvec_bwd_n<4>);
+      return go(k_matvec_bwd_n<8>);
+    }
+  }
   if (cudaFuncSetAttribute(k_matvec_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return T3F_ERR_CUDA;
   k_matvec_bwd<<<(unsigned)grid, 256, smem, s>>>(args);

@@ -437,16 +437,17 @@ extern "C" t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3
   if (math == T3F_MATH_TF32) {
     int* err = static_cast<int*>(ws);
     if (cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
-    T3F_CHECK(run_psweep_tc(vu, vz, 0, Lst, l.ioffL, err, s));
-    T3F_CHECK(run_psweep_tc(vv, vz, 1, Rst, l.ioffR, err, s));
+    T3F_CHECK(run_psweep_tc(vu, vv, vz, Lst, l.ioffL, Rst, l.ioffR, err, s));
     T3F_CHECK(run_passemble(vu, vz, Lst, Rst, l.ioffL, c, part, l.nchunks, s));
     k_reduce_chunks<<<256, 256, 0, s>>>(part, l.nchunks, l.gsize, part);
     T3F_CHECK(launch_status());
     return run_gauge_project(vu, part, static_cast<float*>(vd.p), s);
   }
   if (psweep_supported(vu, vz)) {
-    T3F_CHECK(run_psweep(vu, vz, 0, static_cast<const float*>(vu.p), nullptr, nullptr, Lst, nullptr, l.ioffL, s));
-    T3F_CHECK(run_psweep(vv, vz, 1, static_cast<const float*>(vv.p), nullptr, nullptr, Rst, nullptr, l.ioffR, s));
+    int* err = static_cast<int*>(ws);
+    if (cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
+    T3F_CHECK(run_psweep(vu, vz, 0, static_cast<const float*>(vu.p), nullptr, nullptr, Lst, nullptr, l.ioffL, s, err));
+    T3F_CHECK(run_psweep(vv, vz, 1, static_cast<const float*>(vv.p), nullptr, nullptr, Rst, nullptr, l.ioffR, s, err));
     T3F_CHECK(run_passemble(vu, vz, Lst, Rst, l.ioffL, c, part, l.nchunks, s));
     k_reduce_chunks<<<256, 256, 0, s>>>(part, l.nchunks, l.gsize, part);
     T3F_CHECK(launch_status());
@@ -507,8 +508,10 @@ extern "C" t3f_status t3f_project_sum_backward(const t3f_tt* U, const t3f_tt* V,
   if (psweep_supported(vu, vz)) {
     const float* Up = static_cast<const float*>(vu.p);
     const float* Vp = static_cast<const float*>(vv.p);
-    T3F_CHECK(run_psweep(vu, vz, 0, Up, Vp, Wc, Lst, Pst, l.ioffL, s));
-    T3F_CHECK(run_psweep(vu, vz, 1, Vp, Up, Wc, Rst, Qst, l.ioffL, s));
+    int* err = static_cast<int*>(ws);
+    if (cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
+    T3F_CHECK(run_psweep(vu, vz, 0, Up, Vp, Wc, Lst, Pst, l.ioffL, s, err));
+    T3F_CHECK(run_psweep(vu, vz, 1, Vp, Up, Wc, Rst, Qst, l.ioffL, s, err));
     return run_pgrad(vu, vz, Up, Vp, Wc, Lst, Rst, Pst, Qst, l.ioffL, c, dZ ? static_cast<float*>(vdz.p) : nullptr,
                      dc, s);
   }

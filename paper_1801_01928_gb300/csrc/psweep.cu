@@ -33,6 +33,7 @@ struct PSweepArgs {
   float* st2;
   long long ioff[T3F_MAX_D + 1];
   int J, SPLIT;
+  int* err;  // device error word (nullable): a bounded wait that ran out
 };
 
 __device__ __forceinline__ void fma4x4(float (&acc)[4][4], const float4 a, const float4 b) {
@@ -72,6 +73,20 @@ __device__ __forceinline__ void stage_x_slice_async(float* dst, const float* cor
   }
 }
 
+__device__ __forceinline__ bool ps_bar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;  // about one second
+  }
+}
+
 template <int RU, bool MIXED>
 __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepArgs a) {
   extern __shared__ __align__(16) float sm[];
@@ -94,6 +109,16 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
   float* T1 = C2 + (MIXED ? (size_t)J * TS : 0);   // [J][SP][RU][8]
   float* T2 = T1 + (size_t)J * SP * TS;            // mixed only
   const float* Zp = static_cast<const float*>(Z.p);
+  // Z cores whose staged layout [K][i][b] equals their stored one (left sweep, ranks 8 x 8,
+  // n_k = nmax, 16-byte aligned blocks) land by one TMA bulk copy per object; the others (and
+  // the right sweep, which transposes) keep the zero-filling 4-byte copies
+  __shared__ __align__(8) uint64_t zbar;
+  uint32_t zph = 0;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((unsigned)__cvta_generic_to_shared(&zbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
 
   // initial partials: 1 (and 0) at the starting interface
   for (int e = tid; e < J * TS; e += blockDim.x) {
@@ -133,7 +158,24 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
     // with 4-byte asynchronous copies (zero-filled outside the ranks), one commit group that
     // the first batch's wait covers; e = ((o * 8 + K) * n + i) * 8 + b, the quotient by n taken
     // through an exact 32-bit reciprocal (indices < 2^13)
-    {
+    const bool zbulk = a.dir == 0 && z0 == kRZ && z1 == kRZ && n == nmax && (Z.off[k] & 3) == 0 &&
+                       (Z.osz[k] & 3) == 0 && (reinterpret_cast<uintptr_t>(Zp) & 15) == 0;
+    if (zbulk) {
+      if (tid == 0) {
+        const int nv = min(J, Z.batch - blockIdx.x * J);
+        const uint32_t bytes = (uint32_t)Z.osz[k] * 4u;
+        const unsigned zb = (unsigned)__cvta_generic_to_shared(&zbar);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(zb), "r"(bytes * (uint32_t)nv)
+                     : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int o = 0; o < nv; ++o)
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           (unsigned)__cvta_generic_to_shared(Zc + (size_t)o * kRZ * nmax * kRZ)),
+                       "l"(Zp + core_base(Z, k, blockIdx.x * J + o)), "r"(bytes), "r"(zb)
+                       : "memory");
+      }
+      asm volatile("cp.async.commit_group;\n" ::);  // an empty group keeps the group count
+    } else {
       const unsigned mn = 0xffffffffu / (unsigned)n + 1u;
       for (int e = tid; e < J * kRZ * n * kRZ; e += blockDim.x) {
         const unsigned x = (unsigned)e >> 3, q = n == 1 ? x : __umulhi(x, mn);
@@ -168,6 +210,11 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
         }
       }
       __syncthreads();
+      if (ib == 0 && zbulk) {
+        if (!ps_bar_wait((unsigned)__cvta_generic_to_shared(&zbar), zph) && tid == 0 && a.err)
+          atomicExch(a.err, (int)T3F_ERR_TIMEOUT);
+        zph ^= 1u;
+      }
       float* const XsB = Xs + (size_t)(bt & 1) * NX * SP * RU * RU;
       const int i = ib * SP + h;
       // T-step: T[m][b] = sum_K CurT[K][m] Zs[K][b]
@@ -562,9 +609,10 @@ static t3f_status launch_psweep_t(PSweepArgs& a, cudaStream_t s) {
 
 // dir 0: left sweep (A = U [, B1 = V, B2 = W]); dir 1: right sweep (A = V [, B1 = U, B2 = W]).
 t3f_status run_psweep(const TTV& X, const TTV& Z, int dir, const float* A, const float* B1, const float* B2,
-                      float* st1, float* st2, const long long* ioff, cudaStream_t s) {
+                      float* st1, float* st2, const long long* ioff, cudaStream_t s, int* err) {
   PSweepArgs a;
   memset(&a, 0, sizeof(a));
+  a.err = err;
   a.Z = Z;
   a.A = A;
   a.B1 = B1;

@@ -45,12 +45,12 @@ constexpr uint32_t kPtTmemCols = 32;
 
 struct PtArgs {
   TTV Z;
-  const float* X;                // U (left) or V (right) cores, packed, batch 1
-  long long Xoff[T3F_MAX_D];
+  const float* X[2];             // U (left sweep) and V (right sweep) cores, packed, batch 1
+  long long Xoff[T3F_MAX_D];     // shared by U and V (equal shapes)
   int rx[T3F_MAX_D + 1];
-  int dir;
-  float* st;                     // partial store
-  long long ioff[T3F_MAX_D + 1];
+  float* st[2];                  // partial stores of the two sweeps
+  long long ioff[2][T3F_MAX_D + 1];
+  int nblk;                      // CTAs per direction; blocks [nblk, 2 nblk) run the right sweep
   int* err;
 };
 
@@ -100,7 +100,11 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
   __shared__ int s_bad;
   const TTV& Z = a.Z;
   const int d = Z.d, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int obj0 = blockIdx.x * kPtObj;
+  const int dir = (int)blockIdx.x >= a.nblk ? 1 : 0;
+  const int obj0 = ((int)blockIdx.x - dir * a.nblk) * kPtObj;
+  const float* Xbase = a.X[dir];
+  float* st = a.st[dir];
+  const long long* ioff = a.ioff[dir];
   const int nobj = min(kPtObj, Z.batch - obj0);
   const int row = tid & 127, part = tid >> 7;          // operand row (j, z-rank index) and half
   const int jr = row >> 3, zr = row & 7;
@@ -119,8 +123,8 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
   // partials at the starting interface: [1] for every object
   for (int e = tid; e < kPtObj * kPtRX * kPtRZ; e += blockDim.x) Ls[e] = (e % (kPtRX * kPtRZ)) == 0 ? 1.0f : 0.0f;
   {
-    const int j0 = a.dir == 0 ? 0 : d;
-    if (tid < nobj) a.st[a.ioff[j0] + obj0 + tid] = 1.0f;
+    const int j0 = dir == 0 ? 0 : d;
+    if (tid < nobj) st[ioff[j0] + obj0 + tid] = 1.0f;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -132,10 +136,11 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
   const float* Zp = static_cast<const float*>(Z.p);
 
   for (int s = 0; s < d; ++s) {
-    const int k = a.dir == 0 ? s : d - 1 - s;
+    const int k = dir == 0 ? s : d - 1 - s;
     const int x0 = a.rx[k], x1 = a.rx[k + 1], z0 = Z.r[k], z1 = Z.r[k + 1], n = Z.n[k];
     // the contracted X-side rank (K = cr * n) and the output X-side rank (N)
-    const int cr = a.dir == 0 ? x0 : x1, orr = a.dir == 0 ? x1 : x0;
+    const int cr = dir == 0 ? x0 : x1, orr = dir == 0 ? x1 : x0;
+    const int lgn = n == 16 ? 4 : 3;  // n is 8 or 16
     const int K = cr * n;
     const uint32_t sboA = (uint32_t)(kPtKc / 4) * 128u, sboB = (uint32_t)(K / 4 + (K & 3 ? 1 : 0)) * 128u;
     // ---- Z cores of the CTA's objects: one bulk copy each (landing at an aligned address)
@@ -159,17 +164,22 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
                      : "memory");
       }
     }
-    // ---- shared operand B[o][(c, i)] = X_k (left: U[c][i][o]; right: V[o][i][c]), rows o < 32
-    const float* Xk = a.X + a.Xoff[k];
-    for (int e = tid; e < kPtRX * ((K + 3) & ~3); e += blockDim.x) {
-      const int Kp = (K + 3) & ~3;
-      const int o = e / Kp, kk = e % Kp;
-      float v = 0.0f;
-      if (o < orr && kk < K) {
-        const int c = kk / n, i = kk % n;
-        v = a.dir == 0 ? __ldg(Xk + ((long long)c * n + i) * x1 + o) : __ldg(Xk + ((long long)o * n + i) * x1 + c);
+    // ---- shared operand B[o][(c, i)] = X_k (left: U[c][i][o]; right: V[o][i][c]), rows o < 32;
+    // K = cr n is a multiple of 8. Left: o varies fastest (U's contiguous index); right: c.
+    const float* Xk = Xbase + a.Xoff[k];
+    if (dir == 0) {
+      for (int e = tid; e < kPtRX * K; e += blockDim.x) {
+        const int o = e & (kPtRX - 1), kk = e >> 5;  // kk = c n + i: U[c][i][o] at kk * x1 + o
+        const float v = o < orr ? __ldg(Xk + kk * x1 + o) : 0.0f;
+        *reinterpret_cast<uint32_t*>(Bop + pt_off(o, kk, sboB)) = tf32_bits(v);
       }
-      *reinterpret_cast<uint32_t*>(Bop + pt_off(o, kk, sboB)) = tf32_bits(v);
+    } else {
+      for (int e = tid; e < kPtRX * K; e += blockDim.x) {
+        const int c = e % cr, rest = e / cr;  // V[o][i][c] at (o n + i) x1 + c, c fastest
+        const int i = rest & (n - 1), o = rest >> lgn;
+        const float v = o < orr ? __ldg(Xk + (o * n + i) * x1 + c) : 0.0f;
+        *reinterpret_cast<uint32_t*>(Bop + pt_off(o, (c << lgn) + i, sboB)) = tf32_bits(v);
+      }
     }
     const bool zok = pt_wait(pt_smem(&bar_z), ph_z);
     ph_z ^= 1u;
@@ -179,7 +189,11 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
     // ---- chunks of 4 contracted rank indices
     const int nch = (cr + kPtChunkR - 1) / kPtChunkR;
     const float* zj = Zl + jr * kPtZObj + (int)((reinterpret_cast<uintptr_t>(Zp + core_base(Z, k, obj0 + min(jr, nobj - 1))) & 15) >> 2);
-    const bool rvalid = jr < nobj && zr < (a.dir == 0 ? z1 : z0);
+    const bool rvalid = jr < nobj && zr < (dir == 0 ? z1 : z0);
+    // this row's Z values: left z[g] = Z[g][i][zr] (g < z0), right z[d] = Z[zr][i][d] (d < z1)
+    const int zlen = dir == 0 ? z0 : z1;
+    const int zstep = dir == 0 ? n * z1 : 1;                     // stride between the 8 values
+    const float* zrow = dir == 0 ? zj + zr : zj + zr * n * z1;  // + i * z1 for slice i
     for (int ch = 0; ch < nch; ++ch) {
       const int buf = ch & 1;
       // the products that read this buffer (chunk ch - 2) must be done
@@ -190,30 +204,39 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
         pend[buf] = 0;
       }
       char* Ab = Abuf + buf * kPtABytes;
-      // T[row][(c - 4 ch) * 16 + i] for this thread's two rank indices c
-      for (int cc = part * 2; cc < part * 2 + 2; ++cc) {
-        const int c = ch * kPtChunkR + cc;
-        const float* Lrow = Ls + (jr * kPtRX + c) * kPtRZ;   // left: L[c][gamma]; right: R[c][delta]
+      // T[row][(c - 4 ch) * 16 + i] for this thread's two rank indices c = c0, c0 + 1: the
+      // partial rows of both in registers, each slice's Z values loaded once for both
+      {
+        const int c0 = ch * kPtChunkR + part * 2;
+        float l0[kPtRZ], l1[kPtRZ];
+#pragma unroll
+        for (int g = 0; g < kPtRZ; ++g) {  // left: L[c][gamma]; right: R[c][delta] (zero padded)
+          l0[g] = Ls[(jr * kPtRX + c0) * kPtRZ + g];
+          l1[g] = Ls[(jr * kPtRX + c0 + 1) * kPtRZ + g];
+        }
+        const bool v0 = rvalid && c0 < cr, v1 = rvalid && c0 + 1 < cr;
         for (int i4 = 0; i4 < kPtNmax; i4 += 4) {
-          float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-          if (rvalid && c < cr) {
+          float t0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, t1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          if (v0 && i4 < n) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const int i = i4 + u;
-              if (i < n) {
-                float acc = 0.0f;
-                if (a.dir == 0) {  // sum_gamma L[c][gamma] Z[gamma][i][zr]
-                  for (int g = 0; g < z0; ++g) acc = fmaf(Lrow[g], zj[((long long)g * n + i) * z1 + zr], acc);
-                } else {           // sum_delta R[c][delta] Z[zr][i][delta]
-                  for (int dd = 0; dd < z1; ++dd) acc = fmaf(Lrow[dd], zj[((long long)zr * n + i) * z1 + dd], acc);
-                }
-                t[u] = acc;
+              const float* zp = zrow + (i4 + u) * z1;
+              float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+              for (int g = 0; g < kPtRZ; ++g) {
+                const float zv = g < zlen ? zp[g * zstep] : 0.0f;
+                s0 = fmaf(l0[g], zv, s0);
+                s1 = fmaf(l1[g], zv, s1);
               }
+              t0[u] = s0;
+              t1[u] = v1 ? s1 : 0.0f;
             }
           }
-          const int kk = cc * kPtNmax + i4;
+          const int kk = part * 2 * kPtNmax + i4;
           *reinterpret_cast<uint4*>(Ab + pt_off(row, kk, sboA)) =
-              make_uint4(tf32_bits(t[0]), tf32_bits(t[1]), tf32_bits(t[2]), tf32_bits(t[3]));
+              make_uint4(tf32_bits(t0[0]), tf32_bits(t0[1]), tf32_bits(t0[2]), tf32_bits(t0[3]));
+          *reinterpret_cast<uint4*>(Ab + pt_off(row, kk + kPtNmax, sboA)) =
+              make_uint4(tf32_bits(t1[0]), tf32_bits(t1[1]), tf32_bits(t1[2]), tf32_bits(t1[3]));
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -274,14 +297,14 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
           : "memory");
       // row (j, z) holds the new partial's column z: P[j][o][z] for o < 32
       const int j = (warp * 32 + lane) >> 3, zz = lane & 7;
-      const int zlim = a.dir == 0 ? z1 : z0;
-      const int jint = a.dir == 0 ? k + 1 : k;
+      const int zlim = dir == 0 ? z1 : z0;
+      const int jint = dir == 0 ? k + 1 : k;
 #pragma unroll
       for (int o = 0; o < kPtRX; ++o) {
         const float v = (o < orr && zz < zlim && j < nobj) ? __uint_as_float(r[o]) : 0.0f;
         Ls[(j * kPtRX + o) * kPtRZ + zz] = v;
         if (j < nobj && o < orr && zz < zlim)
-          a.st[a.ioff[jint] + (long long)(obj0 + j) * orr * zlim + o * zlim + zz] = v;
+          st[ioff[jint] + (long long)(obj0 + j) * orr * zlim + o * zlim + zz] = v;
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -310,7 +333,7 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
 bool psweep_tc_supported(const TTV& X, const TTV& Z) {
   if (X.rmax > kPtRX || Z.rmax > kPtRZ || Z.nmax > kPtNmax) return false;
   for (int k = 0; k < Z.d; ++k)
-    if ((Z.n[k] & 7) != 0) return false;  // K steps of 8 modes
+    if (Z.n[k] != 8 && Z.n[k] != 16) return false;  // K steps of 8 modes, shifts for the index split
   return true;
 }
 
@@ -318,26 +341,29 @@ size_t psweep_tc_smem() {
   return 2 * (size_t)kPtABytes + kPtBBytes + sizeof(float) * ((size_t)kPtObj * kPtZObj + (size_t)kPtObj * kPtRX * kPtRZ);
 }
 
-// dir 0: left partials of (X = U, Z) into st; dir 1: right partials of (X = V, Z).
-t3f_status run_psweep_tc(const TTV& X, const TTV& Z, int dir, float* st, const long long* ioff, int* err,
-                         cudaStream_t s) {
+// Both sweeps in one launch: the left partials of (U, Z) into stL, the right partials of
+// (V, Z) into stR (blocks [0, nblk) and [nblk, 2 nblk)).
+t3f_status run_psweep_tc(const TTV& U, const TTV& V, const TTV& Z, float* stL, const long long* ioffL, float* stR,
+                         const long long* ioffR, int* err, cudaStream_t s) {
   PtArgs a;
   memset(&a, 0, sizeof(a));
   a.Z = Z;
-  a.X = static_cast<const float*>(X.p);
-  for (int k = 0; k < X.d; ++k) a.Xoff[k] = X.off[k];
-  for (int k = 0; k <= X.d; ++k) {
-    a.rx[k] = X.r[k];
-    a.ioff[k] = ioff[k];
+  a.X[0] = static_cast<const float*>(U.p);
+  a.X[1] = static_cast<const float*>(V.p);
+  for (int k = 0; k < U.d; ++k) a.Xoff[k] = U.off[k];
+  for (int k = 0; k <= U.d; ++k) {
+    a.rx[k] = U.r[k];
+    a.ioff[0][k] = ioffL[k];
+    a.ioff[1][k] = ioffR[k];
   }
-  a.dir = dir;
-  a.st = st;
+  a.st[0] = stL;
+  a.st[1] = stR;
   a.err = err;
+  a.nblk = (Z.batch + kPtObj - 1) / kPtObj;
   const size_t smem = psweep_tc_smem();
   if (cudaFuncSetAttribute(k_psweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return T3F_ERR_CUDA;
-  const unsigned grid = (unsigned)((Z.batch + kPtObj - 1) / kPtObj);
-  k_psweep_tc<<<grid, kPtThreads, smem, s>>>(a);
+  k_psweep_tc<<<(unsigned)(2 * a.nblk), kPtThreads, smem, s>>>(a);
   return launch_status();
 }
 

@@ -74,13 +74,13 @@ t3f_status run_gauge_project(const TTV& U, const float* Z, float* out, cudaStrea
 // Register-tiled project_sum sweeps (psweep.cu): X side ranks <= 32, Z ranks <= 8.
 bool psweep_supported(const TTV& X, const TTV& Z);
 t3f_status run_psweep(const TTV& X, const TTV& Z, int dir, const float* A, const float* B1, const float* B2,
-                      float* st1, float* st2, const long long* ioff, cudaStream_t s);
+                      float* st1, float* st2, const long long* ioff, cudaStream_t s, int* err = nullptr);
 int passemble_ranges(const TTV& Z);
 // Tensor-core (TF32) form of the project_sum sweeps (psweep_tc.cu): X ranks <= 32, Z ranks
-// <= 8, modes <= 16 and multiples of 8.
+// <= 8, modes 8 or 16; the left (U) and right (V) sweeps in one launch.
 bool psweep_tc_supported(const TTV& X, const TTV& Z);
-t3f_status run_psweep_tc(const TTV& X, const TTV& Z, int dir, float* st, const long long* ioff, int* err,
-                         cudaStream_t s);
+t3f_status run_psweep_tc(const TTV& U, const TTV& V, const TTV& Z, float* stL, const long long* ioffL, float* stR,
+                         const long long* ioffR, int* err, cudaStream_t s);
 t3f_status run_passemble(const TTV& X, const TTV& Z, const float* L, const float* R, const long long* ioff,
                          const float* c, float* part, int nranges, cudaStream_t s);
 t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V, const float* W, const float* L,
