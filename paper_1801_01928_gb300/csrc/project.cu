@@ -24,6 +24,7 @@ struct GaugeArgs {
   TTV U;
   const float* Z;   // compact, U's shape
   float* out;       // compact, U's shape
+  int staged;       // U_k and Z_k fit in shared memory
 };
 
 __global__ void __launch_bounds__(256) k_gauge(const __grid_constant__ GaugeArgs a) {
@@ -39,18 +40,32 @@ __global__ void __launch_bounds__(256) k_gauge(const __grid_constant__ GaugeArgs
     for (int e = threadIdx.x; e < m * r1; e += blockDim.x) Ok[e] = Zk[e];
     return;
   }
+  // U_k and Z_k staged in shared memory when they fit (the host sizes the launch), else read
+  // from global memory
   float* G = sm;  // r1 x r1: G = U^T Z
+  const bool staged = a.staged;
+  float* Us = G + U.rmax * U.rmax;
+  float* Zs = Us + (staged ? m * r1 : 0);
+  if (staged) {
+    for (int e = threadIdx.x; e < m * r1; e += blockDim.x) {
+      Us[e] = __ldg(Uk + e);
+      Zs[e] = Zk[e];
+    }
+    __syncthreads();
+  }
+  const float* Ur = staged ? Us : Uk;
+  const float* Zr = staged ? Zs : Zk;
   for (int e = threadIdx.x; e < r1 * r1; e += blockDim.x) {
     const int a1 = e / r1, b1 = e % r1;
     float s = 0.0f;
-    for (int q = 0; q < m; ++q) s = fmaf(Uk[q * r1 + a1], Zk[q * r1 + b1], s);
+    for (int q = 0; q < m; ++q) s = fmaf(Ur[q * r1 + a1], Zr[q * r1 + b1], s);
     G[e] = s;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < m * r1; e += blockDim.x) {
     const int q = e / r1, b1 = e % r1;
-    float s = Zk[e];
-    for (int a1 = 0; a1 < r1; ++a1) s = fmaf(-Uk[q * r1 + a1], G[a1 * r1 + b1], s);
+    float s = Zr[e];
+    for (int a1 = 0; a1 < r1; ++a1) s = fmaf(-Ur[q * r1 + a1], G[a1 * r1 + b1], s);
     Ok[e] = s;
   }
 }
@@ -60,7 +75,14 @@ t3f_status run_gauge_project(const TTV& U, const float* Z, float* out, cudaStrea
   a.U = U;
   a.Z = Z;
   a.out = out;
-  const size_t smem = sizeof(float) * U.rmax * U.rmax;
+  long long mr = 0;
+  for (int k = 0; k + 1 < U.d; ++k) mr = mr > U.osz[k] ? mr : U.osz[k];
+  const size_t base = sizeof(float) * U.rmax * U.rmax;
+  const size_t full = base + sizeof(float) * 2 * (size_t)mr;
+  a.staged = full <= 200 * 1024 ? 1 : 0;
+  const size_t smem = a.staged ? full : base;
+  if (cudaFuncSetAttribute(k_gauge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return T3F_ERR_CUDA;
   k_gauge<<<U.d, 256, smem, s>>>(a);
   return launch_status();
 }

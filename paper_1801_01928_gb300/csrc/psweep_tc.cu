@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
         *reinterpret_cast<uint32_t*>(Bop + pt_off(o, (c << lgn) + i, sboB)) = tf32_bits(v);
       }
     }
-    const bool zok = pt_wait(pt_smem(&bar_z), ph_z);
+    // one thread polls the barrier, the others wait at the block barrier that follows
+    const bool zok = tid == 0 ? pt_wait(pt_smem(&bar_z), ph_z) : true;
     ph_z ^= 1u;
     zpend = !zok;
     if (__syncthreads_or(!zok)) bad = true;  // block-uniform
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
       // the products that read this buffer (chunk ch - 2) must be done
       bool wok = true;
       if (pend[buf]) {
-        wok = pt_wait(pt_smem(&bar_mma[buf]), ph_mma[buf]);
+        wok = tid == 0 ? pt_wait(pt_smem(&bar_mma[buf]), ph_mma[buf]) : true;
         ph_mma[buf] ^= 1u;
         pend[buf] = 0;
       }
@@ -274,15 +275,16 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
     bool eok = true;
     for (int b2 = 0; b2 < 2; ++b2)
       if (pend[b2]) {
-        eok &= pt_wait(pt_smem(&bar_mma[b2]), ph_mma[b2]);
+        eok &= tid == 0 ? pt_wait(pt_smem(&bar_mma[b2]), ph_mma[b2]) : true;
         ph_mma[b2] ^= 1u;
         pend[b2] = 0;
       }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (__syncthreads_or(!eok)) {
       bad = true;
       break;
     }
+    // thread 0 saw the products complete; the block barrier above orders the reads below
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp < 4) {
       uint32_t r[32];
       asm volatile(

@@ -202,80 +202,129 @@ __global__ void __launch_bounds__(256) k_tangent_gather(const __grid_constant__ 
 
 // ---------------------------------------------------------------------------------------
 // Gram matrix of tangent vectors (FP32 CUDA cores): G[a][b] = sum_k <dA_a,k, dB_b,k>, a
-// split-K product over the concatenated coordinates. A CTA owns a 64 x 64 tile of pairs and
-// one K range; its partial goes to part[split][a][b] and k_tgram_reduce sums the splits in a
-// fixed order (deterministic).
+// split-K product over the concatenated coordinates. A CTA owns a 128 x 128 tile of pairs and
+// a range of 16-column chunks (a chunk never crosses a core or a split; columns past a core's
+// end are zero); 256 threads hold 8 x 8 accumulators each (rows ty*4 + {0..3} and
+// 64 + ty*4 + {0..3}, columns likewise with tx), fed by float4 loads from transposed,
+// double-buffered operand tiles. On a diagonal tile of a self Gram matrix one operand is
+// staged. The CTA's partial goes to part[split][a][b]; the splits are summed in a fixed order.
 // ---------------------------------------------------------------------------------------
-constexpr int kTM = 64, kKC = 32;
+constexpr int kTM = 128, kKC = 16, kLD = kTM + 4;
 
 struct TGramArgs {
   TTV A, B;
   long long ksz[T3F_MAX_D];  // coordinates of core k per object
-  long long Ktot;            // sum_k ksz
-  long long kper;            // K elements per split
-  int nsplit, tilesB;
+  long long nchunks, cper;   // 16-column chunks in all, per split
+  int nsplit, tilesB, self;
   float* part;               // [nsplit][A.batch][B.batch]
 };
 
-__global__ void __launch_bounds__(kThreads) k_tgram(const __grid_constant__ TGramArgs g) {
-  __shared__ float As[kTM][kKC + 1];
-  __shared__ float Bs[kTM][kKC + 1];
+// chunk c of the concatenated coordinates -> (core k, column of the core)
+__device__ __forceinline__ void tg_chunk(const TGramArgs& g, long long c, int* k, long long* col) {
+  long long first = 0;
+  int kk = 0;
+  for (; kk < g.A.d; ++kk) {
+    const long long nk = (g.ksz[kk] + kKC - 1) / kKC;
+    if (c < first + nk) break;
+    first += nk;
+  }
+  *k = kk;
+  *col = (c - first) * kKC;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_tgram(const __grid_constant__ TGramArgs g) {
+  __shared__ __align__(16) float As[2][kKC][kLD];
+  __shared__ __align__(16) float Bs[2][kKC][kLD];
   const int split = blockIdx.x % g.nsplit;
   const int tile = blockIdx.x / g.nsplit;
   const int a0 = (tile / g.tilesB) * kTM, b0 = (tile % g.tilesB) * kTM;
+  const bool one = g.self && a0 == b0;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const long long e0 = (long long)split * g.kper;
-  const long long e1 = min(g.Ktot, e0 + g.kper);
-  float acc[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+  const long long c0 = (long long)split * g.cper, c1 = min(g.nchunks, c0 + g.cper);
   const float* Ap = static_cast<const float*>(g.A.p);
   const float* Bp = static_cast<const float*>(g.B.p);
-  // walk the cores overlapping [e0, e1)
-  long long base = 0;
-  for (int k = 0; k < g.A.d && base < e1; ++k) {
+  float acc[8][8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.0f;
+  // staging: thread t loads rows t / 4 and 64 + t / 4, columns 4 (t % 4) .. + 3 of a chunk
+  const int lr = tid >> 2, lq = (tid & 3) * 4;
+  float4 ra[2], rb[2];
+  auto load = [&](long long c) {
+    int k;
+    long long col;
+    tg_chunk(g, c, &k, &col);
     const long long sz = g.ksz[k];
-    const long long lo = max(e0, base), hi = min(e1, base + sz);
-    for (long long e = lo; e < hi; e += kKC) {
-      const int kc = (int)min((long long)kKC, hi - e);
-      const long long col = e - base;
-      __syncthreads();
-      for (int l = tid; l < kTM * kKC; l += kThreads) {
-        const int row = l / kKC, cc = l % kKC;
-        float va = 0.0f, vb = 0.0f;
-        if (cc < kc) {
-          if (a0 + row < g.A.batch) va = __ldg(Ap + g.A.off[k] + (long long)(a0 + row) * sz + col + cc);
-          if (b0 + row < g.B.batch) vb = __ldg(Bp + g.B.off[k] + (long long)(b0 + row) * sz + col + cc);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = lr + 64 * h;
+      float va[4] = {0.0f, 0.0f, 0.0f, 0.0f}, vb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long cc = col + lq + u;
+        if (cc < sz) {
+          if (a0 + r < g.A.batch) va[u] = __ldg(Ap + g.A.off[k] + (long long)(a0 + r) * sz + cc);
+          if (!one && b0 + r < g.B.batch) vb[u] = __ldg(Bp + g.B.off[k] + (long long)(b0 + r) * sz + cc);
         }
-        As[row][cc] = va;
-        Bs[row][cc] = vb;
       }
-      __syncthreads();
-#pragma unroll 8
-      for (int kk = 0; kk < kKC; ++kk) {
-        float av[4], bv[4];
+      ra[h] = make_float4(va[0], va[1], va[2], va[3]);
+      rb[h] = make_float4(vb[0], vb[1], vb[2], vb[3]);
+    }
+  };
+  auto store = [&](int buf) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) av[u] = As[ty + 16 * u][kk];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) bv[v] = Bs[tx + 16 * v][kk];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    for (int h = 0; h < 2; ++h) {
+      const int r = lr + 64 * h;
+      As[buf][lq + 0][r] = ra[h].x;
+      As[buf][lq + 1][r] = ra[h].y;
+      As[buf][lq + 2][r] = ra[h].z;
+      As[buf][lq + 3][r] = ra[h].w;
+      if (!one) {
+        Bs[buf][lq + 0][r] = rb[h].x;
+        Bs[buf][lq + 1][r] = rb[h].y;
+        Bs[buf][lq + 2][r] = rb[h].z;
+        Bs[buf][lq + 3][r] = rb[h].w;
       }
     }
-    base += sz;
+  };
+  if (c0 < c1) {
+    load(c0);
+    store(0);
+  }
+  __syncthreads();
+  for (long long c = c0; c < c1; ++c) {
+    const int buf = (int)((c - c0) & 1);
+    if (c + 1 < c1) load(c + 1);  // in flight during the products
+    const float(*Ab)[kLD] = As[buf];
+    const float(*Bb)[kLD] = one ? As[buf] : Bs[buf];
+#pragma unroll
+    for (int kk = 0; kk < kKC; ++kk) {
+      const float4 a_lo = *reinterpret_cast<const float4*>(&Ab[kk][ty * 4]);
+      const float4 a_hi = *reinterpret_cast<const float4*>(&Ab[kk][64 + ty * 4]);
+      const float4 b_lo = *reinterpret_cast<const float4*>(&Bb[kk][tx * 4]);
+      const float4 b_hi = *reinterpret_cast<const float4*>(&Bb[kk][64 + tx * 4]);
+      const float av[8] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
+      const float bv[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    }
+    if (c + 1 < c1) store(buf ^ 1);
+    __syncthreads();
   }
   float* P = g.part + (long long)split * g.A.batch * g.B.batch;
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 8; ++u) {
+    const int a = a0 + (u < 4 ? ty * 4 + u : 64 + ty * 4 + u - 4);
+    if (a >= g.A.batch) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int a = a0 + ty + 16 * u, b = b0 + tx + 16 * v;
-      if (a < g.A.batch && b < g.B.batch) P[(long long)a * g.B.batch + b] = acc[u][v];
+    for (int v = 0; v < 8; ++v) {
+      const int b = b0 + (v < 4 ? tx * 4 + v : 64 + tx * 4 + v - 4);
+      if (b < g.B.batch) P[(long long)a * g.B.batch + b] = acc[u][v];
     }
+  }
 }
 
 // Sum of split partials in a fixed order, in two levels so that every SM takes part:
@@ -322,23 +371,22 @@ int dev_sms() {
 
 struct TGramPlan {
   int tilesA, tilesB, nsplit;
-  long long Ktot, kper;
+  long long nchunks, cper;
   size_t part_off, mid_off, total;
 };
 
 TGramPlan tgram_plan(const TTV& A, const TTV& B) {
   TGramPlan p;
-  p.Ktot = 0;
-  for (int k = 0; k < A.d; ++k) p.Ktot += A.osz[k];
+  p.nchunks = 0;
+  for (int k = 0; k < A.d; ++k) p.nchunks += (A.osz[k] + kKC - 1) / kKC;
   p.tilesA = (A.batch + kTM - 1) / kTM;
   p.tilesB = (B.batch + kTM - 1) / kTM;
   const long long tiles = (long long)p.tilesA * p.tilesB;
-  long long ns = ((long long)dev_sms() * 4 + tiles - 1) / tiles;  // about four CTAs per SM in all
-  ns = std::min(ns, (p.Ktot + 255) / 256);              // at least 256 coordinates per split
+  long long ns = ((long long)dev_sms() * 2 + tiles - 1) / tiles;  // two CTAs per SM in all
+  ns = std::min(ns, (p.nchunks + 7) / 8);                          // at least 8 chunks per split
   ns = std::max(ns, 1LL);
-  p.kper = (p.Ktot + ns - 1) / ns;
-  p.kper = (p.kper + kKC - 1) / kKC * kKC;
-  p.nsplit = (int)((p.Ktot + p.kper - 1) / p.kper);
+  p.cper = (p.nchunks + ns - 1) / ns;
+  p.nsplit = (int)((p.nchunks + p.cper - 1) / p.cper);
   p.part_off = kWsHeader;
   p.mid_off = p.part_off + align256(sizeof(float) * (size_t)p.nsplit * A.batch * B.batch);
   p.total = p.mid_off + align256(sizeof(float) * (size_t)kReduceGroups * A.batch * B.batch);
@@ -676,10 +724,11 @@ extern "C" t3f_status t3f_tangent_gram(const t3f_tt* dA, const t3f_tt* dB, float
   g.A = va;
   g.B = vb;
   for (int k = 0; k < va.d; ++k) g.ksz[k] = va.osz[k];
-  g.Ktot = p.Ktot;
-  g.kper = p.kper;
+  g.nchunks = p.nchunks;
+  g.cper = p.cper;
   g.nsplit = p.nsplit;
   g.tilesB = p.tilesB;
+  g.self = (va.p == vb.p && va.batch == vb.batch) ? 1 : 0;
   g.part = reinterpret_cast<float*>(static_cast<char*>(ws) + p.part_off);
   const long long grid = (long long)p.tilesA * p.tilesB * p.nsplit;
   if (grid > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
