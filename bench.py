@@ -544,9 +544,40 @@ def reduced_precision(w, flops, flush, stream, reps=5):
     dX32 = w.dX4.double()
     ms = timed(lambda: t3f.gram_groups_backward(X4b, w.gstart, ws4b, w.devbuf["dG4"], w.tiles4))
     dXb = t3f.gram_groups_backward(X4b, w.gstart, ws4b, w.devbuf["dG4"], w.tiles4)
+    keep["uneven_bwd_bf16_cores"] = (dXb, 1e-5)
     gf = flops["uneven_bwd"] / (ms * 1e-3) / 1e9
     out["uneven_bwd_bf16_cores"] = {"ms": round(ms, 4), "gflops": round(gf, 1), "diff_vs_fp32": round(rel(dXb, dX32), 6),
                                     "path": "BF16 cores, FP32 CUDA-core arithmetic (adjoint work lists)"}
+    # tensor-core adjoints: the uniform Gram (100 x 100) and the uneven batch. Sweeps in both
+    # directions store every interface's partials, then (tile, core, side) items run
+    # T = gM Y_i and dX_i = T R^T on the tensor cores
+    dG3 = w.devbuf["dG"]
+    dA32, _ = t3f.gram_backward(A3, B3, dG3)
+    for math_ in ("tf32", "bf16"):
+        ws3 = t3f.workspace("gram_bwd_tc", A3, B3)
+        ms = timed(lambda: t3f.gram_backward(A3, B3, dG3, math=math_, ws=ws3))
+        dAx, dBx = t3f.gram_backward(A3, B3, dG3, math=math_, ws=ws3)
+        tol = 5e-3 if math_ == "tf32" else 2e-2
+        keep[f"gram_bwd_{math_}"] = ((dAx, dBx), tol)
+        gf = flops["gram_bwd"] / (ms * 1e-3) / 1e9
+        out[f"gram_bwd_{math_}"] = {"ms": round(ms, 4), "gflops": round(gf, 1),
+                                    "diff_vs_fp32": round(rel(dAx.data, dA32.data.double()), 6),
+                                    "roofline": roof(gf, math_),
+                                    "path": "tcgen05 " + math_ + " sweeps storing partials + gradient products"}
+        del ws3
+    for key, X_, math_ in (("uneven_bwd_tf32", X4, "tf32"), ("uneven_bwd_bf16_tc", X4b, "bf16")):
+        ws_ = t3f.gram_groups_prepare(X_, w.gstart, w.tiles4, backward_math=math_)
+        dXx = torch.empty(X_.data.numel(), dtype=torch.float32, device=X_.data.device)
+        ms = timed(lambda: t3f.gram_groups_backward(X_, w.gstart, ws_, w.devbuf["dG4"], w.tiles4, dcores=dXx,
+                                                    math=math_))
+        t3f.gram_groups_backward(X_, w.gstart, ws_, w.devbuf["dG4"], w.tiles4, dcores=dXx, math=math_)
+        keep[key] = (dXx.clone(), 5e-3 if math_ == "tf32" else 2e-2)
+        gf = flops["uneven_bwd"] / (ms * 1e-3) / 1e9
+        out[key] = {"ms": round(ms, 4), "gflops": round(gf, 1), "diff_vs_fp32": round(rel(dXx, dX32), 6),
+                    "roofline": roof(gf, math_), "workspace_mb": round(ws_.numel() / 1e6, 1),
+                    "path": ("F32" if math_ == "tf32" else "BF16") + " cores; tcgen05 " + math_ +
+                            " sweeps storing partials + (tile, core, side) gradient items"}
+        del ws_, dXx
     # project_sum of config 5 with the U- and V-side sweep contractions on the tensor cores
     X5, Z5, c5 = w.tt("X5"), w.tt("Z5"), w.devbuf["c5"]
     U5, V5 = t3f.orthogonalize(X5)
@@ -1011,7 +1042,29 @@ def oracle_errors(w, out, extra=None):
     for key, (G_, tol) in (extra or {}).items():
         if key == "psum_tf32":
             continue
-        if key.startswith("gram_"):
+        if key.startswith("gram_bwd_"):
+            dAo, dBo = objs("A3", G_[0].data), objs("B3", G_[1].data)
+            rec(key + ".dA", [rel(dAo[a], O.gram_vjp([A[a]], B, dG[a:a + 1])[0][0]) for a in (0, 99)], tol)
+            rec(key + ".dB", [rel(dBo[b], O.gram_vjp(A, [B[b]], dG[:, b:b + 1])[1][0]) for b in (3,)], tol)
+        elif key.startswith("uneven_bwd_"):
+            rg_x = rg
+            if "bf16" in key:
+                import torch as _t
+                rg_x = t3f.RaggedTT(w.host["X4"].to(_t.bfloat16).to(_t.float64), dims, modes, ranks, offs)
+            obx = lambda o: [c.double().numpy() for c in rg_x.object_cores(o)]
+            gx = t3f.RaggedTT(G_.detach().cpu(), dims, modes, ranks, offs)
+            eb, off = [], 0
+            rng_b = np.random.default_rng(78)
+            for gi in range(len(w.gstart) - 1):
+                g0, Sg = w.gstart[gi], w.gstart[gi + 1] - w.gstart[gi]
+                a = int(rng_b.integers(0, Sg))
+                M = dG4[off:off + Sg * Sg].reshape(Sg, Sg)
+                grp = [obx(g0 + j) for j in range(Sg)]
+                ref = O.gram_vjp([grp[a]], grp, (M[a, :] + M[:, a])[None, :])[0][0]
+                eb.append(rel([c.double().numpy() for c in gx.object_cores(g0 + a)], ref))
+                off += Sg * Sg
+            rec(key + ".dX", eb, tol)
+        elif key.startswith("gram_"):
             Gx = G_.double().cpu().numpy()
             rec(key + ".G", [rel(Gx[a], [O.dot(A[a], Bb) for Bb in B]) for a in (0, 57, 99)], tol)
         elif key.startswith("uneven_"):

@@ -81,7 +81,7 @@ typedef enum {
   T3F_OP_MATVEC = 7, T3F_OP_MATVEC_BWD = 8,
   T3F_OP_ORTH = 9, T3F_OP_PSUM = 10, T3F_OP_PSUM_BWD = 11,
   T3F_OP_PROJECT = 12, T3F_OP_TANGENT_GRAM = 13, T3F_OP_COMPLETION_HVP = 14,
-  T3F_OP_ROUND = 15
+  T3F_OP_ROUND = 15, T3F_OP_GRAM_BWD_TC = 16
 } t3f_op;
 
 /* Name of a status code (static string). */
@@ -105,7 +105,7 @@ int64_t t3f_packed_size(const t3f_tt* t);
  *   MATVEC, MATVEC_BWD: a = A (TT-matrix), b = x.
  *   ORTH: a = X.    PSUM, PSUM_BWD, PROJECT: a = U, b = Z (the batch being projected).
  *   TANGENT_GRAM: a = dA, b = dB.   COMPLETION_HVP: a = U, b = V, n_items = N.
- *   ROUND: a = X.
+ *   ROUND: a = X.    GRAM_BWD_TC: a = A, b = B (t3f_gram_backward with math TF32 or BF16).
  * Returns 0 for an invalid request (check with the call itself for the status).
  */
 size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* b, int64_t n_items);
@@ -138,12 +138,20 @@ t3f_status t3f_norm(const t3f_tt* A, double* out, void* ws, size_t ws_bytes,
  * of sum_ab dG[a,b] <A_a, B_b>:
  *   dA_a^k[:,i,:] = sum_b dG[a,b] M^{ab}_{k-1} B_b^k[:,i,:] (R^{ab}_{k+1})^T,
  *   dB_b^k[:,i,:] = sum_a dG[a,b] (M^{ab}_{k-1})^T A_a^k[:,i,:] R^{ab}_{k+1},
- * with R the right transfer sweep. The left partials are recomputed inside (nothing is kept
- * from the forward call). dA, dB: F32 descriptors with the shapes of A and B. Either may be
- * NULL to skip it.
+ * with R the right transfer sweep. The partials are recomputed inside (nothing is kept from
+ * the forward call). dA, dB: F32 descriptors with the shapes of A and B. Either may be NULL
+ * to skip it. math (t3f_math):
+ *   FP32: CUDA-core FP32 throughout; ws: t3f_workspace_size(T3F_OP_GRAM_BWD) bytes.
+ *   TF32 (F32 cores) / BF16 (F32 or BF16 cores): tensor cores (tcgen05, FP32 accumulation)
+ *   in tiles of (128/RA) x (128/RB) pairs, ranks <= 64 (zero-padded to 16, 32 or 64), else
+ *   T3F_ERR_UNSUPPORTED. The left and right sweeps store the partials of every interface
+ *   (M scaled by dG) in the workspace, rounded to the operand type; then per (tile, core,
+ *   side) the products T = gM Y_i and dX_i = T R^T run on the tensor cores. ws:
+ *   t3f_workspace_size(T3F_OP_GRAM_BWD_TC) bytes (error word first; a tensor-core wait that
+ *   runs out writes T3F_ERR_TIMEOUT there, see t3f_device_status).
  */
 t3f_status t3f_gram_backward(const t3f_tt* A, const t3f_tt* B, const float* dG,
-                             t3f_tt* dA, t3f_tt* dB, void* ws, size_t ws_bytes,
+                             t3f_tt* dA, t3f_tt* dB, int32_t math, void* ws, size_t ws_bytes,
                              t3f_stream_t stream);
 
 /*
@@ -391,15 +399,24 @@ t3f_status t3f_gram_groups(const t3f_tt_ragged* X, int32_t ngroups, const int32_
 /*
  * Adjoint of t3f_gram_groups: dcores (device float, the layout of X's cores with F32
  * elements) receives the cotangent of sum_g sum_ab dout_g[a][b] <X_a, X_b> for the
- * concatenated per-group cotangents dout (device float, like `out`). FP32 CUDA-core
- * arithmetic: the tiled adjoint drains its own work lists (runs of rank-sorted objects cut so
- * that a tile's seven partial tiles fit one CTA, side at most 16 whatever `tiles`): tiles that
- * need more than half an SM's shared memory in one persistent launch of 512-thread CTAs, the
- * rest in a second of 256-thread CTAs, two per SM. Every off-diagonal tile uses the
- * symmetrised cotangent dout[a][b] + dout[b][a]. Requires the same prepared `ws`.
+ * concatenated per-group cotangents dout (device float, like `out`). Every off-diagonal tile
+ * uses the symmetrised cotangent dout[a][b] + dout[b][a]. Requires the same prepared `ws`,
+ * of at least t3f_gram_groups_backward_workspace_size(..., math) bytes. math (t3f_math):
+ *   FP32: CUDA-core FP32 arithmetic: the tiled adjoint drains its own work lists (runs of
+ *   rank-sorted objects cut so that a tile's seven partial tiles fit one CTA, side at most 16
+ *   whatever `tiles`): tiles that need more than half an SM's shared memory in one
+ *   persistent launch of 512-thread CTAs, the rest in a second of 256-thread CTAs, two per SM.
+ *   TF32 (F32 cores) / BF16 (F32 or BF16 cores): tensor cores over the forward's tensor-core
+ *   tiles: one persistent launch runs every tile's left and right sweeps and stores the
+ *   partials of all interfaces after the prepared tables in `ws`; a second drains the
+ *   (tile, core, side) gradient items (see t3f_gram_backward). A tensor-core wait that runs
+ *   out writes T3F_ERR_TIMEOUT into the workspace's error word.
  */
+size_t t3f_gram_groups_backward_workspace_size(const t3f_tt_ragged* X, int32_t ngroups,
+                                               const int32_t* gstart, const int32_t* tiles,
+                                               int32_t math);
 t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t ngroups,
-                                    const int32_t* gstart, const int32_t* tiles,
+                                    const int32_t* gstart, const int32_t* tiles, int32_t math,
                                     const float* dout, float* dcores, void* ws,
                                     size_t ws_bytes, t3f_stream_t stream);
 

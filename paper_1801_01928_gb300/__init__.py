@@ -12,4 +12,5 @@ from ._binding import (  # noqa: F401
     device_status, gather, gather_backward, gram_groups, gram_groups_backward, gram_groups_prepare,
     gram, gram_backward, launch_count, load, matvec, matvec_backward, norm, orth_ranks, orthogonalize,
     project_sum, project_sum_backward, project, tangent_gram, project_matvec, completion_hvp, fma_probe, round_tt, round_ranks,
+    workspace,
 )

@@ -21,7 +21,7 @@ F32, F64, BF16 = 0, 1, 2
 MATH = {"fp32": 0, "tf32": 1, "bf16": 2}
 OP = dict(gram=1, gram_bwd=2, norm=3, gather=4, gather_bwd=5, rgather_bwd=6, matvec=7,
           matvec_bwd=8, orth=9, psum=10, psum_bwd=11, project=12, tangent_gram=13, completion_hvp=14,
-          round=15)
+          round=15, gram_bwd_tc=16)
 _TORCH_DTYPE = {F32: torch.float32, F64: torch.float64, BF16: torch.bfloat16}
 _CODE = {v: k for k, v in _TORCH_DTYPE.items()}
 
@@ -53,7 +53,7 @@ _SIGS = {
     "t3f_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, _P, _P, ctypes.c_int64]),
     "t3f_gram": (ctypes.c_int32, [_P, _P, _VP, ctypes.c_int32, _VP, _SZ, _VP]),
     "t3f_norm": (ctypes.c_int32, [_P, _VP, _VP, _SZ, _VP]),
-    "t3f_gram_backward": (ctypes.c_int32, [_P, _P, _VP, _P, _P, _VP, _SZ, _VP]),
+    "t3f_gram_backward": (ctypes.c_int32, [_P, _P, _VP, _P, _P, ctypes.c_int32, _VP, _SZ, _VP]),
     "t3f_gather": (ctypes.c_int32, [_P, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "t3f_gather_noalloc": (ctypes.c_int32, [_P, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
     "t3f_gather_noalloc_status": (ctypes.c_int32, [_VP]),
@@ -201,6 +201,11 @@ def _ws(op: str, a: TT, b: Optional[TT], n_items: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
+def workspace(op: str, a: TT, b: Optional[TT] = None, n_items: int = 0) -> torch.Tensor:
+    """A device workspace of t3f_workspace_size(op) bytes (op: a key of OP)."""
+    return _ws(op, a, b, n_items, a.data.device)
+
+
 # ---------------------------------------------------------------------------------------
 # Operations (names follow include/t3f.h)
 # ---------------------------------------------------------------------------------------
@@ -221,13 +226,17 @@ def norm(A: TT) -> torch.Tensor:
     return out
 
 
-def gram_backward(A: TT, B: TT, dG: torch.Tensor, need_A=True, need_B=True):
+def gram_backward(A: TT, B: TT, dG: torch.Tensor, need_A=True, need_B=True, math: str = "fp32",
+                  ws: Optional[torch.Tensor] = None):
+    """Cotangents of sum_ab dG[a,b] <A_a, B_b>; math "tf32" / "bf16" runs the tensor-core
+    adjoint (its workspace holds the stored partials; pass `ws` to reuse one)."""
     dev = A.data.device
     dA = A.empty_like(torch.float32) if need_A else None
     dB = B.empty_like(torch.float32) if need_B else None
-    ws = _ws("gram_bwd", A, B, 0, dev)
+    if ws is None:
+        ws = _ws("gram_bwd" if math == "fp32" else "gram_bwd_tc", A, B, 0, dev)
     dG = dG.contiguous().to(torch.float32)
-    _check(_lib().t3f_gram_backward(_ref(A), _ref(B), _ptr(dG), _ref(dA), _ref(dB), _ptr(ws),
+    _check(_lib().t3f_gram_backward(_ref(A), _ref(B), _ptr(dG), _ref(dA), _ref(dB), MATH[math], _ptr(ws),
                                     ws.numel(), _stream(dev)), "t3f_gram_backward")
     return dA, dB
 
@@ -417,7 +426,9 @@ _SIGS.update({
     "t3f_gram_groups_prepare": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, _VP, _SZ, _VP]),
     "t3f_gram_groups": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, ctypes.c_int32, _VP, _VP, _VP, _SZ,
                                          _VP]),
-    "t3f_gram_groups_backward": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, _VP, _VP, _VP, _SZ, _VP]),
+    "t3f_gram_groups_backward": (ctypes.c_int32, [_RP, ctypes.c_int32, _I32P, _I32P, ctypes.c_int32, _VP, _VP, _VP,
+                                                  _SZ, _VP]),
+    "t3f_gram_groups_backward_workspace_size": (ctypes.c_size_t, [_RP, ctypes.c_int32, _I32P, _I32P, ctypes.c_int32]),
 })
 EXPORTS = tuple(_SIGS)
 
@@ -476,11 +487,14 @@ def _tiles_arg(tiles):
     return None if tiles is None else _i32(tiles)
 
 
-def gram_groups_prepare(X: RaggedTT, gstart, tiles=None) -> torch.Tensor:
-    """Workspace holding the work list and object tables of the grouped Gram (host copies)."""
+def gram_groups_prepare(X: RaggedTT, gstart, tiles=None, backward_math: str = "fp32") -> torch.Tensor:
+    """Workspace holding the work list and object tables of the grouped Gram (host copies),
+    sized for the adjoint in `backward_math` too (the tensor-core adjoint stores its partials
+    there)."""
     gs = _i32(gstart)
     tl = _tiles_arg(tiles)
-    nbytes = _lib().t3f_gram_groups_workspace_size(ctypes.byref(X.desc()), len(gstart) - 1, gs, tl)
+    nbytes = _lib().t3f_gram_groups_backward_workspace_size(ctypes.byref(X.desc()), len(gstart) - 1, gs, tl,
+                                                            MATH[backward_math])
     if nbytes == 0:
         raise T3FError(-2, "t3f_gram_groups_workspace_size")
     ws = torch.empty(int(nbytes), dtype=torch.uint8, device=X.data.device)
@@ -505,11 +519,15 @@ def gram_groups(X: RaggedTT, gstart, ws: torch.Tensor, tiles=None, want_norms=Tr
     return out, (norms if want_norms else None)
 
 
-def gram_groups_backward(X: RaggedTT, gstart, ws: torch.Tensor, dout: torch.Tensor, tiles=None, dcores=None):
+def gram_groups_backward(X: RaggedTT, gstart, ws: torch.Tensor, dout: torch.Tensor, tiles=None, dcores=None,
+                         math: str = "fp32"):
+    """Core cotangents of the grouped Gram; math "tf32" / "bf16" needs a workspace prepared
+    with the same backward_math."""
     dev = X.data.device
     dcores = torch.empty(X.data.numel(), dtype=torch.float32, device=dev) if dcores is None else dcores
     _check(_lib().t3f_gram_groups_backward(ctypes.byref(X.desc()), len(gstart) - 1, _i32(gstart), _tiles_arg(tiles),
-                                           _ptr(dout), _ptr(dcores), _ptr(ws), ws.numel(), _stream(dev)),
+                                           MATH[math], _ptr(dout), _ptr(dcores), _ptr(ws), ws.numel(),
+                                           _stream(dev)),
            "t3f_gram_groups_backward")
     return dcores
 

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libt3f.so")
 
-SOURCES = ["api.cu", "sweep.cu", "gram.cu", "gather.cu", "matvec.cu", "orth.cu", "project.cu", "psweep.cu", "gram_tile.cu", "gram_tile_bwd.cu", "gram_groups.cu", "gram_mma.cu", "tangent.cu", "tgram_tc.cu", "probe.cu", "round.cu", "psweep_tc.cu"]
+SOURCES = ["api.cu", "sweep.cu", "gram.cu", "gather.cu", "matvec.cu", "orth.cu", "project.cu", "psweep.cu", "gram_tile.cu", "gram_tile_bwd.cu", "gram_groups.cu", "gram_mma.cu", "gram_mma_bwd.cu", "tangent.cu", "tgram_tc.cu", "probe.cu", "round.cu", "psweep_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -127,7 +127,8 @@ extern "C" t3f_status t3f_device_status(const void* ws, t3f_stream_t stream) {
 extern "C" size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* b, int64_t n_items) {
   TTV va, vb;
   if (!a || make_view(a, &va, -1, a->m != nullptr) != T3F_OK) return 0;
-  const bool need_b = op == T3F_OP_GRAM || op == T3F_OP_GRAM_BWD || op == T3F_OP_RGATHER_BWD ||
+  const bool need_b = op == T3F_OP_GRAM || op == T3F_OP_GRAM_BWD || op == T3F_OP_GRAM_BWD_TC ||
+                      op == T3F_OP_RGATHER_BWD ||
                       op == T3F_OP_MATVEC || op == T3F_OP_MATVEC_BWD || op == T3F_OP_PSUM ||
                       op == T3F_OP_PSUM_BWD || op == T3F_OP_PROJECT || op == T3F_OP_TANGENT_GRAM ||
                       op == T3F_OP_COMPLETION_HVP;
@@ -135,6 +136,7 @@ extern "C" size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* 
   switch (op) {
     case T3F_OP_GRAM: return kWsHeader;
     case T3F_OP_GRAM_BWD: return ws_gram_bwd(va, vb);
+    case T3F_OP_GRAM_BWD_TC: return ws_gram_bwd_tc(va, vb);
     case T3F_OP_NORM: return ws_norm(va);
     case T3F_OP_GATHER: return ws_gather(va, n_items, false);
     case T3F_OP_GATHER_BWD: return ws_gather(va, n_items, true);

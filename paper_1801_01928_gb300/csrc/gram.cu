@@ -286,7 +286,7 @@ extern "C" t3f_status t3f_norm(const t3f_tt* A, double* out, void* ws, size_t ws
 }
 
 extern "C" t3f_status t3f_gram_backward(const t3f_tt* A, const t3f_tt* B, const float* dG,
-                                        t3f_tt* dA, t3f_tt* dB, void* ws, size_t ws_bytes,
+                                        t3f_tt* dA, t3f_tt* dB, int32_t math, void* ws, size_t ws_bytes,
                                         t3f_stream_t stream) {
   TTV va, vb, vda, vdb;
   T3F_CHECK(gram_views(A, B, &va, &vb));
@@ -307,6 +307,14 @@ extern "C" t3f_status t3f_gram_backward(const t3f_tt* A, const t3f_tt* B, const 
     for (int k = 0; k <= vb.d; ++k)
       if (vdb.r[k] != vb.r[k] || (k < vb.d && vdb.n[k] != vb.n[k])) return T3F_ERR_SHAPE;
     args.dB = static_cast<float*>(vdb.p);
+  }
+  if (math != T3F_MATH_FP32 && math != T3F_MATH_TF32 && math != T3F_MATH_BF16) return T3F_ERR_ARG;
+  if (math != T3F_MATH_FP32) {
+    if (!gram_mma_supported(va, vb, math)) return T3F_ERR_UNSUPPORTED;
+    T3F_CHECK(check_ws(ws, ws_bytes, ws_gram_bwd_tc(va, vb)));
+    int* err = static_cast<int*>(ws);
+    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
+    return run_gram_tc_backward(va, vb, dG, args.dA, args.dB, math, static_cast<char*>(ws) + kWsHeader, err, s);
   }
   T3F_CHECK(check_ws(ws, ws_bytes, ws_gram_bwd(va, vb)));
   if (args.dA && cudaMemsetAsync(args.dA, 0, sizeof(float) * t3f_packed_size(dA), s) != cudaSuccess)

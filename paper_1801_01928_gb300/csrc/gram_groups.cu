@@ -39,6 +39,12 @@ t3f_status launch_gram_mma_list(int math, const void* cores, int dtype, int dmax
                                 const int* rk, const int* nmodes, const int* items, int nitems, int* head,
                                 const int* gstart, const int* gd, float* gout, const long long* gout_off,
                                 const int* perm, int* err, cudaStream_t s);
+t3f_status launch_gram_tc_backward_list(int math, const void* cores, int dtype, int dmax, const long long* off,
+                                        const int* rk, const int* nmodes, const int* items, int nitems,
+                                        const int* gitems, int ngitems, int* heads, const int* gstart,
+                                        const int* gd, const long long* gout_off, const int* perm,
+                                        const float* dout, float* dX, char* scr, const long long* soff, int* err,
+                                        cudaStream_t s);
 
 namespace {
 
@@ -68,6 +74,10 @@ struct Plan {
   std::vector<int> items;    // 8 ints per item (forward tiles, all bucket pairs)
   std::vector<int> mitems;   // tensor-core tiles (every bucket pair)
   int nmitems = 0;
+  std::vector<long long> tsoff;  // tensor-core adjoint: first slot orientation of each tile
+  std::vector<int> titems;   // tensor-core adjoint gradient items: tile, core, side, 0
+  int ntitems = 0;
+  long long tunits = 0;      // slot orientations (128 x 128 operands) of all tiles
   std::vector<int> bitems;   // 8 ints per item (adjoint tiles for 512-thread CTAs, one per SM)
   int nbitems = 0;
   size_t bsmem = 0;
@@ -87,7 +97,8 @@ struct Plan {
   std::vector<Range> br;     // [group][bucket]
   size_t smem = 0;
   // workspace layout (bytes)
-  size_t o_items, o_mitems, o_bitems, o_sitems, o_off, o_rk, o_nm, o_gs, o_gd, o_go, o_perm, o_scr, o_sscr, total;
+  size_t o_items, o_mitems, o_bitems, o_sitems, o_off, o_rk, o_nm, o_gs, o_gd, o_go, o_perm, o_scr, o_sscr, o_tsoff,
+      o_titems, total;
 };
 
 int bucket_of(int r) {
@@ -330,6 +341,36 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
     for (size_t w = 0; w < its.size(); ++w)
       for (int x = 0; x < 8; ++x) P->mitems[w * 8 + x] = its[w].v[x];
     P->nmitems = (int)its.size();
+    // tensor-core adjoint: every tile keeps both sweep directions' partials (d interfaces
+    // each, two orientations); one gradient item per (tile, core, side), largest first
+    struct Gi {
+      double cost;
+      int v[4];
+    };
+    std::vector<Gi> gis;
+    long long u = 0;
+    P->tsoff.resize(its.size());
+    for (size_t w = 0; w < its.size(); ++w) {
+      const int g = its[w].v[0], d = P->gd[g], RA = its[w].v[5], RB = its[w].v[7];
+      P->tsoff[w] = u;
+      u += 4LL * d;
+      for (int k = 0; k < d; ++k)
+        for (int side = 0; side < 2; ++side) {
+          Gi gi;
+          gi.cost = (double)P->nmodes[(size_t)g * dmax + k] * (128.0 + (side ? RA : RB));
+          gi.v[0] = (int)w;
+          gi.v[1] = k;
+          gi.v[2] = side;
+          gi.v[3] = 0;
+          gis.push_back(gi);
+        }
+    }
+    std::stable_sort(gis.begin(), gis.end(), [](const Gi& x, const Gi& y) { return x.cost > y.cost; });
+    P->titems.resize(gis.size() * 4);
+    for (size_t w = 0; w < gis.size(); ++w)
+      for (int x = 0; x < 4; ++x) P->titems[w * 4 + x] = gis[w].v[x];
+    P->ntitems = (int)gis.size();
+    P->tunits = u;
   }
   // adjoint tiles (seven partial tiles per pair). Runs of rank-sorted objects grow (side at
   // most 16) while their square tile fits a full-size CTA (512 threads, one per SM); a tile
@@ -460,6 +501,8 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
   P->o_perm = o; o += a256(sizeof(int) * P->perm.size());
   P->o_scr = o; o += a256(sizeof(float) * (size_t)P->bstride * P->bgrid);
   P->o_sscr = o; o += a256(sizeof(float) * (size_t)P->sstride * P->sgrid);
+  P->o_tsoff = o; o += a256(sizeof(long long) * P->tsoff.size());
+  P->o_titems = o; o += a256(sizeof(int) * P->titems.size());
   P->total = o;
   return T3F_OK;
 }
@@ -494,7 +537,9 @@ t3f_status gg_tables_upload(const Plan& P, char* w, cudaStream_t s) {
              {P.o_gs, P.gs.data(), sizeof(int) * P.gs.size()},
              {P.o_gd, P.gd.data(), sizeof(int) * P.gd.size()},
              {P.o_go, P.gout.data(), sizeof(long long) * P.gout.size()},
-             {P.o_perm, P.perm.data(), sizeof(int) * P.perm.size()}};
+             {P.o_perm, P.perm.data(), sizeof(int) * P.perm.size()},
+             {P.o_tsoff, P.tsoff.data(), sizeof(long long) * P.tsoff.size()},
+             {P.o_titems, P.titems.data(), sizeof(int) * P.titems.size()}};
   for (const Cp& c : cps)
     if (c.bytes && cudaMemcpyAsync(w + c.off, c.src, c.bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
       return T3F_ERR_CUDA;
@@ -510,6 +555,23 @@ extern "C" size_t t3f_gram_groups_workspace_size(const t3f_tt_ragged* X, int32_t
   Plan P;
   if (build_plan(X, ngroups, gstart, tiles, &P) != T3F_OK) return 0;
   return P.total;
+}
+
+// Scratch of the tensor-core adjoint: every slot orientation is a 128 x 128 operand of the
+// math's element type.
+size_t gg_tc_scratch(const Plan& P, int math) {
+  const size_t es = math == T3F_MATH_TF32 ? 4 : 2;
+  return (size_t)P.tunits * 128u * 128u * es;
+}
+
+extern "C" size_t t3f_gram_groups_backward_workspace_size(const t3f_tt_ragged* X, int32_t ngroups,
+                                                          const int32_t* gstart, const int32_t* tiles,
+                                                          int32_t math) {
+  Plan P;
+  if (build_plan(X, ngroups, gstart, tiles, &P) != T3F_OK) return 0;
+  if (math == T3F_MATH_FP32) return P.total;
+  if (math != T3F_MATH_TF32 && math != T3F_MATH_BF16) return 0;
+  return P.total + gg_tc_scratch(P, math);
 }
 
 extern "C" t3f_status t3f_gram_groups_prepare(const t3f_tt_ragged* X, int32_t ngroups, const int32_t* gstart,
@@ -561,11 +623,13 @@ extern "C" t3f_status t3f_gram_groups(const t3f_tt_ragged* X, int32_t ngroups, c
 }
 
 extern "C" t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t ngroups, const int32_t* gstart,
-                                               const int32_t* tiles, const float* dout, float* dcores, void* ws,
-                                               size_t ws_bytes, t3f_stream_t stream) {
+                                               const int32_t* tiles, int32_t math, const float* dout, float* dcores,
+                                               void* ws, size_t ws_bytes, t3f_stream_t stream) {
   Plan P;
   T3F_CHECK(build_plan(X, ngroups, gstart, tiles, &P));
-  T3F_CHECK(check_ws(ws, ws_bytes, P.total));
+  if (math != T3F_MATH_FP32 && math != T3F_MATH_TF32 && math != T3F_MATH_BF16) return T3F_ERR_ARG;
+  if (math == T3F_MATH_TF32 && X->dtype != T3F_F32) return T3F_ERR_DTYPE;
+  T3F_CHECK(check_ws(ws, ws_bytes, P.total + (math == T3F_MATH_FP32 ? 0 : gg_tc_scratch(P, math))));
   if (!dout || !dcores) return T3F_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   char* w = static_cast<char*>(ws);
@@ -581,6 +645,19 @@ extern "C" t3f_status t3f_gram_groups_backward(const t3f_tt_ragged* X, int32_t n
     }
   }
   if (cudaMemsetAsync(dcores, 0, sizeof(float) * nel, s) != cudaSuccess) return T3F_ERR_CUDA;
+  if (math != T3F_MATH_FP32) {
+    // header words: 0 error, 5 and 6 the sweep and gradient list heads
+    int* hw = reinterpret_cast<int*>(w);
+    if (cudaMemsetAsync(hw, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
+    if (cudaMemsetAsync(hw + 5, 0, 2 * sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
+    return launch_gram_tc_backward_list(
+        math, X->cores, X->dtype, P.dmax, reinterpret_cast<const long long*>(w + P.o_off),
+        reinterpret_cast<const int*>(w + P.o_rk), reinterpret_cast<const int*>(w + P.o_nm),
+        reinterpret_cast<const int*>(w + P.o_mitems), P.nmitems, reinterpret_cast<const int*>(w + P.o_titems),
+        P.ntitems, hw + 5, reinterpret_cast<const int*>(w + P.o_gs), reinterpret_cast<const int*>(w + P.o_gd),
+        reinterpret_cast<const long long*>(w + P.o_go), reinterpret_cast<const int*>(w + P.o_perm), dout, dcores,
+        w + P.total, reinterpret_cast<const long long*>(w + P.o_tsoff), hw, s);
+  }
   // list heads: header word 2 (full-size CTAs) and word 4 (half-size CTAs)
   int* head = reinterpret_cast<int*>(w + 2 * sizeof(int));
   int* shead = reinterpret_cast<int*>(w + 4 * sizeof(int));

@@ -18,13 +18,12 @@
 #include <algorithm>
 #include <string.h>
 
-#include "t3f_internal.cuh"
+#include "gram_mma.cuh"
 
 namespace t3f {
 
 namespace {
 
-constexpr uint32_t kLBO = 144;
 constexpr int kMmaThreads = 256;
 constexpr uint32_t kTmemCols = 256;  // T at columns 0..127, D at 128..255
 constexpr uint32_t kSkew = 64;  // extra bytes between consecutive operands (16-bank shift)
@@ -80,173 +79,13 @@ struct GramMmaArgs {
   const int* items;           // [item][8]: group, a0, na, b0, nb, RA, sym, RB
   int nitems;
   int* head;                  // work-list counter
+  // adjoint sweeps (k_gram_mma_sweeps): the partials of every interface go to scratch slots
+  char* scr;                  // scratch base
+  const long long* soff;      // work-list mode: first slot orientation of item w (128 x 128 operands)
+  long long sstride;          // uniform mode: slot orientations of one tile
+  const float* gcot;          // cotangent: work list [group][S][S] (gout_off, perm); uniform dG
+  int ldg;                    // uniform: row stride of dG
 };
-
-template <int KIND>
-struct OpT;
-// TF32: 4-byte elements rounded to nearest (ties away) before the tensor core reads them
-template <>
-struct OpT<0> {
-  static constexpr int ES = 4;
-  static constexpr uint32_t FMT = 2;
-  static constexpr int KI = 8;  // K per instruction
-  static __device__ __forceinline__ void st(char* p, float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    *reinterpret_cast<uint32_t*>(p) = r;
-  }
-  static __device__ __forceinline__ uint32_t cv(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return r;
-  }
-  static __device__ __forceinline__ uint4 pack(const float (&v)[4]) {
-    return make_uint4(cv(v[0]), cv(v[1]), cv(v[2]), cv(v[3]));
-  }
-};
-template <>
-struct OpT<1> {
-  static constexpr int ES = 2;
-  static constexpr uint32_t FMT = 1;
-  static constexpr int KI = 16;
-  static __device__ __forceinline__ void st(char* p, float v) {
-    *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
-  }
-  static __device__ __forceinline__ uint32_t cv2(float lo, float hi) {
-    const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&b);
-  }
-  static __device__ __forceinline__ uint4 pack(const float (&v)[8]) {
-    return make_uint4(cv2(v[0], v[1]), cv2(v[2], v[3]), cv2(v[4], v[5]), cv2(v[6], v[7]));
-  }
-};
-
-// byte offset of element (row r, column k) of a K-major operand whose rows are 8-row groups SBO apart
-template <int ES>
-__device__ __forceinline__ uint32_t eoff(int r, int k, uint32_t sbo) {
-  constexpr int T = 16 / ES;
-  return (uint32_t)(r >> 3) * sbo + (uint32_t)(k / T) * kLBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k % T) * ES;
-}
-
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kLBO >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// D = F32, A and B of format fmt, both K-major, M = 128, N = n
-__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, uint32_t n) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
-}
-
-template <int KIND>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  if constexpr (KIND == 0) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.b32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the barrier phase with a bound of about one second; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > (1ll << 31)) return false;
-  return true;
-}
-
-__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void async_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 32 lanes x 16 consecutive FP32 columns (lane = thread's row of the warp's lane quarter)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-template <typename ST>
-__device__ __forceinline__ float ldc(const void* p, long long i) {
-  return ldf<ST>(static_cast<const ST*>(p), i);
-}
-
-// Raw bits of one stored element (F32 or BF16), converted only when the slice is packed, so
-// the loads of a slice stay in flight while the products run.
-template <typename ST>
-__device__ __forceinline__ uint32_t ld_raw(const ST* p);
-template <>
-__device__ __forceinline__ uint32_t ld_raw<float>(const float* p) { return __float_as_uint(__ldg(p)); }
-template <>
-__device__ __forceinline__ uint32_t ld_raw<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p));
-}
-
-// T raw elements -> one 16-byte operand row (TF32: 4 x 4 bytes, BF16: 8 x 2 bytes)
-template <int KIND, typename ST, int T>
-__device__ __forceinline__ uint4 pack_raw(const uint32_t (&v)[T]) {
-  if constexpr (KIND == 0) {
-    return OpT<0>::pack({__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]), __uint_as_float(v[3])});
-  } else if constexpr (sizeof(ST) == 2) {
-    return make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16));
-  } else {
-    return make_uint4(OpT<1>::cv2(__uint_as_float(v[0]), __uint_as_float(v[1])),
-                      OpT<1>::cv2(__uint_as_float(v[2]), __uint_as_float(v[3])),
-                      OpT<1>::cv2(__uint_as_float(v[4]), __uint_as_float(v[5])),
-                      OpT<1>::cv2(__uint_as_float(v[6]), __uint_as_float(v[7])));
-  }
-}
-
-// Two 16-lane x 8-column TMEM loads (columns c and c + 8 of lanes L..L+15): thread t gets
-// lanes L + t/4 and L + 8 + t/4, columns 2(t%4) and 2(t%4)+1 of each 8-column block.
-__device__ __forceinline__ void tmem_ld_16x16(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%8];\n"
-      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%4,%5,%6,%7}, [%9];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-      : "r"(taddr), "r"(taddr + 8u)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ uint32_t bf2(uint32_t lo, uint32_t hi) {
-  const __nv_bfloat162 b = __floats2bfloat162_rn(__uint_as_float(lo), __uint_as_float(hi));
-  return *reinterpret_cast<const uint32_t*>(&b);
-}
 
 // BF16 transposing epilogue: TMEM rows (x, kappa) (x = row / RL) and columns m = 0..127 go to
 // operand x at (row m, K = kappa) of a K-major BF16 operand array (operand stride BIG, row
@@ -308,15 +147,62 @@ struct MmaState {
   bool pending1, pending2;  // a committed product batch not yet waited for
   int bad;                  // this thread saw a wait run out
   long long* s_base;        // [2 core parities][2 sides][8 objects]
-  int* s_r0;
-  int* s_r1;
+  int* s_r0;                // K (left-rank) limit of the swept core
+  int* s_r1;                // row (right-rank) limit
+  int* s_cs;                // element strides of the slice operand: K index, row index, mode index
+  int* s_rs;
+  int* s_is;
+  float* s_g;               // adjoint sweeps: cotangent of pair (a, b) at [a * 8 + b]
 };
+
+// Adjoint sweeps: the partial D (TMEM columns from tcol; lanes (b, be), columns (a, al)) goes
+// to one scratch slot in two orientations, each a 128 x 128 K-major operand with 16-byte core
+// matrices packed along K (LBO 128 bytes, SBO 16 * 128 bytes per 8 rows):
+//   o1: rows (b, be), K = (a, al)          o0: rows (a, al), K = (b, be)
+// rounded to the operand type and scaled by the pair's cotangent when sg is given.
+template <int KIND, int RA, int RB>
+__device__ __forceinline__ void store_partial(uint32_t tcol, char* o0, char* o1, const float* sg) {
+  using O = OpT<KIND>;
+  constexpr int ES = O::ES, T = 16 / ES;
+  constexpr uint32_t SBO = (128u / T) * 128u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
+  const int row = q * 32 + lane, b = row / RB;
+#pragma unroll
+  for (int cc = 0; cc < 64; cc += 16) {
+    const int c0 = h * 64 + cc;
+    float v[16];
+    tmem_ld16(tcol + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+    if (sg) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] *= sg[((c0 + j) / RA) * 8 + b];
+    }
+#pragma unroll
+    for (int ch = 0; ch < 16 / T; ++ch) {
+      float u[T];
+#pragma unroll
+      for (int t = 0; t < T; ++t) u[t] = v[ch * T + t];
+      *reinterpret_cast<uint4*>(o1 + (uint32_t)(row >> 3) * SBO + (uint32_t)((c0 + ch * T) / T) * 128u +
+                                (uint32_t)(row & 7) * 16u) = O::pack(u);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int c = c0 + j;
+      O::st(o0 + (uint32_t)(c >> 3) * SBO + (uint32_t)(row / T) * 128u + (uint32_t)(c & 7) * 16u +
+                (uint32_t)(row % T) * ES,
+            v[j]);
+    }
+  }
+}
 
 // One tile: na x nb pairs (a0.., b0..) of one group (or of the uniform batches), d cores.
 // Returns false (block-uniformly) when a tensor-core wait ran out.
+// Adjoint sweeps (slots != nullptr): dir 0 runs the left sweep and stores M_0 .. M_{d-1};
+// dir 1 runs the same recursion over the cores in reverse order with transposed slices
+// (R_k = sum_i A_k,i R_{k+1} B_k,i^T) and stores R_1 .. R_d. Slot j of direction dir holds
+// interface j (dir 0) or j + 1 (dir 1); M is stored scaled by the pair's cotangent.
 template <int KIND, int RA, int RB, typename ST>
 __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int grp, int a0, int na, int b0, int nb,
-                              int sym, int d) {
+                              int sym, int d, int dir = 0, char* slots = nullptr) {
   using O = OpT<KIND>;
   constexpr int ES = O::ES;
   constexpr int T = 16 / ES;
@@ -344,36 +230,80 @@ __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int 
   long long(*s_base)[2][8] = reinterpret_cast<long long(*)[2][8]>(st.s_base);
   int(*s_r0)[2][8] = reinterpret_cast<int(*)[2][8]>(st.s_r0);
   int(*s_r1)[2][8] = reinterpret_cast<int(*)[2][8]>(st.s_r1);
+  int(*s_cs)[2][8] = reinterpret_cast<int(*)[2][8]>(st.s_cs);
+  int(*s_rs)[2][8] = reinterpret_cast<int(*)[2][8]>(st.s_rs);
+  int(*s_is)[2][8] = reinterpret_cast<int(*)[2][8]>(st.s_is);
+  constexpr uint32_t kSlot = 128u * 128u * ES;  // bytes of one orientation of a slot
 
-  auto nmode = [&](int k) { return g.mode == 0 ? g.A.n[k] : g.nmodes[grp * g.dmax + k]; };
+  // swept core k is stored core kc (reversed for dir 1)
+  auto nmode = [&](int k) {
+    const int kc = dir ? d - 1 - k : k;
+    return g.mode == 0 ? g.A.n[kc] : g.nmodes[grp * g.dmax + kc];
+  };
   // per-object core offsets and ranks of core k into parity slot par (missing objects: rank 0)
+  // (the slice operand's rows are the swept core's right-rank index, K its left-rank index;
+  // reversed, the stored core's left and right ranks trade places)
   auto fill_info = [&](int k, int par) {
     if (tid < 16) {
       const int side = tid / 8, o = tid % 8, cnt = side ? nb : na, o0 = side ? b0 : a0;
+      const int kc = dir ? d - 1 - k : k;
       long long base = 0;
-      int r0 = 0, r1 = 0;
+      int rl = 0, rr = 0;
       if (o < cnt) {
         if (g.mode == 0) {
           const TTV& V = side ? g.B : g.A;
-          base = V.off[k] + (long long)(o0 + o) * V.osz[k];
-          r0 = V.r[k];
-          r1 = V.r[k + 1];
+          base = V.off[kc] + (long long)(o0 + o) * V.osz[kc];
+          rl = V.r[kc];
+          rr = V.r[kc + 1];
         } else {
           const int pos = o0 + o;
-          base = g.off[(long long)pos * g.dmax + k];
-          r0 = g.rk[(long long)pos * (g.dmax + 1) + k];
-          r1 = g.rk[(long long)pos * (g.dmax + 1) + k + 1];
+          base = g.off[(long long)pos * g.dmax + kc];
+          rl = g.rk[(long long)pos * (g.dmax + 1) + kc];
+          rr = g.rk[(long long)pos * (g.dmax + 1) + kc + 1];
         }
       }
+      const int n = nmode(k), row_stride = n * rr;
       s_base[par][side][o] = base;
-      s_r0[par][side][o] = r0;
-      s_r1[par][side][o] = r1;
+      s_r0[par][side][o] = dir ? rr : rl;
+      s_r1[par][side][o] = dir ? rl : rr;
+      s_cs[par][side][o] = dir ? 1 : row_stride;
+      s_rs[par][side][o] = dir ? row_stride : 1;
+      s_is[par][side][o] = rr;
     }
   };
   // M_0 = 1 for every pair: zero all M_b, then element (row a*RA, col 0) of every M_b
   for (uint32_t e = (uint32_t)tid * 16u; e < TB * BIGB; e += kMmaThreads * 16u)
     *reinterpret_cast<uint4*>(mop + e) = make_uint4(0u, 0u, 0u, 0u);
   fill_info(0, 0);
+  if (slots) {
+    // the pairs' cotangents, and the boundary slot: M_0 (scaled) or R_d, one at (a*RA, b*RB)
+    if (tid < 64) {
+      const int a = tid / 8, b = tid % 8;
+      float gv = 0.f;
+      if (a < na && b < nb) {
+        if (g.mode == 0) {
+          gv = g.swap ? g.gcot[(long long)(b0 + b) * g.ldg + (a0 + a)] : g.gcot[(long long)(a0 + a) * g.ldg + (b0 + b)];
+        } else {
+          const long long S = g.gstart[grp + 1] - g.gstart[grp];
+          const long long la = g.perm[a0 + a], lb = g.perm[b0 + b];
+          const float* o = g.gcot + g.gout_off[grp];
+          gv = o[la * S + lb] + (sym ? o[lb * S + la] : 0.f);
+        }
+      }
+      st.s_g[tid] = gv;
+    }
+    char* const o0 = slots + (size_t)((dir * d + (dir ? d - 1 : 0)) * 2) * kSlot;
+    for (uint32_t e = (uint32_t)tid * 16u; e < 2u * kSlot; e += kMmaThreads * 16u)
+      *reinterpret_cast<uint4*>(o0 + e) = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    if (tid < TA * TB) {
+      constexpr uint32_t SB = (128u / T) * 128u;
+      const int a = tid / TB, b = tid % TB, ra = a * RA, rb = b * RB;
+      const float v = (a < na && b < nb) ? (dir ? 1.f : st.s_g[a * 8 + b]) : 0.f;
+      O::st(o0 + (uint32_t)(ra >> 3) * SB + (uint32_t)(rb / T) * 128u + (uint32_t)(ra & 7) * 16u, v);
+      O::st(o0 + kSlot + (uint32_t)(rb >> 3) * SB + (uint32_t)(ra / T) * 128u + (uint32_t)(rb & 7) * 16u, v);
+    }
+  }
   __syncthreads();
   if (tid < TA * TB) O::st(mop + (tid / TA) * BIGB + eoff<ES>((tid % TA) * RA, 0, SBOB), 1.0f);
 
@@ -381,12 +311,13 @@ __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int 
   // object o = (suX + j*USX) / KGX, columns c = ((suX + j*USX) % KGX) * T + t, row srX
   uint32_t pb[UPB][T], pa[UPA][T];
   auto load_slice = [&](int k, int i) {
-    const int par = k & 1, n = nmode(k);
+    const int par = k & 1;
 #pragma unroll
     for (int j = 0; j < UPB; ++j) {
       const int w = suB + j * USB, o = w / KGB, c0 = (w % KGB) * T;
-      const int r0 = s_r0[par][1][o], r1 = s_r1[par][1][o], stp = n * r1;
-      const ST* ptr = static_cast<const ST*>(Bp) + s_base[par][1][o] + (long long)c0 * stp + i * r1 + srB;
+      const int r0 = s_r0[par][1][o], r1 = s_r1[par][1][o], stp = s_cs[par][1][o];
+      const ST* ptr = static_cast<const ST*>(Bp) + s_base[par][1][o] + (long long)c0 * stp +
+                      (long long)i * s_is[par][1][o] + (long long)srB * s_rs[par][1][o];
       const bool rok = srB < r1;
 #pragma unroll
       for (int t = 0; t < T; ++t) {
@@ -397,8 +328,9 @@ __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int 
 #pragma unroll
     for (int j = 0; j < UPA; ++j) {
       const int w = suA + j * USA, o = w / KGA, c0 = (w % KGA) * T;
-      const int r0 = s_r0[par][0][o], r1 = s_r1[par][0][o], stp = n * r1;
-      const ST* ptr = static_cast<const ST*>(Ap) + s_base[par][0][o] + (long long)c0 * stp + i * r1 + srA;
+      const int r0 = s_r0[par][0][o], r1 = s_r1[par][0][o], stp = s_cs[par][0][o];
+      const ST* ptr = static_cast<const ST*>(Ap) + s_base[par][0][o] + (long long)c0 * stp +
+                      (long long)i * s_is[par][0][o] + (long long)srA * s_rs[par][0][o];
       const bool rok = srA < r1;
 #pragma unroll
       for (int t = 0; t < T; ++t) {
@@ -490,10 +422,15 @@ __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int 
     st.ph2 ^= 1u;
     st.pending2 = false;
     tc_after();
-    // ---- epilogue 2: D (rows (b, bp), cols (a, ap)) -> M_b[(a, ap), bp], or the Gram entries
+    // ---- epilogue 2: D (rows (b, bp), cols (a, ap)) -> M_b[(a, ap), bp], or the Gram entries;
+    // the adjoint sweeps also store D to its slot (after core k: interface k + 1, or d - 1 - k)
     if (k + 1 < d) {
+      if (slots) {
+        char* const o0 = slots + (size_t)((dir * d + (dir ? d - 2 - k : k + 1)) * 2) * kSlot;
+        store_partial<KIND, RA, RB>(st.tmem + 128u, o0, o0 + kSlot, dir ? nullptr : st.s_g);
+      }
       epi_transpose<KIND, RB, SBOB, BIGB>(st.tmem + 128u, mop);
-    } else {
+    } else if (!slots) {
       const int b = row / RB, bp = row % RB;
 #pragma unroll
       for (int cc = 0; cc < 64; cc += 16) {
@@ -531,8 +468,8 @@ __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int 
 
 template <int KIND, int RA, int RB, typename ST>
 __device__ __forceinline__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, int a0, int na,
-                                         int b0, int nb, int sym, int d) {
-  return mma_tile_sync<KIND, RA, RB, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d);
+                                         int b0, int nb, int sym, int d, int dir = 0, char* slots = nullptr) {
+  return mma_tile_sync<KIND, RA, RB, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots);
 }
 
 // Common prologue / epilogue of the kernels: TMEM allocation, barriers, and the release of
@@ -582,65 +519,85 @@ __host__ __device__ constexpr int mma_ctas_per_sm(int es, int RA, int RB) {
   return mma_layout(es, RA, RB).total + 1024u <= kSmemCap / 2u ? 2 : 1;
 }
 
-// Uniform batches: one tile per CTA, fixed (RA, RB).
+// Per-CTA state of the sweep kernels besides the dynamic operand area.
+struct MmaShared {
+  uint64_t bar[2];
+  long long base[2][2][8];
+  int r0[2][2][8], r1[2][2][8], cs[2][2][8], rs[2][2][8], is[2][2][8];
+  float gv[64];
+  int item[8];
+  uint32_t tmem;
+  int valid, wi, dir;
+};
+
+__device__ __forceinline__ void mma_bind(MmaState& st, MmaShared& sh) {
+  st.s_base = &sh.base[0][0][0];
+  st.s_r0 = &sh.r0[0][0][0];
+  st.s_r1 = &sh.r1[0][0][0];
+  st.s_cs = &sh.cs[0][0][0];
+  st.s_rs = &sh.rs[0][0][0];
+  st.s_is = &sh.is[0][0][0];
+  st.s_g = sh.gv;
+}
+
+// Uniform batches: one tile per CTA, fixed (RA, RB). With g.scr set (adjoint sweeps) the grid
+// is twice the tile count: the second half runs the reversed sweeps.
 template <int KIND, int RA, int RB, typename ST>
 __global__ void __launch_bounds__(kMmaThreads, mma_ctas_per_sm(OpT<KIND>::ES, RA, RB)) k_gram_mma(const __grid_constant__ GramMmaArgs g) {
   extern __shared__ __align__(128) char sm[];
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ uint32_t s_tmem;
-  __shared__ long long s_base[2][2][8];
-  __shared__ int s_r0[2][2][8], s_r1[2][2][8];
+  __shared__ __align__(16) MmaShared sh;
   MmaState st;
-  st.s_base = &s_base[0][0][0];
-  st.s_r0 = &s_r0[0][0][0];
-  st.s_r1 = &s_r1[0][0][0];
-  mma_setup(st, s_bar, &s_tmem, sm, g.smem_bytes);
+  mma_bind(st, sh);
+  mma_setup(st, sh.bar, &sh.tmem, sm, g.smem_bytes);
   constexpr int TA = 128 / RA, TB = 128 / RB;
-  const int ntb = (g.B.batch + TB - 1) / TB;
-  const int a0 = (blockIdx.x / ntb) * TA, b0 = (blockIdx.x % ntb) * TB;
+  const int ntb = (g.B.batch + TB - 1) / TB, nta = (g.A.batch + TA - 1) / TA;
+  const int dir = g.scr ? (int)(blockIdx.x / (unsigned)(nta * ntb)) : 0;
+  const int w = (int)(blockIdx.x % (unsigned)(nta * ntb));
+  const int a0 = (w / ntb) * TA, b0 = (w % ntb) * TB;
+  char* const slots = g.scr ? g.scr + (size_t)w * (size_t)g.sstride * (128u * 128u * OpT<KIND>::ES) : nullptr;
   const bool ok = mma_tile<KIND, RA, RB, ST>(g, sm, st, 0, a0, min(TA, g.A.batch - a0), b0,
-                                             min(TB, g.B.batch - b0), 0, g.A.d);
+                                             min(TB, g.B.batch - b0), 0, g.A.d, dir, slots);
   mma_teardown(g, st, !ok);
 }
 
-// Work-list mode: persistent CTAs drain tiles of any of the six shapes RA <= RB.
+// Work-list mode: persistent CTAs drain tiles of any of the six shapes RA <= RB. With g.scr set
+// (adjoint sweeps) the counter runs over twice the items: item w in both directions.
 template <int KIND, typename ST>
 __global__ void __launch_bounds__(kMmaThreads, 1) k_gram_mma_list(const __grid_constant__ GramMmaArgs g) {
   extern __shared__ __align__(128) char sm[];
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ uint32_t s_tmem;
-  __shared__ long long s_base[2][2][8];
-  __shared__ int s_r0[2][2][8], s_r1[2][2][8];
-  __shared__ int s_item[8];
-  __shared__ int s_valid;
+  __shared__ __align__(16) MmaShared sh;
   MmaState st;
-  st.s_base = &s_base[0][0][0];
-  st.s_r0 = &s_r0[0][0][0];
-  st.s_r1 = &s_r1[0][0][0];
-  mma_setup(st, s_bar, &s_tmem, sm, g.smem_bytes);
+  mma_bind(st, sh);
+  mma_setup(st, sh.bar, &sh.tmem, sm, g.smem_bytes);
   const int tid = threadIdx.x;
+  const int total = g.scr ? 2 * g.nitems : g.nitems;
   bool ok = true;
   while (ok) {
     __syncthreads();
     if (tid == 0) {
       const int w = atomicAdd(g.head, 1);
-      s_valid = w < g.nitems ? 1 : 0;
-      if (w < g.nitems)
-        for (int x = 0; x < 8; ++x) s_item[x] = g.items[w * 8 + x];
+      sh.valid = w < total ? 1 : 0;
+      if (w < total) {
+        const int wi = w % g.nitems;
+        for (int x = 0; x < 8; ++x) sh.item[x] = g.items[wi * 8 + x];
+        sh.wi = wi;
+        sh.dir = w >= g.nitems ? 1 : 0;
+      }
     }
     __syncthreads();
-    if (!s_valid) break;
-    const int grp = s_item[0], a0 = s_item[1], na = s_item[2], b0 = s_item[3], nb = s_item[4], RA = s_item[5],
-              sym = s_item[6], RB = s_item[7];
-    const int d = g.gd[grp];
+    if (!sh.valid) break;
+    const int grp = sh.item[0], a0 = sh.item[1], na = sh.item[2], b0 = sh.item[3], nb = sh.item[4], RA = sh.item[5],
+              sym = sh.item[6], RB = sh.item[7];
+    const int dir = sh.dir, d = g.gd[grp];
+    char* const slots = g.scr ? g.scr + (size_t)g.soff[sh.wi] * (128u * 128u * OpT<KIND>::ES) : nullptr;
     const int key = RA * 1000 + RB;
     switch (key) {
-      case 16016: ok = mma_tile<KIND, 16, 16, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
-      case 16032: ok = mma_tile<KIND, 16, 32, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
-      case 16064: ok = mma_tile<KIND, 16, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
-      case 32032: ok = mma_tile<KIND, 32, 32, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
-      case 32064: ok = mma_tile<KIND, 32, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
-      default: ok = mma_tile<KIND, 64, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d); break;
+      case 16016: ok = mma_tile<KIND, 16, 16, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      case 16032: ok = mma_tile<KIND, 16, 32, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      case 16064: ok = mma_tile<KIND, 16, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      case 32032: ok = mma_tile<KIND, 32, 32, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      case 32064: ok = mma_tile<KIND, 32, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      default: ok = mma_tile<KIND, 64, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
     }
   }
   mma_teardown(g, st, !ok);
@@ -654,7 +611,7 @@ t3f_status launch_mma(const GramMmaArgs& g0, cudaStream_t s) {
   g.smem_bytes = mma_layout(OpT<KIND>::ES, RA, RB).total;
   g.mode = 0;
   constexpr int TA = 128 / RA, TB = 128 / RB;
-  const long long grid = (long long)((g.A.batch + TA - 1) / TA) * ((g.B.batch + TB - 1) / TB);
+  const long long grid = (long long)((g.A.batch + TA - 1) / TA) * ((g.B.batch + TB - 1) / TB) * (g.scr ? 2 : 1);
   if (grid <= 0) return T3F_OK;
   if (grid > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
   auto kern = k_gram_mma<KIND, RA, RB, ST>;
@@ -698,7 +655,8 @@ t3f_status launch_list(const GramMmaArgs& g0, cudaStream_t s) {
     return T3F_ERR_CUDA;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMmaThreads, g.smem_bytes) != cudaSuccess)
     return T3F_ERR_CUDA;
-  const int grid = std::max(1, std::min(g.nitems, sms * std::max(per_sm, 1)));
+  const int total = g.scr ? 2 * g.nitems : g.nitems;
+  const int grid = std::max(1, std::min(total, sms * std::max(per_sm, 1)));
   kern<<<grid, kMmaThreads, g.smem_bytes, s>>>(g);
   return launch_status();
 }
@@ -727,6 +685,64 @@ t3f_status launch_gram_mma_list(int math, const void* cores, int dtype, int dmax
   g.nitems = nitems;
   g.head = head;
   g.err = err;
+  if (math == T3F_MATH_TF32) {
+    if (dtype != T3F_F32) return T3F_ERR_DTYPE;
+    return launch_list<0, float>(g, s);
+  }
+  if (dtype == T3F_BF16) return launch_list<1, __nv_bfloat16>(g, s);
+  return launch_list<1, float>(g, s);
+}
+
+// Adjoint sweeps over uniform batches (A the side of the smaller padded rank; swap = the
+// caller's batches were exchanged, dG stays in the caller's [a][b] order with row stride ldg):
+// both directions of every tile store their partials into scr, sstride slot orientations
+// per tile.
+t3f_status run_gram_mma_sweeps(const TTV& A, const TTV& B, int swap, const float* dG, int ldg, int math, char* scr,
+                               long long sstride, int* err, cudaStream_t s) {
+  GramMmaArgs g;
+  memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.B = B;
+  g.swap = swap;
+  g.gcot = dG;
+  g.ldg = ldg;
+  g.scr = scr;
+  g.sstride = sstride;
+  g.err = err;
+  const int ra = pad_pow2_16(A.rmax), rb = pad_pow2_16(B.rmax);
+  if (math == T3F_MATH_TF32) {
+    if (A.dtype != T3F_F32) return T3F_ERR_DTYPE;
+    return dispatch_r<0, float>(ra, rb, g, s);
+  }
+  if (A.dtype == T3F_BF16) return dispatch_r<1, __nv_bfloat16>(ra, rb, g, s);
+  return dispatch_r<1, float>(ra, rb, g, s);
+}
+
+// Adjoint sweeps over the tensor-core tile list of a ragged collection: item w in both
+// directions (the counter runs to 2 nitems), slots of item w from soff[w]; dout holds the
+// groups' cotangents like the forward's output. heads[0] must be zero.
+t3f_status launch_gram_mma_sweeps_list(int math, const void* cores, int dtype, int dmax, const long long* off,
+                                       const int* rk, const int* nmodes, const int* items, int nitems, int* heads,
+                                       const int* gstart, const int* gd, const long long* gout_off, const int* perm,
+                                       const float* dout, char* scr, const long long* soff, int* err, cudaStream_t s) {
+  GramMmaArgs g;
+  memset(&g, 0, sizeof(g));
+  g.cores = cores;
+  g.off = off;
+  g.rk = rk;
+  g.dmax = dmax;
+  g.nmodes = nmodes;
+  g.gd = gd;
+  g.gstart = gstart;
+  g.perm = perm;
+  g.gout_off = gout_off;
+  g.gcot = dout;
+  g.items = items;
+  g.nitems = nitems;
+  g.head = heads;
+  g.err = err;
+  g.scr = scr;
+  g.soff = soff;
   if (math == T3F_MATH_TF32) {
     if (dtype != T3F_F32) return T3F_ERR_DTYPE;
     return launch_list<0, float>(g, s);

@@ -113,6 +113,12 @@ size_t ws_project(const TTV& U, const TTV& Z);
 size_t ws_tangent_gram(const TTV& A, const TTV& B);
 size_t ws_completion_hvp(const TTV& U, const TTV& V, long long N);
 
+// tensor-core Gram adjoint (gram_mma_bwd.cu): the sweeps' partial slots and the gradient products
+size_t gram_tc_bwd_tiles(const TTV& A, const TTV& B);
+long long gram_tc_bwd_slots(const TTV& A);
+size_t ws_gram_bwd_tc(const TTV& A, const TTV& B);
+t3f_status run_gram_tc_backward(const TTV& A, const TTV& B, const float* dG, float* dA, float* dB, int math,
+                                char* scr, int* err, cudaStream_t s);
 size_t ws_round(const TTV& X);
 
 // Deterministic two-level sum of nsplit partial arrays of `size` floats (tangent.cu); mid
