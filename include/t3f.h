@@ -216,6 +216,10 @@ t3f_status t3f_gather_backward(const t3f_tt* X, const int32_t* idx, int64_t N,
  *   C^k[(a*r_x+b), i, (a'*r_x+b')] = sum_j A^k[a,i,j,a'] x^k[b,j,b'],
  * so C has ranks r^A_k * r^x_k and modes m_k. A: TT-matrix (m != NULL), x: TT-vector with
  * n_k equal to A's column modes; C: F32 TT-vector descriptor of the product's shape.
+ * With one column mode 2, 4 or 8 on every core a persistent kernel runs the (pair, core)
+ * units, each unit's two cores fetched whole by TMA bulk copies one unit ahead. ws
+ * (optional, t3f_workspace_size(T3F_OP_MATVEC) bytes): its error word receives
+ * T3F_ERR_TIMEOUT if a copy's bounded wait runs out (see t3f_device_status).
  */
 t3f_status t3f_matvec(const t3f_tt* A, const t3f_tt* x, t3f_tt* C, void* ws,
                       size_t ws_bytes, t3f_stream_t stream);

@@ -281,7 +281,8 @@ def matvec(A: TT, x: TT) -> TT:
     P = max(A.batch, x.batch)
     ranks = [a * b for a, b in zip(A.ranks, x.ranks)]
     C = TT.empty(A.m, ranks, P, None, torch.float32, dev)
-    _check(_lib().t3f_matvec(_ref(A), _ref(x), _ref(C), None, 0, _stream(dev)), "t3f_matvec")
+    ws = _ws("matvec", A, x, 0, dev)
+    _check(_lib().t3f_matvec(_ref(A), _ref(x), _ref(C), _ptr(ws), ws.numel(), _stream(dev)), "t3f_matvec")
     return C
 
 

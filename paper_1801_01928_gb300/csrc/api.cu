@@ -141,7 +141,7 @@ extern "C" size_t t3f_workspace_size(int32_t op, const t3f_tt* a, const t3f_tt* 
     case T3F_OP_GATHER: return ws_gather(va, n_items, false);
     case T3F_OP_GATHER_BWD: return ws_gather(va, n_items, true);
     case T3F_OP_RGATHER_BWD: return ws_rgather(va, vb, n_items);
-    case T3F_OP_MATVEC: return 0;
+    case T3F_OP_MATVEC: return kWsHeader;
     case T3F_OP_MATVEC_BWD: return 0;
     case T3F_OP_ORTH: return ws_orth(va);
     case T3F_OP_PSUM: return ws_psum(va, vb, false);

@@ -18,12 +18,9 @@ struct MatvecArgs {
   TTV A, x, C;
   int bA, bx, P;       // batches; P = number of products
   int maxA, maxX;      // staged floats per core (max over k)
-  // specialised kernels: CTA units (pair, core k, rows a in [u * kMvRows, ...)); units of core
-  // k are ucum[k] .. ucum[k + 1] - 1 within a pair
-  int ucum[T3F_MAX_D + 1];
+  int* err;            // timeout word of the persistent kernel (nullable)
 };
 
-constexpr int kMvRows = 5;  // rows a of A's left rank per CTA of the specialised kernels
 
 __global__ void __launch_bounds__(256) k_matvec(const __grid_constant__ MatvecArgs a) {
   extern __shared__ float sm[];
@@ -74,57 +71,149 @@ __global__ void __launch_bounds__(256) k_matvec(const __grid_constant__ MatvecAr
   }
 }
 
-// Forward for column modes n = N and x's left rank r_x <= RB (the common shapes): a thread
-// owns positions q = (i, a', b') of the row block, keeps x[b, :, b'] for every b in registers,
-// and for every row a loads A[a, i, :, a'] once to write the r_x outputs (a, b), b < r_x:
-// about N + 2 instructions per output instead of a division chain per output.
-template <int N, int RB>
-__global__ void __launch_bounds__(256) k_matvec_n(const __grid_constant__ MatvecArgs a) {
-  extern __shared__ float sm[];
-  const int per = a.ucum[a.A.d];
-  const int p = blockIdx.x / per, u = blockIdx.x % per;
-  int k = 0;
-  while (u >= a.ucum[k + 1]) ++k;
-  const int al0 = (u - a.ucum[k]) * kMvRows;
+// Persistent forward for column modes n = N on every core: CTAs take (pair, core) units in
+// turn. The next unit's A and x cores arrive by TMA bulk copies -- each core whole, the copy
+// rounded out to 16-byte boundaries into a landing zone with slack -- in the other half of a
+// double buffer while the current unit's rows are written. A thread item is (position
+// q = (i, a', b') of the row block, group of four rows b of x): it keeps x[b, :, b'] of its
+// four b in registers and, for every row a, loads A[a, i, :, a'] once to write four outputs
+// (consecutive threads write consecutive addresses of four rows).
+constexpr int kMvGroup = 4;  // the full-group path below writes exactly four rows
+
+__device__ __forceinline__ uint32_t mv_s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ const float* mv_floor16(const float* p) {
+  return reinterpret_cast<const float*>(reinterpret_cast<uintptr_t>(p) & ~uintptr_t(15));
+}
+// bytes of the 16-byte-aligned range covering nfl floats from p
+__device__ __forceinline__ uint32_t mv_raw_bytes(const float* p, long long nfl) {
+  const uintptr_t b = reinterpret_cast<uintptr_t>(p), e = b + (uintptr_t)nfl * 4u;
+  return (uint32_t)(((e + 15) & ~uintptr_t(15)) - (b & ~uintptr_t(15)));
+}
+__device__ __forceinline__ bool mv_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, 2) k_matvec_p(const __grid_constant__ MatvecArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ __align__(8) uint64_t bar[2];
   const TTV& A = a.A;
   const TTV& X = a.x;
-  const int ra0 = A.r[k], ra1 = A.r[k + 1], rx0 = X.r[k], rx1 = X.r[k + 1];
-  const int m = A.m[k];
-  float* As = sm;             // [ra0][m][N][ra1]
-  float* Xs = sm + a.maxA;    // [rx0][N][rx1]
-  const float* Ap = static_cast<const float*>(A.p) + core_base(A, k, a.bA == 1 ? 0 : p);
-  const float* Xp = static_cast<const float*>(X.p) + core_base(X, k, a.bx == 1 ? 0 : p);
-  const int sa = ra0 * m * N * ra1, sx = rx0 * N * rx1;
-  for (int e = threadIdx.x; e < sa; e += blockDim.x) As[e] = __ldg(Ap + e);
-  for (int e = threadIdx.x; e < sx; e += blockDim.x) Xs[e] = __ldg(Xp + e);
+  const int d = A.d, units = a.P * d, tid = threadIdx.x;
+  const int lx_off = a.maxA + 8, half = lx_off + a.maxX + 8;  // floats, multiples of 4
+  auto a_ptr = [&](int u) {
+    return static_cast<const float*>(A.p) + core_base(A, u % d, a.bA == 1 ? 0 : u / d);
+  };
+  auto x_ptr = [&](int u) {
+    return static_cast<const float*>(X.p) + core_base(X, u % d, a.bx == 1 ? 0 : u / d);
+  };
+  auto issue = [&](int u, int b) {
+    const float* Ap = a_ptr(u);
+    const float* Xp = x_ptr(u);
+    const int k = u % d;
+    const uint32_t ba = mv_raw_bytes(Ap, A.osz[k]), bx = mv_raw_bytes(Xp, X.osz[k]);
+    const uint32_t bb = mv_s32(&bar[b]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(ba + bx) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     mv_s32(sm + b * half)),
+                 "l"(mv_floor16(Ap)), "r"(ba), "r"(bb)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     mv_s32(sm + b * half + lx_off)),
+                 "l"(mv_floor16(Xp)), "r"(bx), "r"(bb)
+                 : "memory");
+  };
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mv_s32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mv_s32(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if ((int)blockIdx.x < units) issue(blockIdx.x, 0);
+  }
   __syncthreads();
-  float* Cp = static_cast<float*>(a.C.p) + core_base(a.C, k, p);
-  const int rowlen = m * ra1 * rx1;
-  for (int q = threadIdx.x; q < rowlen; q += blockDim.x) {
-    const int i = q / (ra1 * rx1), c1 = q - i * (ra1 * rx1);
-    const int ap = c1 / rx1, bp = c1 - ap * rx1;
-    float xr[RB][N];
+  uint32_t ph0 = 0, ph1 = 0;
+  int b = 0;
+  for (int u = blockIdx.x; u < units; u += gridDim.x, b ^= 1) {
+    int good = 1;
+    if (tid == 0) good = mv_wait(mv_s32(&bar[b]), b ? ph1 : ph0) ? 1 : 0;
+    if (!__syncthreads_and(good)) {
+      // the copy did not land: report, wait once more (bounded) for it, and leave
+      if (tid == 0) {
+        if (a.err) atomicExch(a.err, (int)T3F_ERR_TIMEOUT);
+        mv_wait(mv_s32(&bar[b]), b ? ph1 : ph0);
+      }
+      return;
+    }
+    if (b) ph1 ^= 1u; else ph0 ^= 1u;
+    // prefetch the next unit into the other half (released by the previous iteration's barrier)
+    if (tid == 0 && u + (int)gridDim.x < units) issue(u + gridDim.x, b ^ 1);
+    const float* Ap = a_ptr(u);
+    const float* Xp = x_ptr(u);
+    const float* As = sm + b * half + ((reinterpret_cast<uintptr_t>(Ap) & 15) >> 2);
+    const float* Xs = sm + b * half + lx_off + ((reinterpret_cast<uintptr_t>(Xp) & 15) >> 2);
+    const int p = u / d, k = u % d;
+    const int ra0 = A.r[k], ra1 = A.r[k + 1], rx0 = X.r[k], rx1 = X.r[k + 1], m = A.m[k];
+    float* Cp = static_cast<float*>(a.C.p) + core_base(a.C, k, p);
+    const int L = m * ra1 * rx1, ng = (rx0 + kMvGroup - 1) / kMvGroup, AI = m * N * ra1, rowstep = rx0 * L;
+    for (int it = tid; it < L * ng; it += blockDim.x) {
+      const int g = it / L, q = it - g * L;
+      const int i = q / (ra1 * rx1), c1 = q - i * (ra1 * rx1);
+      const int ap = c1 / rx1, bp = c1 - ap * rx1, be0 = g * kMvGroup;
+      float xr[kMvGroup][N];
 #pragma unroll
-    for (int be = 0; be < RB; ++be)
+      for (int bb = 0; bb < kMvGroup; ++bb)
 #pragma unroll
-      for (int j = 0; j < N; ++j) xr[be][j] = be < rx0 ? Xs[(be * N + j) * rx1 + bp] : 0.0f;
-    const float* Ar = As + (i * N) * ra1 + ap;  // A[al, i, j, ap] at al * m * N * ra1 + j * ra1
-    float* cq = Cp + q;
-    const int al1 = min(ra0, al0 + kMvRows);
-    for (int al = al0; al < al1; ++al) {
-      float av[N];
+        for (int j = 0; j < N; ++j) xr[bb][j] = be0 + bb < rx0 ? Xs[((be0 + bb) * N + j) * rx1 + bp] : 0.0f;
+      const float* Ar = As + (i * N) * ra1 + ap;  // A[al, i, j, ap] at al * AI + j * ra1
+      float* cq = Cp + (long long)be0 * L + q;    // rows (al, be0 + bb) at cq + al * rowstep + bb * L
+      const long long o1 = L, o2 = 2LL * L, o3 = 3LL * L;
+      if (be0 + kMvGroup <= rx0) {
+        // a full group of four rows: no predicates in the row loop
+#pragma unroll 2
+        for (int al = 0; al < ra0; ++al, cq += rowstep, Ar += AI) {
+          float av[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) av[j] = Ar[(al * m * N + j) * ra1];
+          for (int j = 0; j < N; ++j) av[j] = Ar[j * ra1];
+          float sv[kMvGroup];
 #pragma unroll
-      for (int be = 0; be < RB; ++be) {
-        if (be < rx0) {
-          float s = 0.0f;
+          for (int bb = 0; bb < kMvGroup; ++bb) {
+            float t = 0.0f;
 #pragma unroll
-          for (int j = 0; j < N; ++j) s = fmaf(av[j], xr[be][j], s);
-          cq[(long long)(al * rx0 + be) * rowlen] = s;
+            for (int j = 0; j < N; ++j) t = fmaf(av[j], xr[bb][j], t);
+            sv[bb] = t;
+          }
+          cq[0] = sv[0];
+          cq[o1] = sv[1];
+          cq[o2] = sv[2];
+          cq[o3] = sv[3];
+        }
+      } else {
+        for (int al = 0; al < ra0; ++al, cq += rowstep, Ar += AI) {
+          float av[N];
+#pragma unroll
+          for (int j = 0; j < N; ++j) av[j] = Ar[j * ra1];
+#pragma unroll
+          for (int bb = 0; bb < kMvGroup; ++bb) {
+            if (be0 + bb < rx0) {
+              float t = 0.0f;
+#pragma unroll
+              for (int j = 0; j < N; ++j) t = fmaf(av[j], xr[bb][j], t);
+              cq[(long long)bb * L] = t;
+            }
+          }
         }
       }
     }
+    __syncthreads();
   }
 }
 
@@ -257,8 +346,10 @@ __global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ Ma
     }
     asm volatile("cp.async.commit_group;\n" ::);
   };
-  // dx: thread per (b, bp) with N accumulators
+  // dx: thread per (b, bp) with N accumulators; with at most 256 pairs (b, bp) the sum over
+  // q = (i, a') is split into H parts over otherwise idle threads, reduced once at the end
   const int nbb = rx0 * rx1;
+  const int H = nbb <= (int)blockDim.x ? max(1, min(8, (int)blockDim.x / max(nbb, 1))) : 1;
   float dxa[2][N];
 #pragma unroll
   for (int u = 0; u < 2; ++u)
@@ -277,7 +368,29 @@ __global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ Ma
     }
     __syncthreads();
     const float* G = Gb + (al & 1) * a.maxRow;  // [b][i][ap][bp]
-    if (a.dx) {
+    if (a.dx && nbb <= (int)blockDim.x) {
+      if (tid < nbb * H) {
+        const int bb = tid % nbb, h = tid / nbb;
+        const int q0 = h * nia / H, q1 = (h + 1) * nia / H;
+        const int b = bb / rx1, bp = bb % rx1;
+        const float* g = G + (long long)b * rowlen + bp + q0 * rx1;
+        const float* at = At + (long long)al * m * ra1 * N + q0 * N;
+#pragma unroll 4
+        for (int q = q0; q < q1; ++q, g += rx1, at += N) {
+          const float gv = *g;
+          if constexpr (N == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(at);
+            dxa[0][0] = fmaf(gv, v.x, dxa[0][0]);
+            dxa[0][1] = fmaf(gv, v.y, dxa[0][1]);
+            dxa[0][2] = fmaf(gv, v.z, dxa[0][2]);
+            dxa[0][3] = fmaf(gv, v.w, dxa[0][3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) dxa[0][j] = fmaf(gv, at[j], dxa[0][j]);
+          }
+        }
+      }
+    } else if (a.dx) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int e = tid + u * (int)blockDim.x;
@@ -342,7 +455,25 @@ __global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ Ma
     }
     __syncthreads();  // this buffer is restaged two blocks later
   }
-  if (a.dx) {
+  if (a.dx && nbb <= (int)blockDim.x) {
+    // the H partial sums of every (b, bp) through shared memory (free after the last block)
+    float* dXp = a.dx + core_base(X, k, ox);
+    if (tid < nbb * H) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) Red[tid * N + j] = dxa[0][j];
+    }
+    __syncthreads();
+    if (tid < nbb) {
+      const int b = tid / rx1, bp = tid % rx1;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        float v = 0.0f;
+        for (int h = 0; h < H; ++h) v += Red[(h * nbb + tid) * N + j];
+        float* dst = dXp + (b * N + j) * rx1 + bp;
+        if (a.atomicX) atomicAdd(dst, v); else *dst = v;
+      }
+    }
+  } else if (a.dx) {
     float* dXp = a.dx + core_base(X, k, ox);
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -390,9 +521,11 @@ extern "C" t3f_status t3f_matvec(const t3f_tt* A, const t3f_tt* x, t3f_tt* C, vo
   int P;
   T3F_CHECK(matvec_views(A, x, &va, &vx, &P));
   T3F_CHECK(check_product(va, vx, P, C, &vc));
-  (void)ws;
-  (void)ws_bytes;
   MatvecArgs args;
+  memset(&args, 0, sizeof(args));
+  // the error word of the persistent kernel's bounded waits (optional)
+  args.err = (ws && ws_bytes >= kWsHeader) ? static_cast<int*>(ws) : nullptr;
+  if (args.err && cudaMemsetAsync(args.err, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess) return T3F_ERR_CUDA;
   args.A = va;
   args.x = vx;
   args.C = vc;
@@ -411,41 +544,35 @@ extern "C" t3f_status t3f_matvec(const t3f_tt* A, const t3f_tt* x, t3f_tt* C, vo
   const long long grid = (long long)P * va.d;
   if (grid > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
-  // the specialised kernels need one column mode for every core and r_x <= 16 on the left;
-  // their CTAs take kMvRows rows a of one core each, so the boundary cores (left rank 1) do
-  // not leave most of the grid with a tenth of the work
-  int nall = va.n[0], rxmax = 0;
-  args.ucum[0] = 0;
-  for (int k = 0; k < va.d; ++k) {
+  int nall = va.n[0];
+  for (int k = 0; k < va.d; ++k)
     if (va.n[k] != nall) nall = -1;
-    if (vx.r[k] > rxmax) rxmax = vx.r[k];
-    args.ucum[k + 1] = args.ucum[k] + (va.r[k] + kMvRows - 1) / kMvRows;
+  const size_t psm = sizeof(float) * 2 * ((size_t)args.maxA + 8 + ((args.maxX + 3) & ~3) + 8);
+  if ((nall == 2 || nall == 4 || nall == 8) && psm <= 200 * 1024) {
+    // persistent kernel with TMA-staged cores: as many CTAs as fit on the GPU at once
+    args.maxX = (args.maxX + 3) & ~3;
+    auto runp = [&](auto kern) -> t3f_status {
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess)
+        return T3F_ERR_CUDA;
+      int dev = 0, sms = 0, per = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, psm) != cudaSuccess)
+        return T3F_ERR_CUDA;
+      const long long g = std::min<long long>(grid, (long long)sms * std::max(per, 1));
+      kern<<<(unsigned)g, 256, psm, s>>>(args);
+      return launch_status();
+    };
+    if (nall == 2) return runp(k_matvec_p<2>);
+    if (nall == 4) return runp(k_matvec_p<4>);
+    return runp(k_matvec_p<8>);
   }
-  const long long ugrid = (long long)P * args.ucum[va.d];
   auto run = [&](auto kern, long long g) -> t3f_status {
-    if (g > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
     kern<<<(unsigned)g, 256, smem, s>>>(args);
     return launch_status();
   };
-  if (rxmax <= 16 && (nall == 2 || nall == 4 || nall == 8)) {
-    const int RB = rxmax <= 4 ? 4 : (rxmax <= 8 ? 8 : (rxmax <= 12 ? 12 : 16));
-    switch (nall * 100 + RB) {
-      case 204: return run(k_matvec_n<2, 4>, ugrid);
-      case 208: return run(k_matvec_n<2, 8>, ugrid);
-      case 212: return run(k_matvec_n<2, 12>, ugrid);
-      case 216: return run(k_matvec_n<2, 16>, ugrid);
-      case 404: return run(k_matvec_n<4, 4>, ugrid);
-      case 408: return run(k_matvec_n<4, 8>, ugrid);
-      case 412: return run(k_matvec_n<4, 12>, ugrid);
-      case 416: return run(k_matvec_n<4, 16>, ugrid);
-      case 804: return run(k_matvec_n<8, 4>, ugrid);
-      case 808: return run(k_matvec_n<8, 8>, ugrid);
-      case 812: return run(k_matvec_n<8, 12>, ugrid);
-      default: return run(k_matvec_n<8, 16>, ugrid);
-    }
-  }
   return run(k_matvec, grid);
 }
 
