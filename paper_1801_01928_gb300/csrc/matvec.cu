@@ -301,6 +301,8 @@ __global__ void __launch_bounds__(256) k_matvec_bwd(const __grid_constant__ Matv
 //   dA[a, i, j, a'] = sum_{b, b'} G[b][i][a'][b'] xt[b][b'][j]    thread per (i, a') and part of
 //                                                                 the b range, parts summed
 //                                                                 in shared memory
+constexpr int kMvRed = 256 * 8;  // floats of one half of the adjoint's parts buffer
+
 template <int N>
 __global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ MatvecBwdArgs a) {
   extern __shared__ __align__(16) float sm[];
@@ -312,8 +314,8 @@ __global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ Ma
   const int tid = threadIdx.x;
   float* At = sm;                      // [ra0][m][ra1][N]
   float* Xt = At + a.maxA;             // [rx0][rx1][N]
-  float* Gb = Xt + a.maxX;             // [2][maxRow]
-  float* Red = Gb + 2 * a.maxRow;      // dA partial sums [parts][m * ra1][N]
+  float* Gb = Xt + a.maxX;             // [3][maxRow]: a ring of dC row blocks, two ahead
+  float* Red = Gb + 3 * a.maxRow;      // [2][kMvRed]: dA partial sums [parts][m * ra1][N]
   const int oa = a.bA == 1 ? 0 : p, ox = a.bx == 1 ? 0 : p;
   const float* Ap = static_cast<const float*>(A.p) + core_base(A, k, oa);
   const float* Xp = static_cast<const float*>(X.p) + core_base(X, k, ox);
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ Ma
   const int blk = rx0 * rowlen;
   const bool vec = ((reinterpret_cast<uintptr_t>(Gp) & 15) == 0) && (blk & 3) == 0;
   auto stage = [&](int al) {
-    float* dst = Gb + (al & 1) * a.maxRow;
+    float* dst = Gb + (al % 3) * a.maxRow;
     const float* src = Gp + (long long)al * blk;
     if (vec) {
       for (int e4 = tid; e4 < blk / 4; e4 += blockDim.x) {
@@ -358,16 +360,31 @@ __global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ Ma
   // dA: items (i, ap) x parts of the b range
   const int nia = m * ra1;
   const int parts = max(1, min(rx0, (int)blockDim.x / max(nia, 1)));
-  stage(0);
-  for (int al = 0; al < ra0; ++al) {
-    if (al + 1 < ra0) {
-      stage(al + 1);
-      asm volatile("cp.async.wait_group 1;\n" ::);
-    } else {
-      asm volatile("cp.async.wait_group 0;\n" ::);
+  // dA[al, i, j, ap] from the parts of row al (written in the iteration of row al)
+  float* dAp = a.dA ? a.dA + core_base(A, k, oa) : nullptr;
+  auto reduce_dA = [&](int al, const float* R) {
+    for (int e = tid; e < nia * N; e += blockDim.x) {
+      const int ap = e % ra1, j = (e / ra1) % N, i = e / (ra1 * N);
+      const int q = i * ra1 + ap;
+      float s = 0.0f;
+      for (int pp = 0; pp < parts; ++pp) s += R[(pp * nia + q) * N + j];
+      float* dst = dAp + ((al * m + i) * N + j) * ra1 + ap;
+      if (a.atomicA) atomicAdd(dst, s); else *dst = s;
     }
+  };
+  // one barrier per row block: after it, block al has landed, the parts of row al - 1 are
+  // complete, and ring slot (al + 2) % 3 (last read for row al - 1) may be restaged
+  stage(0);
+  if (ra0 > 1) stage(1);
+  for (int al = 0; al < ra0; ++al) {
+    if (al + 1 < ra0)
+      asm volatile("cp.async.wait_group 1;\n" ::);
+    else
+      asm volatile("cp.async.wait_group 0;\n" ::);
     __syncthreads();
-    const float* G = Gb + (al & 1) * a.maxRow;  // [b][i][ap][bp]
+    if (al + 2 < ra0) stage(al + 2);
+    if (a.dA && al > 0) reduce_dA(al - 1, Red + ((al - 1) & 1) * kMvRed);
+    const float* G = Gb + (al % 3) * a.maxRow;  // [b][i][ap][bp]
     if (a.dx && nbb <= (int)blockDim.x) {
       if (tid < nbb * H) {
         const int bb = tid % nbb, h = tid / nbb;
@@ -439,28 +456,19 @@ __global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ Ma
           }
         }
 #pragma unroll
-        for (int j = 0; j < N; ++j) Red[(part * nia + it) * N + j] = acc[j];
-      }
-      __syncthreads();
-      // dA[al, i, j, ap] from the parts
-      float* dAp = a.dA + core_base(A, k, oa);
-      for (int e = tid; e < nia * N; e += blockDim.x) {
-        const int ap = e % ra1, j = (e / ra1) % N, i = e / (ra1 * N);
-        const int q = i * ra1 + ap;
-        float s = 0.0f;
-        for (int pp = 0; pp < parts; ++pp) s += Red[(pp * nia + q) * N + j];
-        float* dst = dAp + ((al * m + i) * N + j) * ra1 + ap;
-        if (a.atomicA) atomicAdd(dst, s); else *dst = s;
+        for (int j = 0; j < N; ++j) Red[(al & 1) * kMvRed + (part * nia + it) * N + j] = acc[j];
       }
     }
-    __syncthreads();  // this buffer is restaged two blocks later
   }
+  __syncthreads();
+  if (a.dA && ra0 > 0) reduce_dA(ra0 - 1, Red + ((ra0 - 1) & 1) * kMvRed);
   if (a.dx && nbb <= (int)blockDim.x) {
-    // the H partial sums of every (b, bp) through shared memory (free after the last block)
+    // the H partial sums of every (b, bp) through the other half of the parts buffer
+    float* const Rx = Red + (ra0 & 1) * kMvRed;
     float* dXp = a.dx + core_base(X, k, ox);
     if (tid < nbb * H) {
 #pragma unroll
-      for (int j = 0; j < N; ++j) Red[tid * N + j] = dxa[0][j];
+      for (int j = 0; j < N; ++j) Rx[tid * N + j] = dxa[0][j];
     }
     __syncthreads();
     if (tid < nbb) {
@@ -468,7 +476,7 @@ __global__ void __launch_bounds__(256) k_matvec_bwd_n(const __grid_constant__ Ma
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         float v = 0.0f;
-        for (int h = 0; h < H; ++h) v += Red[(h * nbb + tid) * N + j];
+        for (int h = 0; h < H; ++h) v += Rx[(h * nbb + tid) * N + j];
         float* dst = dXp + (b * N + j) * rx1 + bp;
         if (a.atomicX) atomicAdd(dst, v); else *dst = v;
       }
@@ -640,7 +648,7 @@ extern "C" t3f_status t3f_matvec_backward(const t3f_tt* A, const t3f_tt* x, cons
     b2.maxA = (args.maxA + 3) & ~3;
     b2.maxX = (args.maxX + 3) & ~3;
     b2.maxRow = (args.maxRow + 3) & ~3;
-    const size_t sm2 = sizeof(float) * ((size_t)b2.maxA + b2.maxX + 2 * (size_t)b2.maxRow + 256 * 8);
+    const size_t sm2 = sizeof(float) * ((size_t)b2.maxA + b2.maxX + 3 * (size_t)b2.maxRow + 2 * (size_t)kMvRed);
     if (sm2 <= 200 * 1024) {
       auto go = [&](auto kern) -> t3f_status {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2) != cudaSuccess)
