@@ -494,8 +494,9 @@ def tensor_peaks():
 
 
 def reduced_precision(w, flops, flush, stream, reps=5):
-    """TF32 / BF16 tensor-core Gram of config 3a and the uneven batch with BF16 cores, each
-    timed with CUDA events (L2 flushed before every repetition) and compared with the FP32
+    """TF32 / BF16 tensor-core Gram and Gram adjoint of config 3a and of the uneven batch (BF16
+    on BF16 cores), the FP32 paths on BF16 cores and the TF32 project_sum of config 5, each
+    timed by CUDA-graph replay (L2 flushed before every replay) and compared with the FP32
     result of the same inputs (normwise relative difference)."""
     t3f, torch = w.t3f, w.torch
     A3, B3 = w.tt("A3"), w.tt("B3")
@@ -506,19 +507,9 @@ def reduced_precision(w, flops, flush, stream, reps=5):
     G4_32 = w.G4.double()
 
     def timed(fn):
-        fn()
-        torch.cuda.synchronize()
-        tot = 0.0
-        for _ in range(reps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            tot += e0.elapsed_time(e1)
-        return tot / reps
+        # device time by CUDA-graph replay (L2 flushed before each replay), as for the step's
+        # own uneven batch: the per-call host planning of the grouped calls is not device work
+        return graph_time(torch, fn, flush, stream, reps)
 
     def rel(x, y):
         return float((x.double() - y).norm() / y.norm())
