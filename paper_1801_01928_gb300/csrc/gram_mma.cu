@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kMmaThreads = 256;
 constexpr uint32_t kTmemCols = 256;  // T at columns 0..127, D at 128..255
+constexpr uint32_t kTmemColsPipe = 512;  // pipelined: a second T at columns 256..383
 constexpr uint32_t kSkew = 64;  // extra bytes between consecutive operands (16-bank shift)
 
 constexpr uint32_t kSmemCap = 227u * 1024u;
@@ -55,6 +56,19 @@ __host__ __device__ constexpr MmaLayout mma_layout(int es, int RA, int RB) {
   L.o_mop = L.o_as + (uint32_t)L.nbuf * TA * L.sl_a;
   L.o_top = L.o_mop + TB * L.big_b;
   L.total = L.o_top + TA * L.big_a;
+  return L;
+}
+
+// Pipelined variant (BF16 work lists): three slice buffers and two copies of T_a, so that
+// slice i + 1's first product runs while slice i's T is transposed.
+__host__ __device__ constexpr MmaLayout mma_layout_pipe(int es, int RA, int RB) {
+  MmaLayout L = mma_layout(es, RA, RB);
+  const uint32_t TA = 128u / (uint32_t)RA, TB = 128u / (uint32_t)RB;
+  L.nbuf = 3;
+  L.o_as = 3u * TB * L.sl_b;
+  L.o_mop = L.o_as + 3u * TA * L.sl_a;
+  L.o_top = L.o_mop + TB * L.big_b;
+  L.total = L.o_top + 2u * TA * L.big_a;
   return L;
 }
 
@@ -145,6 +159,11 @@ __device__ __forceinline__ void epi_transpose(uint32_t tcol, char* dst) {
 struct MmaState {
   uint32_t tmem, bar1, bar2, ph1, ph2;
   bool pending1, pending2;  // a committed product batch not yet waited for
+  // pipelined loop: one barrier per T buffer (first products) and per T copy (second
+  // products), so that no barrier ever has two completions outstanding
+  uint32_t b1[2], b2[2], q1[2], q2[2];  // indexed by constants or through the pipe_* helpers
+  bool pd1[2], pd2[2];
+  uint32_t cols;            // tensor-memory columns allocated
   int bad;                  // this thread saw a wait run out
   long long* s_base;        // [2 core parities][2 sides][8 objects]
   int* s_r0;                // K (left-rank) limit of the swept core
@@ -154,6 +173,29 @@ struct MmaState {
   int* s_is;
   float* s_g;               // adjoint sweeps: cotangent of pair (a, b) at [a * 8 + b]
 };
+
+
+// Pipelined loop helpers: wait for / record a product batch on barrier pair `which` (1: first
+// products, 2: second products), buffer p; p selects between scalars so nothing is indexed at
+// run time (which would move the state to local memory).
+__device__ __forceinline__ void pipe_wait(MmaState& st, int which, int p) {
+  uint32_t& ph = which == 1 ? (p ? st.q1[1] : st.q1[0]) : (p ? st.q2[1] : st.q2[0]);
+  bool& pd = which == 1 ? (p ? st.pd1[1] : st.pd1[0]) : (p ? st.pd2[1] : st.pd2[0]);
+  const uint32_t bar = which == 1 ? (p ? st.b1[1] : st.b1[0]) : (p ? st.b2[1] : st.b2[0]);
+  if (pd) {
+    st.bad |= !mbar_wait(bar, ph);
+    ph ^= 1u;
+    pd = false;
+  }
+}
+__device__ __forceinline__ void pipe_commit(MmaState& st, int which, int p) {
+  const uint32_t bar = which == 1 ? (p ? st.b1[1] : st.b1[0]) : (p ? st.b2[1] : st.b2[0]);
+  if (threadIdx.x == 0) mma_commit(bar);
+}
+__device__ __forceinline__ void pipe_mark(MmaState& st, int which, int p) {
+  bool& pd = which == 1 ? (p ? st.pd1[1] : st.pd1[0]) : (p ? st.pd2[1] : st.pd2[0]);
+  pd = true;
+}
 
 // Adjoint sweeps: the partial D (TMEM columns from tcol; lanes (b, be), columns (a, al)) goes
 // to one scratch slot in two orientations, each a 128 x 128 K-major operand with 16-byte core
@@ -200,14 +242,16 @@ __device__ __forceinline__ void store_partial(uint32_t tcol, char* o0, char* o1,
 // dir 1 runs the same recursion over the cores in reverse order with transposed slices
 // (R_k = sum_i A_k,i R_{k+1} B_k,i^T) and stores R_1 .. R_d. Slot j of direction dir holds
 // interface j (dir 0) or j + 1 (dir 1); M is stored scaled by the pair's cotangent.
-template <int KIND, int RA, int RB, typename ST>
+// PIPE (BF16 work lists): three slice buffers, T and its shared-memory copy double-buffered;
+// slice i + 1's first product is issued before slice i's T is transposed.
+template <int KIND, int RA, int RB, typename ST, bool PIPE = false>
 __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int grp, int a0, int na, int b0, int nb,
                               int sym, int d, int dir = 0, char* slots = nullptr) {
   using O = OpT<KIND>;
   constexpr int ES = O::ES;
   constexpr int T = 16 / ES;
   constexpr int TA = 128 / RA, TB = 128 / RB;
-  constexpr MmaLayout L = mma_layout(ES, RA, RB);
+  constexpr MmaLayout L = PIPE ? mma_layout_pipe(ES, RA, RB) : mma_layout(ES, RA, RB);
   constexpr int NBUF = L.nbuf;
   constexpr uint32_t SBOA = L.sbo_a, SBOB = L.sbo_b, BIGA = L.big_a, BIGB = L.big_b, SLA = L.sl_a, SLB = L.sl_b;
   constexpr uint32_t ID1 = idesc(O::FMT, RB), ID2 = idesc(O::FMT, RA);
@@ -355,11 +399,86 @@ __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int 
     }
   };
 
+  // pipelined loop: MMA1 of slice j (slice buffer sb) into T buffer tb, MMA2 of slice j from
+  // T copy tb and slice buffer sb
+  auto issue_mma1 = [&](int sb, int tb) {
+    const uint64_t da = sdesc(su32(mop), SBOB), db = sdesc(su32(bsl + sb * TB * SLB), SBOB);
+#pragma unroll
+    for (int b = 0; b < TB; ++b)
+#pragma unroll
+      for (int kk = 0; kk < RB / O::KI; ++kk)
+        mma<KIND>(st.tmem + (uint32_t)tb * 256u + (uint32_t)(b * RB), da + ((b * BIGB + kk * 2 * kLBO) >> 4),
+                  db + ((b * SLB + kk * 2 * kLBO) >> 4), ID1, kk > 0);
+  };
+  auto issue_mma2 = [&](int sb, int tb, bool acc) {
+    const uint64_t da = sdesc(su32(top + tb * TA * BIGA), SBOA), db = sdesc(su32(asl + sb * TA * SLA), SBOA);
+#pragma unroll
+    for (int a = 0; a < TA; ++a)
+#pragma unroll
+      for (int kk = 0; kk < RA / O::KI; ++kk)
+        mma<KIND>(st.tmem + 128u + (uint32_t)(a * RA), da + ((a * BIGA + kk * 2 * kLBO) >> 4),
+                  db + ((a * SLA + kk * 2 * kLBO) >> 4), ID2, (acc || kk > 0) ? 1u : 0u);
+  };
+
   int iter = 0;
   load_slice(0, 0);
   for (int k = 0; k < d; ++k) {
     const int n = nmode(k);
     if (k + 1 < d) fill_info(k + 1, (k + 1) & 1);  // read after the next block barrier
+    if constexpr (PIPE) {
+      // prologue: slice 0 -> buffer 0, its first product into T buffer 0
+      store_slice(0);
+      async_fence();
+      tc_before();
+      if (__syncthreads_or(st.bad)) return false;
+      if (tid == 0) {
+        tc_after();
+        issue_mma1(0, 0);
+      }
+      pipe_commit(st, 1, 0);
+      pipe_mark(st, 1, 0);
+      if (n > 1)
+        load_slice(k, 1);
+      else if (k + 1 < d)
+        load_slice(k + 1, 0);
+      for (int i = 0; i < n; ++i) {
+        const int p = i & 1;
+        // slice i - 2's second product frees T copy p and slice buffer (i + 1) % 3
+        pipe_wait(st, 2, p);
+        if (i + 1 < n) {
+          store_slice((i + 1) % 3);
+          async_fence();
+          tc_before();
+          if (__syncthreads_or(st.bad)) return false;
+          // slice i + 1's first product into the other T buffer (transposed in iteration i - 1)
+          if (tid == 0) {
+            tc_after();
+            issue_mma1((i + 1) % 3, p ^ 1);
+          }
+          pipe_commit(st, 1, p ^ 1);
+          pipe_mark(st, 1, p ^ 1);
+          if (i + 2 < n)
+            load_slice(k, i + 2);
+          else if (k + 1 < d)
+            load_slice(k + 1, 0);
+        }
+        pipe_wait(st, 1, p);
+        tc_after();
+        epi_transpose<KIND, RA, SBOA, BIGA>(st.tmem + (uint32_t)p * 256u, top + p * TA * BIGA);
+        async_fence();
+        tc_before();
+        if (__syncthreads_or(st.bad)) return false;
+        if (tid == 0) {
+          tc_after();
+          issue_mma2(i % 3, p, i > 0);
+        }
+        pipe_commit(st, 2, p);
+        pipe_mark(st, 2, p);
+      }
+      pipe_wait(st, 2, 0);
+      pipe_wait(st, 2, 1);
+      tc_after();
+    } else {
     for (int i = 0; i < n; ++i, ++iter) {
       const int s = NBUF == 2 ? (iter & 1) : 0;
       if (NBUF == 1 && st.pending2) {  // the single slice buffer is still read by MMA2
@@ -422,6 +541,7 @@ __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int 
     st.ph2 ^= 1u;
     st.pending2 = false;
     tc_after();
+    }
     // ---- epilogue 2: D (rows (b, bp), cols (a, ap)) -> M_b[(a, ap), bp], or the Gram entries;
     // the adjoint sweeps also store D to its slot (after core k: interface k + 1, or d - 1 - k)
     if (k + 1 < d) {
@@ -466,25 +586,24 @@ __device__ bool mma_tile_sync(const GramMmaArgs& g, char* sm, MmaState& st, int 
   return true;
 }
 
-template <int KIND, int RA, int RB, typename ST>
+template <int KIND, int RA, int RB, typename ST, bool PIPE = false>
 __device__ __forceinline__ bool mma_tile(const GramMmaArgs& g, char* sm, MmaState& st, int grp, int a0, int na,
                                          int b0, int nb, int sym, int d, int dir = 0, char* slots = nullptr) {
-  return mma_tile_sync<KIND, RA, RB, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots);
+  return mma_tile_sync<KIND, RA, RB, ST, PIPE>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots);
 }
 
 // Common prologue / epilogue of the kernels: TMEM allocation, barriers, and the release of
 // the tensor memory after a bounded wait for anything still in flight.
-__device__ __forceinline__ void mma_setup(MmaState& st, uint64_t* bars, uint32_t* s_tmem, char* sm, uint32_t bytes) {
+// bars: 6 mbarriers (the plain loop's two, the pipelined loop's four)
+__device__ __forceinline__ void mma_setup(MmaState& st, uint64_t* bars, uint32_t* s_tmem, char* sm, uint32_t bytes,
+                                          uint32_t cols = kTmemCols) {
   const int tid = threadIdx.x, warp = tid >> 5;
   for (uint32_t e = (uint32_t)tid * 16u; e < bytes; e += kMmaThreads * 16u)
     *reinterpret_cast<uint4*>(sm + e) = make_uint4(0u, 0u, 0u, 0u);
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[1])));
-  }
+  if (tid == 0)
+    for (int j = 0; j < 6; ++j) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[j])));
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)),
-                 "r"(kTmemCols));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(s_tmem)), "r"(cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   async_fence();
@@ -492,10 +611,17 @@ __device__ __forceinline__ void mma_setup(MmaState& st, uint64_t* bars, uint32_t
   __syncthreads();
   tc_after();
   st.tmem = *s_tmem;
+  st.cols = cols;
   st.bar1 = su32(&bars[0]);
   st.bar2 = su32(&bars[1]);
   st.ph1 = st.ph2 = 0;
   st.pending1 = st.pending2 = false;
+  for (int j = 0; j < 2; ++j) {
+    st.b1[j] = su32(&bars[2 + j]);
+    st.b2[j] = su32(&bars[4 + j]);
+    st.q1[j] = st.q2[j] = 0;
+    st.pd1[j] = st.pd2[j] = false;
+  }
   st.bad = 0;
 }
 
@@ -506,12 +632,16 @@ __device__ __forceinline__ void mma_teardown(const GramMmaArgs& g, MmaState& st,
     if (threadIdx.x == 0 && g.err) atomicExch(g.err, (int)T3F_ERR_TIMEOUT);
     if (st.pending1) mbar_wait(st.bar1, st.ph1);
     if (st.pending2) mbar_wait(st.bar2, st.ph2);
+    for (int j = 0; j < 2; ++j) {
+      if (st.pd1[j]) mbar_wait(st.b1[j], st.q1[j]);
+      if (st.pd2[j]) mbar_wait(st.b2[j], st.q2[j]);
+    }
   }
   tc_before();
   __syncthreads();
   tc_after();
   if ((threadIdx.x >> 5) == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(kTmemCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(st.cols));
 }
 
 // CTAs per SM the shared memory of a tile shape allows (at most 2: the tensor memory holds two)
@@ -521,7 +651,7 @@ __host__ __device__ constexpr int mma_ctas_per_sm(int es, int RA, int RB) {
 
 // Per-CTA state of the sweep kernels besides the dynamic operand area.
 struct MmaShared {
-  uint64_t bar[2];
+  uint64_t bar[6];
   long long base[2][2][8];
   int r0[2][2][8], r1[2][2][8], cs[2][2][8], rs[2][2][8], is[2][2][8];
   float gv[64];
@@ -568,7 +698,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_gram_mma_list(const __grid_c
   __shared__ __align__(16) MmaShared sh;
   MmaState st;
   mma_bind(st, sh);
-  mma_setup(st, sh.bar, &sh.tmem, sm, g.smem_bytes);
+  constexpr bool PIPE = KIND == 1;  // the pipelined loop fits shared memory for BF16 operands
+  mma_setup(st, sh.bar, &sh.tmem, sm, g.smem_bytes, PIPE ? kTmemColsPipe : kTmemCols);
   const int tid = threadIdx.x;
   const int total = g.scr ? 2 * g.nitems : g.nitems;
   bool ok = true;
@@ -592,12 +723,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_gram_mma_list(const __grid_c
     char* const slots = g.scr ? g.scr + (size_t)g.soff[sh.wi] * (128u * 128u * OpT<KIND>::ES) : nullptr;
     const int key = RA * 1000 + RB;
     switch (key) {
-      case 16016: ok = mma_tile<KIND, 16, 16, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
-      case 16032: ok = mma_tile<KIND, 16, 32, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
-      case 16064: ok = mma_tile<KIND, 16, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
-      case 32032: ok = mma_tile<KIND, 32, 32, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
-      case 32064: ok = mma_tile<KIND, 32, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
-      default: ok = mma_tile<KIND, 64, 64, ST>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      case 16016: ok = mma_tile<KIND, 16, 16, ST, PIPE>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      case 16032: ok = mma_tile<KIND, 16, 32, ST, PIPE>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      case 16064: ok = mma_tile<KIND, 16, 64, ST, PIPE>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      case 32032: ok = mma_tile<KIND, 32, 32, ST, PIPE>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      case 32064: ok = mma_tile<KIND, 32, 64, ST, PIPE>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
+      default: ok = mma_tile<KIND, 64, 64, ST, PIPE>(g, sm, st, grp, a0, na, b0, nb, sym, d, dir, slots); break;
     }
   }
   mma_teardown(g, st, !ok);
@@ -637,7 +768,8 @@ uint32_t list_smem(int es) {
   uint32_t m = 0;
   const int rs[3] = {16, 32, 64};
   for (int x = 0; x < 3; ++x)
-    for (int y = x; y < 3; ++y) m = std::max(m, mma_layout(es, rs[x], rs[y]).total);
+    for (int y = x; y < 3; ++y)
+      m = std::max(m, (es == 2 ? mma_layout_pipe(es, rs[x], rs[y]) : mma_layout(es, rs[x], rs[y])).total);
   return m;
 }
 
