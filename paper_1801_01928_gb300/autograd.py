@@ -49,12 +49,13 @@ class _CompletionLoss(torch.autograd.Function):
 
 class _Gram(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, a_data, b_data, a_meta, b_meta):
+    def forward(ctx, a_data, b_data, a_meta, b_meta, math):
         A = B.TT(a_data.detach(), *a_meta)
         Bt = B.TT(b_data.detach(), *b_meta)
         ctx.save_for_backward(a_data, b_data)
         ctx.meta = (a_meta, b_meta)
-        return B.gram(A, Bt)
+        ctx.math = math
+        return B.gram(A, Bt, math=math)
 
     @staticmethod
     def backward(ctx, dG):
@@ -63,9 +64,9 @@ class _Gram(torch.autograd.Function):
         A = B.TT(a_data.detach(), *a_meta)
         Bt = B.TT(b_data.detach(), *b_meta)
         need_a, need_b = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        dA, dB = B.gram_backward(A, Bt, dG, need_A=need_a, need_B=need_b)
+        dA, dB = B.gram_backward(A, Bt, dG, need_A=need_a, need_B=need_b, math=ctx.math)
         return (dA.data.to(a_data.dtype) if need_a else None,
-                dB.data.to(b_data.dtype) if need_b else None, None, None)
+                dB.data.to(b_data.dtype) if need_b else None, None, None, None)
 
 
 class _ProjectSum(torch.autograd.Function):
@@ -97,9 +98,10 @@ def completion_loss(X: B.TT, idx: torch.Tensor, y: torch.Tensor) -> torch.Tensor
     return _CompletionLoss.apply(X.data, _meta(X), idx, y)
 
 
-def gram(A: B.TT, Bt: B.TT) -> torch.Tensor:
-    """FP32 [A.batch, B.batch] Gram matrix; differentiable w.r.t. A.data and B.data."""
-    return _Gram.apply(A.data, Bt.data, _meta(A), _meta(Bt))
+def gram(A: B.TT, Bt: B.TT, math: str = "fp32") -> torch.Tensor:
+    """FP32 [A.batch, B.batch] Gram matrix; differentiable w.r.t. A.data and B.data. math
+    "tf32" / "bf16" runs the forward and the adjoint on the tensor cores."""
+    return _Gram.apply(A.data, Bt.data, _meta(A), _meta(Bt), math)
 
 
 def project_sum(U: B.TT, V: B.TT, Z: B.TT, c: torch.Tensor) -> B.TT:

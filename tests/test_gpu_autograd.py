@@ -136,3 +136,26 @@ def test_project_sum_autograd(lib):
     fd = _fd(f, Zt.data.detach(), DZ, 1e-2)
     ad = float((Zt.data.grad.double() * DZ.double()).sum())
     assert abs(fd - ad) / abs(ad) < 1e-3
+
+
+@pytest.mark.parametrize("math_", ["tf32", "bf16"])
+def test_gram_autograd_tensor_cores(lib, math_):
+    # the tensor-core forward and adjoint behind torch.autograd, against the oracle's
+    # cotangents at the math's tolerance (A and B distinct, both requiring gradients)
+    from paper_1801_01928_gb300 import autograd as AG
+    torch.manual_seed(502)
+    rng = np.random.default_rng(502)
+    n = [3, 4, 2, 5]
+    A = round32(S.random_tt(rng, 9, n, [1, 6, 20, 9, 1], 0.3))
+    Bc = round32(S.random_tt(rng, 6, n, [1, 4, 12, 30, 1], 0.3))
+    At, Bt = _tt(lib, A), _tt(lib, Bc)
+    At.data.requires_grad_(True)
+    Bt.data.requires_grad_(True)
+    W = torch.randn(At.batch, Bt.batch, device="cuda")
+    G = AG.gram(At, Bt, math=math_)
+    Gref = O.gram(objects(A), objects(Bc))
+    assert rel_err(G.detach().double().cpu().numpy(), Gref) < TOL[math_]
+    (G * W).sum().backward()
+    dA, dB = O.gram_vjp(objects(A), objects(Bc), W.double().cpu().numpy())
+    assert rel_err_cores(_host_cores(lib, At.data.grad, At), batched(dA)) < TOL[math_]
+    assert rel_err_cores(_host_cores(lib, Bt.data.grad, Bt), batched(dB)) < TOL[math_]
