@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(256, 1) k_completion(const __grid_constant__ C
   float4* LW = RH + (size_t)d * H * T;                                     // [d][H][T]
   unsigned short* POS = reinterpret_cast<unsigned short*>(LW + (size_t)d * H * T);  // [d][T]
   unsigned char* IDX = reinterpret_cast<unsigned char*>(POS + (size_t)d * T);       // [d][T]
-  int* WC = reinterpret_cast<int*>(IDX + (((size_t)d * T + 15) & ~(size_t)15));    // [d][NB][NW]
-  int* CNT = WC + (size_t)d * NB * NW;                                              // [d][NB]
+  unsigned short* WC = reinterpret_cast<unsigned short*>(IDX + (((size_t)d * T + 15) & ~(size_t)15));  // [d][NB][NW]
+  int* CNT = reinterpret_cast<int*>(WC + (((size_t)d * NB * NW + 1) & ~(size_t)1));                      // [d][NB]
   int* BO = CNT + (size_t)d * NB;                                                   // [d][NB+1]
 
   // stage the cores as zero-padded R x R slices with stride SS: the whole object(s) land in
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256, 1) k_completion(const __grid_constant__ C
       if (tid < T) {
         IDX[k * T + tid] = (unsigned char)sl;
         POS[k * T + tid] = (unsigned short)rank;
-        if (rank == 0) WC[(k * NB + sl) * NW + warp] = __popc(m);
+        if (rank == 0) WC[(k * NB + sl) * NW + warp] = (unsigned short)__popc(m);
       }
     }
     __syncthreads();
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(256, 1) k_completion(const __grid_constant__ C
       int run = 0;
       for (int w = 0; w < NW; ++w) {
         const int c = WC[e * NW + w];
-        WC[e * NW + w] = run;
+        WC[e * NW + w] = (unsigned short)run;
         run += c;
       }
       CNT[e] = run;
@@ -658,17 +658,23 @@ static size_t completion_smem(int d, int nmax, int R, int T, bool same) {
   size_t b = sizeof(float) * ((same ? 1 : 2) * (size_t)d * nmax * SS + 2 * (size_t)d * R * T);
   b += 2 * (size_t)d * T;                           // POS
   b += ((size_t)d * T + 15) & ~(size_t)15;          // IDX
-  b += sizeof(int) * ((size_t)d * NB * NW + (size_t)d * NB + (size_t)d * (NB + 1));
+  b += sizeof(unsigned short) * (((size_t)d * NB * NW + 1) & ~(size_t)1);  // WC (counts <= T)
+  b += sizeof(int) * ((size_t)d * NB + (size_t)d * (NB + 1));
   return b;
 }
 
-// Choose the bucketed adjoint when its items fit one CTA and its buffers fit shared memory.
+// Choose the bucketed adjoint when its items fit one CTA and its buffers fit shared memory:
+// the largest chunk T whose buffers let two CTAs share an SM (one CTA's barrier waits overlap
+// the other's chains), else the largest that fits one CTA.
 static bool plan_completion(const TTV& L, bool same, int R, GatherLayout* lay) {
   if (R > 8 || L.nmax > 254) return false;
   const int d = L.d;
+  for (int pass = 0; pass < 2; ++pass)
   for (int T = 256; T >= 128; T -= 32) {
     if (L.nmax * R > T) continue;
-    if (completion_smem(d, L.nmax, R, T, same) > 220 * 1024) continue;
+    // two CTAs per SM: 228 KB per SM less 1 KB reserved and the static block per CTA
+    const size_t cap = pass == 0 ? (228 * 1024 - 2 * 1200) / 2 : 220 * 1024;
+    if (completion_smem(d, L.nmax, R, T, same) > cap) continue;
     // boundary cores take one item per slice, interior cores share the rest evenly
     int bnd = 0, inner = 0;
     for (int k = 0; k < d; ++k) {
@@ -685,7 +691,7 @@ static bool plan_completion(const TTV& L, bool same, int R, GatherLayout* lay) {
     }
     lay->item0[d] = it;
     if (it > T) continue;
-    lay->bucketed = 1;
+    lay->bucketed = pass == 0 ? 2 : 1;  // CTAs per SM
     lay->T = T;
     lay->NB = L.nmax + 1;
     lay->smem = completion_smem(d, L.nmax, R, T, same);
@@ -707,7 +713,7 @@ static GatherLayout gather_layout(const TTV& L, const TTV& Rv, long long N, bool
     lay.grid = gather_grid(N, num_sms() * 8);
   } else if (lay.R && plan_completion(L, same, R, &lay)) {
     long long g = (N + lay.T - 1) / lay.T;
-    if (g > num_sms()) g = num_sms();
+    if (g > (long long)num_sms() * lay.bucketed) g = (long long)num_sms() * lay.bucketed;
     lay.grid = (int)(g < 1 ? 1 : g);
   } else {
     lay.smem = sizeof(float) * ((same ? 1 : 2) * SL + (size_t)L.d * nmax * (R * R + 1) +
