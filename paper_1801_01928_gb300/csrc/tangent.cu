@@ -136,19 +136,23 @@ struct TGatherArgs {
 
 template <int R>
 __device__ void stage_slices(float* dst, const float* src, const TGatherArgs& g) {
+  constexpr int SS = R * R + 4;  // slice stride: consecutive slices start 4 banks apart
   const int total = g.d * g.nmax * R * R;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int b = e % R, a = (e / R) % R, i = (e / (R * R)) % g.nmax, k = e / (R * R * g.nmax);
     float v = 0.0f;
     if (i < g.n[k] && a < g.r[k] && b < g.r[k + 1]) v = __ldg(src + g.off[k] + ((long long)a * g.n[k] + i) * g.r[k + 1] + b);
-    dst[e] = v;
+    dst[(k * g.nmax + i) * SS + a * R + b] = v;
   }
 }
 
 template <int R>
 __global__ void __launch_bounds__(256) k_tangent_gather(const __grid_constant__ TGatherArgs g) {
-  extern __shared__ float sm[];
-  const int SL = g.d * g.nmax * R * R;
+  extern __shared__ __align__(16) float sm[];
+  // the tuples of a warp read slices at random indices: a slice stride of R^2 + 4 floats
+  // spreads the same offset of different slices over distinct banks
+  constexpr int SS = R * R + 4;
+  const int SL = g.d * g.nmax * SS;
   float* Us = sm;
   float* Vs = sm + SL;
   float* Ws = sm + 2 * SL;
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(256) k_tangent_gather(const __grid_constant__ 
         atomicExch(g.err, (int)T3F_ERR_ARG);
         i = i < 0 ? 0 : g.n[k] - 1;
       }
-      const int so = (k * g.nmax + i) * R * R;
+      const int so = (k * g.nmax + i) * SS;
       float np[R], nq[R];
 #pragma unroll
       for (int b = 0; b < R; ++b) np[b] = nq[b] = 0.0f;
@@ -805,7 +809,7 @@ extern "C" t3f_status t3f_completion_hvp(const t3f_tt* U, const t3f_tt* V, const
   T3F_CHECK(check_ws(ws, ws_bytes, need));
   int R = vu.rmax <= 4 ? 4 : (vu.rmax <= 8 ? 8 : (vu.rmax <= 16 ? 16 : 0));
   if (!R) return T3F_ERR_UNSUPPORTED;
-  const size_t smem = sizeof(float) * 3 * (size_t)vu.d * vu.nmax * R * R;
+  const size_t smem = sizeof(float) * 3 * (size_t)vu.d * vu.nmax * (R * R + 4);
   if (smem > 200 * 1024) return T3F_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   float* wv = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(rg));
