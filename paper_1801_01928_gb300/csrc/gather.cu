@@ -152,9 +152,12 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_fwd(const __grid_cons
   __shared__ double red[kGatherThreads / 32];
   __shared__ __align__(8) uint64_t bar;
   float* Ls = sm;
-  float* landing = sm + g.d * g.nmax * R * R;  // 16-byte aligned (R * R is a multiple of 16)
+  // slices R^2 + 4 floats apart: the random slice indices of a warp's tuples fall on
+  // different banks
+  constexpr int SS = R * R + 4;
+  float* landing = sm + g.d * g.nmax * SS;  // 16-byte aligned (SS is a multiple of 4)
   bar_init(&bar);
-  if (!stage_object_tma<R>(Ls, R * R, landing, g.L, g.Lnfl, g.Loff, g.rl, g.n, g.d, g.nmax, &bar, 0u) &&
+  if (!stage_object_tma<R>(Ls, SS, landing, g.L, g.Lnfl, g.Loff, g.rl, g.n, g.d, g.nmax, &bar, 0u) &&
       threadIdx.x == 0)
     atomicExch(g.err, (int)T3F_ERR_TIMEOUT);
   __syncthreads();
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_fwd(const __grid_cons
     for (int a = 0; a < R; ++a) l[a] = a == 0 ? 1.0f : 0.0f;
     for (int k = 0; k < g.d; ++k) {
       const int i = load_index(g, k, t);
-      const float* S = Ls + (k * g.nmax + i) * R * R;
+      const float* S = Ls + (k * g.nmax + i) * SS;
       float nl[R];
 #pragma unroll
       for (int b = 0; b < R; ++b) nl[b] = 0.0f;
@@ -202,7 +205,8 @@ template <int R>
 __global__ void __launch_bounds__(kGatherThreads) k_gather_bwd(const __grid_constant__ GatherArgs g) {
   extern __shared__ float sm[];
   __shared__ double red[kGatherThreads / 32];
-  const int SL = g.d * g.nmax * R * R;   // staged floats per core set
+  constexpr int SS = R * R + 4;          // slice stride (distinct banks for random slices)
+  const int SL = g.d * g.nmax * SS;      // staged floats per core set
   const int GS = R * R + 1;              // odd slice stride of the accumulator
   float* Ls = sm;
   float* Rs = g.same ? Ls : Ls + SL;
@@ -211,10 +215,10 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_bwd(const __grid_cons
   // both objects land in the accumulator region (zeroed afterwards), one after the other
   __shared__ __align__(8) uint64_t bar;
   bar_init(&bar);
-  bool ok = stage_object_tma<R>(Ls, R * R, acc, g.L, g.Lnfl, g.Loff, g.rl, g.n, g.d, g.nmax, &bar, 0u);
+  bool ok = stage_object_tma<R>(Ls, SS, acc, g.L, g.Lnfl, g.Loff, g.rl, g.n, g.d, g.nmax, &bar, 0u);
   __syncthreads();
   if (!g.same) {
-    ok &= stage_object_tma<R>(Rs, R * R, acc, g.Rg, g.Rnfl, g.Roff, g.rr, g.n, g.d, g.nmax, &bar, 1u);
+    ok &= stage_object_tma<R>(Rs, SS, acc, g.Rg, g.Rnfl, g.Roff, g.rr, g.n, g.d, g.nmax, &bar, 1u);
     __syncthreads();
   }
   if (!ok && threadIdx.x == 0) atomicExch(g.err, (int)T3F_ERR_TIMEOUT);
@@ -234,7 +238,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_bwd(const __grid_cons
 #pragma unroll
         for (int a = 0; a < R; ++a) sfx[(k * R + a) * nth + tid] = rho[a];
         const int i = load_index(g, k, t);
-        const float* S = Rs + (k * g.nmax + i) * R * R;
+        const float* S = Rs + (k * g.nmax + i) * SS;
         float nr[R];
 #pragma unroll
         for (int a = 0; a < R; ++a) {
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_bwd(const __grid_cons
       for (int a = 0; a < R; ++a) sfx[a * nth + tid] = rho[a];
       const int i0 = load_index(g, 0, t);
       // X(i_t) = row 0 of the first suffix core's slice times the suffix at interface 1
-      const float* S0 = Rs + i0 * R * R;
+      const float* S0 = Rs + i0 * SS;
       float x = 0.0f;
 #pragma unroll
       for (int b = 0; b < R; ++b) x = fmaf(S0[b], rho[b], x);
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_bwd(const __grid_cons
           }
         }
         if (k + 1 < g.d) {
-          const float* S = Ls + (k * g.nmax + i) * R * R;
+          const float* S = Ls + (k * g.nmax + i) * SS;
           float nl[R];
 #pragma unroll
           for (int b = 0; b < R; ++b) nl[b] = 0.0f;
@@ -705,18 +709,17 @@ static GatherLayout gather_layout(const TTV& L, const TTV& Rv, long long N, bool
   lay.R = pick_R(L.rmax > Rv.rmax ? L.rmax : Rv.rmax);
   const int R = lay.R ? lay.R : 16;
   const int nmax = L.nmax;
-  const size_t SL = (size_t)L.d * nmax * R * R;
   if (!bwd) {
     // padded slices + the TMA landing zone of the packed object (rounded out to 16 bytes)
     const long long nfl = L.off[L.d - 1] + L.osz[L.d - 1];
-    lay.smem = sizeof(float) * SL + (size_t)((nfl * 4 + 12 + 15) / 16) * 16;
+    lay.smem = sizeof(float) * (size_t)L.d * nmax * (R * R + 4) + (size_t)((nfl * 4 + 12 + 15) / 16) * 16;
     lay.grid = gather_grid(N, num_sms() * 8);
   } else if (lay.R && plan_completion(L, same, R, &lay)) {
     long long g = (N + lay.T - 1) / lay.T;
     if (g > (long long)num_sms() * lay.bucketed) g = (long long)num_sms() * lay.bucketed;
     lay.grid = (int)(g < 1 ? 1 : g);
   } else {
-    lay.smem = sizeof(float) * ((same ? 1 : 2) * SL + (size_t)L.d * nmax * (R * R + 1) +
+    lay.smem = sizeof(float) * ((same ? 1 : 2) * (size_t)L.d * nmax * (R * R + 4) + (size_t)L.d * nmax * (R * R + 1) +
                                 (size_t)L.d * R * kGatherThreads);
     lay.grid = gather_grid(N, num_sms() * 2);
   }
