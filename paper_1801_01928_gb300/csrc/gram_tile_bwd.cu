@@ -734,26 +734,40 @@ bool gram_tile_bwd_fits_small(int na, int nb, int RA, int RB, bool single) {
   return na * (RA / 4) * nb * (RB / 4) <= 256 && gram_tile_bwd_smem(na, nb, RA, RB, single) <= kGTBSmallSmem;
 }
 
-// Largest balanced tile whose buffers fit one CTA (512 threads, one block per thread).
-void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB) {
+// Relative throughput of the half-size form (two 256-thread CTAs per SM, whose barrier and
+// load waits overlap) against one 512-thread CTA per SM on the same work.
+constexpr double kGTBHalfGain = 1.15;
+
+// Tile of a uniform batch: the balanced tile with the least work per SM, as full-size CTAs
+// (512 threads, one per SM) or half-size ones (256 threads, two per SM, half an SM's shared
+// memory with two staging buffers); one 4 x 4 block per thread either way.
+void plan_gram_tile_bwd(int RA, int RB, int batchA, int batchB, int* TA, int* TB, int* threads) {
   *TA = 1;
   *TB = 1;
+  *threads = 512;
   double best = 1e300;
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  for (int ta = 1; ta <= 16 && ta <= batchA; ++ta)
-    for (int tb = 1; tb <= 16 && tb <= batchB; ++tb) {
-      if (ta * (RA / 4) * tb * (RB / 4) > 512) continue;  // one 4 x 4 block per thread
-      if (!gram_tile_bwd_fits(ta, tb, RA, RB)) continue;
-      const long long tiles = (long long)((batchA + ta - 1) / ta) * ((batchB + tb - 1) / tb);
-      const long long per_sm = (tiles + sms - 1) / sms;
-      const double work = (double)per_sm * ta * tb * (1.0 + 0.5 / ta + 0.5 / tb);
-      if (work < best - 1e-9) {
-        best = work;
-        *TA = ta;
-        *TB = tb;
+  for (int half = 0; half <= 1; ++half)
+    for (int ta = 1; ta <= 16 && ta <= batchA; ++ta)
+      for (int tb = 1; tb <= 16 && tb <= batchB; ++tb) {
+        if (half ? !gram_tile_bwd_fits_small(ta, tb, RA, RB, false)
+                 : (ta * (RA / 4) * tb * (RB / 4) > 512 || !gram_tile_bwd_fits(ta, tb, RA, RB)))
+          continue;
+        const long long tiles = (long long)((batchA + ta - 1) / ta) * ((batchB + tb - 1) / tb);
+        const long long slots = half ? 2LL * sms : sms;
+        const long long rounds = (tiles + slots - 1) / slots;
+        // per-SM work: rounds x tile work (staging shared by the tile's pairs), two CTAs' worth
+        // per round for the half-size form at its higher throughput
+        double work = (double)rounds * ta * tb * (1.0 + 0.5 / ta + 0.5 / tb);
+        if (half) work *= 2.0 / kGTBHalfGain;
+        if (work < best - 1e-9) {
+          best = work;
+          *TA = ta;
+          *TB = tb;
+          *threads = half ? 256 : 512;
+        }
       }
-    }
 }
 
 bool gram_tile_bwd_supported(const TTV& A, const TTV& B) {
@@ -764,8 +778,8 @@ bool gram_tile_bwd_supported(const TTV& A, const TTV& B) {
 
 size_t ws_gram_tile_bwd(const TTV& A, const TTV& B) {
   const int RA = pad4b(A.rmax), RB = pad4b(B.rmax);
-  int ta, tb;
-  plan_gram_tile_bwd(RA, RB, A.batch, B.batch, &ta, &tb);
+  int ta, tb, th;
+  plan_gram_tile_bwd(RA, RB, A.batch, B.batch, &ta, &tb, &th);
   const long long tiles = (long long)((A.batch + ta - 1) / ta) * ((B.batch + tb - 1) / tb);
   const long long stride = (long long)(A.d + 1) * ta * tb * RA * RB;
   return kWsHeader + align256(sizeof(float) * stride * tiles);
@@ -780,7 +794,8 @@ t3f_status run_gram_tile_bwd(const TTV& A, const TTV& B, const float* dG, float*
   g.B = B;
   g.RA = pad4b(A.rmax);
   g.RB = pad4b(B.rmax);
-  plan_gram_tile_bwd(g.RA, g.RB, A.batch, B.batch, &g.TA, &g.TB);
+  int threads;
+  plan_gram_tile_bwd(g.RA, g.RB, A.batch, B.batch, &g.TA, &g.TB, &threads);
   g.dG = dG;
   g.dA = dA;
   g.dB = dB;
@@ -793,7 +808,7 @@ t3f_status run_gram_tile_bwd(const TTV& A, const TTV& B, const float* dG, float*
   auto go = [&](auto kern) -> t3f_status {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return T3F_ERR_CUDA;
-    kern<<<(unsigned)grid, 512, smem, s>>>(g);
+    kern<<<(unsigned)grid, threads, smem, s>>>(g);
     return T3F_OK;
   };
   T3F_CHECK(A.dtype == T3F_F32 ? go(k_gram_tile_bwd<float>) : go(k_gram_tile_bwd<__nv_bfloat16>));

@@ -373,13 +373,14 @@ static t3f_status check_like(const t3f_tt* t, const TTV& ref, TTV* v) {
 
 struct PsumLayout {
   long long ioffL[T3F_MAX_D + 1], ioffR[T3F_MAX_D + 1];
-  size_t offL, offR, offP, offQ, offW, offPart, total;
+  size_t offL, offR, offP, offQ, offW, offPart, offImg, total;
   int jchunk, nchunks;
   long long gsize;
 };
 
 static PsumLayout psum_layout(const TTV& U, const TTV& Z, bool bwd) {
   PsumLayout l;
+  l.offImg = 0;
   const long long nL = partial_offsets(U, Z, Z.batch, l.ioffL);
   for (int j = 0; j <= U.d; ++j) l.ioffR[j] = l.ioffL[j];
   l.gsize = 0;
@@ -405,6 +406,10 @@ static PsumLayout psum_layout(const TTV& U, const TTV& Z, bool bwd) {
     l.offPart = o;
     o += align256(sizeof(float) * l.gsize * l.nchunks);
     l.offP = l.offQ = l.offW = 0;
+    if (psweep_tc_supported(U, Z)) {  // operand images of the TF32 sweeps
+      l.offImg = o;
+      o += align256(psweep_tc_img_bytes(U));
+    }
   } else {
     // split the batch so that (sum_k n_k) * nchunks CTAs cover the GPU a few times
     long long slices = 0;
@@ -459,7 +464,7 @@ extern "C" t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3
   if (math == T3F_MATH_TF32) {
     int* err = static_cast<int*>(ws);
     if (cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
-    T3F_CHECK(run_psweep_tc(vu, vv, vz, Lst, l.ioffL, Rst, l.ioffR, err, s));
+    T3F_CHECK(run_psweep_tc(vu, vv, vz, Lst, l.ioffL, Rst, l.ioffR, w + l.offImg, err, s));
     T3F_CHECK(run_passemble(vu, vz, Lst, Rst, l.ioffL, c, part, l.nchunks, s));
     k_reduce_chunks<<<256, 256, 0, s>>>(part, l.nchunks, l.gsize, part);
     T3F_CHECK(launch_status());

@@ -383,11 +383,18 @@ __global__ void __launch_bounds__(512) k_passemble(const __grid_constant__ PAsse
       const unsigned qn = __umulhi((unsigned)e, mNC);  // e / NC, exact for e < 2^16
       const int col = e - (int)qn * NC, b = (int)(qn & 7), o = (int)(qn >> 3);
       const int i = col / RU, ap = col % RU;
-      const float* rr = Rk + (o * RU + ap) * kRZ;
-      const float* zz = Zk + ((o * kRZ + b) * n + i) * kRZ;
-      float s = 0.0f;
-#pragma unroll
-      for (int dl = 0; dl < kRZ; ++dl) s = fmaf(rr[dl], zz[dl], s);
+      // both 8-float rows are 32-byte aligned: two 16-byte loads each
+      const float4* rr = reinterpret_cast<const float4*>(Rk + (o * RU + ap) * kRZ);
+      const float4* zz = reinterpret_cast<const float4*>(Zk + ((o * kRZ + b) * n + i) * kRZ);
+      const float4 r0 = rr[0], r1 = rr[1], q0 = zz[0], q1 = zz[1];
+      float s = r0.x * q0.x;
+      s = fmaf(r0.y, q0.y, s);
+      s = fmaf(r0.z, q0.z, s);
+      s = fmaf(r0.w, q0.w, s);
+      s = fmaf(r1.x, q1.x, s);
+      s = fmaf(r1.y, q1.y, s);
+      s = fmaf(r1.z, q1.z, s);
+      s = fmaf(r1.w, q1.w, s);
       ST[((size_t)o * kRZ + b) * NCP + col] = s;
     }
     __syncthreads();

@@ -12,10 +12,14 @@
 //   T'[(j, gamma), (beta, i)] = sum_delta R^{(j)}[beta][delta] Z_j[gamma][i][delta]
 //   R'^{(j)}[alpha][gamma]    = sum_{(beta, i)} T'[(j, gamma), (beta, i)] V_k[alpha][i][beta]
 // T is built 4 rank indices (64 K values) at a time into one of two operand buffers while the
-// tensor cores consume the other. The Z cores of the CTA's objects arrive by TMA bulk copies
-// (one per object and core, rounded out to 16-byte boundaries). The partials are stored in the
-// layout of the CUDA-core sweeps ([r_X][r_Z] per object and interface), so the FP32 assembly
-// and gauge projection consume them unchanged.
+// tensor cores consume the other; the two threads of a row split the modes (n = 16) or the
+// rank indices (n = 8), so each loads its row's Z values once per chunk. The shared operand of
+// a core is the same for every CTA: a pre-pass writes it once per (sweep, core) into the
+// workspace as the byte image of its shared-memory layout (TF32 values), and each CTA brings
+// it in with one bulk copy, beside the Z cores of its objects (one bulk copy per object and
+// core, rounded out to 16-byte boundaries). The partials are stored in the layout of the
+// CUDA-core sweeps ([r_X][r_Z] per object and interface), so the FP32 assembly and gauge
+// projection consume them unchanged.
 //
 // Shared-memory operands are K-major without swizzle: 8-row x 16-byte core matrices, adjacent
 // along K (LBO = 128 bytes), 8-row groups SBO = (K / 4) * 128 bytes apart. Every mbarrier wait
@@ -42,16 +46,25 @@ constexpr uint32_t kPtABytes = 128u * kPtKc * 4u;            // 32 KB
 constexpr uint32_t kPtBBytes = (uint32_t)kPtRX * kPtRX * kPtNmax * 4u;  // 64 KB (K up to 512)
 constexpr int kPtZObj = kPtRZ * kPtNmax * kPtRZ + 8;       // floats per object landing (+ slack)
 constexpr uint32_t kPtTmemCols = 32;
+constexpr size_t kPtImgStride = kPtBBytes;       // bytes per (sweep, core) operand image
 
 struct PtArgs {
   TTV Z;
-  const float* X[2];             // U (left sweep) and V (right sweep) cores, packed, batch 1
-  long long Xoff[T3F_MAX_D];     // shared by U and V (equal shapes)
-  int rx[T3F_MAX_D + 1];
+  int rx[T3F_MAX_D + 1];         // X ranks (U and V have equal shapes)
   float* st[2];                  // partial stores of the two sweeps
   long long ioff[2][T3F_MAX_D + 1];
   int nblk;                      // CTAs per direction; blocks [nblk, 2 nblk) run the right sweep
   int* err;
+  const char* img;               // [2][d] operand images of kPtImgStride bytes (pre-pass output)
+};
+
+struct PtImgArgs {
+  const float* X[2];
+  long long Xoff[T3F_MAX_D];
+  int rx[T3F_MAX_D + 1];
+  int n[T3F_MAX_D];
+  int d;
+  char* img;
 };
 
 __device__ __forceinline__ uint32_t pt_smem(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -89,6 +102,32 @@ __device__ __forceinline__ uint32_t tf32_bits(float v) {
   return r;
 }
 
+// Operand image of block (sweep, core): B[o][(c, i)] = U_k[c][i][o] (left) or V_k[o][i][c]
+// (right) as TF32 in the K-major layout the sweep kernel reads (rows o < 32, zero past the
+// output rank). 16-byte unit u of the image holds row o = 8 (u / 2K) + u % 8 and the four K
+// values 4 ((u % 2K) / 8) .. + 3, so consecutive threads write consecutive bytes.
+__global__ void __launch_bounds__(256) k_psweep_tc_img(const __grid_constant__ PtImgArgs a) {
+  const int dir = (int)blockIdx.x / a.d, k = (int)blockIdx.x % a.d;
+  const int x0 = a.rx[k], x1 = a.rx[k + 1], n = a.n[k];
+  const int cr = dir == 0 ? x0 : x1, orr = dir == 0 ? x1 : x0;
+  const int K = cr * n, lgn = n == 16 ? 4 : 3;
+  const float* Xk = a.X[dir] + a.Xoff[k];
+  uint4* out = reinterpret_cast<uint4*>(a.img + (size_t)blockIdx.x * kPtImgStride);
+  for (int u = threadIdx.x; u < 8 * K; u += blockDim.x) {
+    const int g = u / (2 * K), rem = u - g * 2 * K;
+    const int o = 8 * g + (rem & 7), kk0 = 4 * (rem >> 3);
+    uint32_t v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int kk = kk0 + q, c = kk >> lgn, i = kk & (n - 1);
+      float x = 0.0f;
+      if (o < orr) x = dir == 0 ? __ldg(Xk + (long long)kk * x1 + o) : __ldg(Xk + ((long long)o * n + i) * x1 + c);
+      v[q] = tf32_bits(x);
+    }
+    out[u] = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+}
+
 __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_constant__ PtArgs a) {
   extern __shared__ __align__(128) char smem[];
   char* Abuf = smem;                                   // [2][kPtABytes]
@@ -102,7 +141,6 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
   const int d = Z.d, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int dir = (int)blockIdx.x >= a.nblk ? 1 : 0;
   const int obj0 = ((int)blockIdx.x - dir * a.nblk) * kPtObj;
-  const float* Xbase = a.X[dir];
   float* st = a.st[dir];
   const long long* ioff = a.ioff[dir];
   const int nobj = min(kPtObj, Z.batch - obj0);
@@ -140,13 +178,13 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
     const int x0 = a.rx[k], x1 = a.rx[k + 1], z0 = Z.r[k], z1 = Z.r[k + 1], n = Z.n[k];
     // the contracted X-side rank (K = cr * n) and the output X-side rank (N)
     const int cr = dir == 0 ? x0 : x1, orr = dir == 0 ? x1 : x0;
-    const int lgn = n == 16 ? 4 : 3;  // n is 8 or 16
     const int K = cr * n;
-    const uint32_t sboA = (uint32_t)(kPtKc / 4) * 128u, sboB = (uint32_t)(K / 4 + (K & 3 ? 1 : 0)) * 128u;
+    const uint32_t sboA = (uint32_t)(kPtKc / 4) * 128u;
     // ---- Z cores of the CTA's objects: one bulk copy each (landing at an aligned address)
     const long long zsz = (long long)z0 * n * z1;
+    const uint32_t sboB = (uint32_t)(K / 4) * 128u, imgb = (uint32_t)K * 128u;  // K is a multiple of 8
     if (tid == 0) {
-      uint32_t bytes = 0;
+      uint32_t bytes = imgb;
       for (int j = 0; j < nobj; ++j) {
         const float* src = Zp + core_base(Z, k, obj0 + j);
         const uintptr_t s0 = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
@@ -154,6 +192,12 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
       }
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(pt_smem(&bar_z)), "r"(bytes) : "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // the shared operand X_k (no product of the previous core is in flight: they were all
+      // waited for before its partials were read out)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       pt_smem(Bop)),
+                   "l"(a.img + (size_t)(dir * d + k) * kPtImgStride), "r"(imgb), "r"(pt_smem(&bar_z))
+                   : "memory");
       for (int j = 0; j < nobj; ++j) {
         const float* src = Zp + core_base(Z, k, obj0 + j);
         const uintptr_t s0 = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
@@ -162,23 +206,6 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
                          pt_smem(Zl + j * kPtZObj)),
                      "l"(s0), "r"(b), "r"(pt_smem(&bar_z))
                      : "memory");
-      }
-    }
-    // ---- shared operand B[o][(c, i)] = X_k (left: U[c][i][o]; right: V[o][i][c]), rows o < 32;
-    // K = cr n is a multiple of 8. Left: o varies fastest (U's contiguous index); right: c.
-    const float* Xk = Xbase + a.Xoff[k];
-    if (dir == 0) {
-      for (int e = tid; e < kPtRX * K; e += blockDim.x) {
-        const int o = e & (kPtRX - 1), kk = e >> 5;  // kk = c n + i: U[c][i][o] at kk * x1 + o
-        const float v = o < orr ? __ldg(Xk + kk * x1 + o) : 0.0f;
-        *reinterpret_cast<uint32_t*>(Bop + pt_off(o, kk, sboB)) = tf32_bits(v);
-      }
-    } else {
-      for (int e = tid; e < kPtRX * K; e += blockDim.x) {
-        const int c = e % cr, rest = e / cr;  // V[o][i][c] at (o n + i) x1 + c, c fastest
-        const int i = rest & (n - 1), o = rest >> lgn;
-        const float v = o < orr ? __ldg(Xk + (o * n + i) * x1 + c) : 0.0f;
-        *reinterpret_cast<uint32_t*>(Bop + pt_off(o, (c << lgn) + i, sboB)) = tf32_bits(v);
       }
     }
     // one thread polls the barrier, the others wait at the block barrier that follows
@@ -195,6 +222,12 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
     const int zlen = dir == 0 ? z0 : z1;
     const int zstep = dir == 0 ? n * z1 : 1;                     // stride between the 8 values
     const float* zrow = dir == 0 ? zj + zr : zj + zr * n * z1;  // + i * z1 for slice i
+    // right sweep: a row's eight values of a slice are contiguous (two 16-byte loads)
+    const bool zvec = dir == 1 && z1 == kPtRZ && (reinterpret_cast<uintptr_t>(zrow) & 15) == 0;
+    // n = 16: the row's two threads take 8 modes each for all 4 rank indices of a chunk;
+    // n = 8: 2 rank indices each for all 8 modes
+    const bool nsplit = n == 16;
+    const int nc = nsplit ? kPtChunkR : kPtChunkR / 2, iA = nsplit ? part * 8 : 0;
     for (int ch = 0; ch < nch; ++ch) {
       const int buf = ch & 1;
       // the products that read this buffer (chunk ch - 2) must be done
@@ -205,39 +238,53 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_psweep_tc(const __grid_consta
         pend[buf] = 0;
       }
       char* Ab = Abuf + buf * kPtABytes;
-      // T[row][(c - 4 ch) * 16 + i] for this thread's two rank indices c = c0, c0 + 1: the
-      // partial rows of both in registers, each slice's Z values loaded once for both
+      // T[row][(c - 4 ch) * 16 + i] for this thread's rank indices c and modes i: the partial
+      // rows in registers, each slice's Z values loaded once for all of them (rows past the
+      // rank are zero in Ls)
       {
-        const int c0 = ch * kPtChunkR + part * 2;
-        float l0[kPtRZ], l1[kPtRZ];
+        const int cA = ch * kPtChunkR + (nsplit ? 0 : part * 2);
+        float l[kPtChunkR][kPtRZ];
 #pragma unroll
-        for (int g = 0; g < kPtRZ; ++g) {  // left: L[c][gamma]; right: R[c][delta] (zero padded)
-          l0[g] = Ls[(jr * kPtRX + c0) * kPtRZ + g];
-          l1[g] = Ls[(jr * kPtRX + c0 + 1) * kPtRZ + g];
-        }
-        const bool v0 = rvalid && c0 < cr, v1 = rvalid && c0 + 1 < cr;
-        for (int i4 = 0; i4 < kPtNmax; i4 += 4) {
-          float t0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, t1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-          if (v0 && i4 < n) {
+        for (int c = 0; c < kPtChunkR; ++c)
+#pragma unroll
+          for (int g = 0; g < kPtRZ; ++g)  // left: L[c][gamma]; right: R[c][delta]
+            l[c][g] = c < nc ? Ls[(jr * kPtRX + cA + c) * kPtRZ + g] : 0.0f;
+#pragma unroll
+        for (int ih = 0; ih < 8; ih += 4) {
+          const int i4 = iA + ih;
+          float t[kPtChunkR][4];
+#pragma unroll
+          for (int c = 0; c < kPtChunkR; ++c)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t[c][u] = 0.0f;
+          if (rvalid) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const float* zp = zrow + (i4 + u) * z1;
-              float s0 = 0.0f, s1 = 0.0f;
+              float z[kPtRZ];
+              if (zvec) {
+                const float4 p = *reinterpret_cast<const float4*>(zrow + (i4 + u) * kPtRZ);
+                const float4 q = *reinterpret_cast<const float4*>(zrow + (i4 + u) * kPtRZ + 4);
+                z[0] = p.x; z[1] = p.y; z[2] = p.z; z[3] = p.w;
+                z[4] = q.x; z[5] = q.y; z[6] = q.z; z[7] = q.w;
+              } else {
+                const float* zp = zrow + (i4 + u) * z1;
 #pragma unroll
-              for (int g = 0; g < kPtRZ; ++g) {
-                const float zv = g < zlen ? zp[g * zstep] : 0.0f;
-                s0 = fmaf(l0[g], zv, s0);
-                s1 = fmaf(l1[g], zv, s1);
+                for (int g = 0; g < kPtRZ; ++g) z[g] = g < zlen ? zp[g * zstep] : 0.0f;
               }
-              t0[u] = s0;
-              t1[u] = v1 ? s1 : 0.0f;
+#pragma unroll
+              for (int c = 0; c < kPtChunkR; ++c) {
+                float sacc = 0.0f;
+#pragma unroll
+                for (int g = 0; g < kPtRZ; ++g) sacc = fmaf(l[c][g], z[g], sacc);
+                t[c][u] = sacc;
+              }
             }
           }
-          const int kk = part * 2 * kPtNmax + i4;
-          *reinterpret_cast<uint4*>(Ab + pt_off(row, kk, sboA)) =
-              make_uint4(tf32_bits(t0[0]), tf32_bits(t0[1]), tf32_bits(t0[2]), tf32_bits(t0[3]));
-          *reinterpret_cast<uint4*>(Ab + pt_off(row, kk + kPtNmax, sboA)) =
-              make_uint4(tf32_bits(t1[0]), tf32_bits(t1[1]), tf32_bits(t1[2]), tf32_bits(t1[3]));
+#pragma unroll
+          for (int c = 0; c < kPtChunkR; ++c)
+            if (c < nc)
+              *reinterpret_cast<uint4*>(Ab + pt_off(row, (cA - ch * kPtChunkR + c) * kPtNmax + i4, sboA)) =
+                  make_uint4(tf32_bits(t[c][0]), tf32_bits(t[c][1]), tf32_bits(t[c][2]), tf32_bits(t[c][3]));
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -339,20 +386,35 @@ bool psweep_tc_supported(const TTV& X, const TTV& Z) {
   return true;
 }
 
+size_t psweep_tc_img_bytes(const TTV& X) { return 2 * (size_t)X.d * kPtImgStride; }
+
 size_t psweep_tc_smem() {
   return 2 * (size_t)kPtABytes + kPtBBytes + sizeof(float) * ((size_t)kPtObj * kPtZObj + (size_t)kPtObj * kPtRX * kPtRZ);
 }
 
-// Both sweeps in one launch: the left partials of (U, Z) into stL, the right partials of
-// (V, Z) into stR (blocks [0, nblk) and [nblk, 2 nblk)).
+// The operand images (one launch over the 2 d (sweep, core) pairs), then both sweeps in one
+// launch: the left partials of (U, Z) into stL, the right partials of (V, Z) into stR (blocks
+// [0, nblk) and [nblk, 2 nblk)). img: psweep_tc_img_bytes(U) bytes, 16-byte aligned.
 t3f_status run_psweep_tc(const TTV& U, const TTV& V, const TTV& Z, float* stL, const long long* ioffL, float* stR,
-                         const long long* ioffR, int* err, cudaStream_t s) {
+                         const long long* ioffR, void* img, int* err, cudaStream_t s) {
+  if (reinterpret_cast<uintptr_t>(img) & 15) return T3F_ERR_WORKSPACE;
+  PtImgArgs ia;
+  memset(&ia, 0, sizeof(ia));
+  ia.X[0] = static_cast<const float*>(U.p);
+  ia.X[1] = static_cast<const float*>(V.p);
+  ia.d = U.d;
+  ia.img = static_cast<char*>(img);
+  for (int k = 0; k < U.d; ++k) {
+    ia.Xoff[k] = U.off[k];
+    ia.n[k] = U.n[k];
+  }
+  for (int k = 0; k <= U.d; ++k) ia.rx[k] = U.r[k];
+  k_psweep_tc_img<<<(unsigned)(2 * U.d), 256, 0, s>>>(ia);
+  T3F_CHECK(launch_status());
   PtArgs a;
   memset(&a, 0, sizeof(a));
   a.Z = Z;
-  a.X[0] = static_cast<const float*>(U.p);
-  a.X[1] = static_cast<const float*>(V.p);
-  for (int k = 0; k < U.d; ++k) a.Xoff[k] = U.off[k];
+  a.img = static_cast<const char*>(img);
   for (int k = 0; k <= U.d; ++k) {
     a.rx[k] = U.r[k];
     a.ioff[0][k] = ioffL[k];

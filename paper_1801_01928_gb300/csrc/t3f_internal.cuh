@@ -77,10 +77,12 @@ t3f_status run_psweep(const TTV& X, const TTV& Z, int dir, const float* A, const
                       float* st1, float* st2, const long long* ioff, cudaStream_t s, int* err = nullptr);
 int passemble_ranges(const TTV& Z);
 // Tensor-core (TF32) form of the project_sum sweeps (psweep_tc.cu): X ranks <= 32, Z ranks
-// <= 8, modes 8 or 16; the left (U) and right (V) sweeps in one launch.
+// <= 8, modes 8 or 16; the left (U) and right (V) sweeps in one launch after a pre-pass that
+// writes the per-core shared operands into img (psweep_tc_img_bytes(U) bytes of workspace).
 bool psweep_tc_supported(const TTV& X, const TTV& Z);
+size_t psweep_tc_img_bytes(const TTV& X);
 t3f_status run_psweep_tc(const TTV& U, const TTV& V, const TTV& Z, float* stL, const long long* ioffL, float* stR,
-                         const long long* ioffR, int* err, cudaStream_t s);
+                         const long long* ioffR, void* img, int* err, cudaStream_t s);
 t3f_status run_passemble(const TTV& X, const TTV& Z, const float* L, const float* R, const long long* ioff,
                          const float* c, float* part, int nranges, cudaStream_t s);
 t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V, const float* W, const float* L,
