@@ -373,7 +373,7 @@ static t3f_status check_like(const t3f_tt* t, const TTV& ref, TTV* v) {
 
 struct PsumLayout {
   long long ioffL[T3F_MAX_D + 1], ioffR[T3F_MAX_D + 1];
-  size_t offL, offR, offP, offQ, offW, offPart, offImg, total;
+  size_t offL, offR, offP, offQ, offW, offPart, offImg, offXT, total;
   int jchunk, nchunks;
   long long gsize;
 };
@@ -381,6 +381,7 @@ struct PsumLayout {
 static PsumLayout psum_layout(const TTV& U, const TTV& Z, bool bwd) {
   PsumLayout l;
   l.offImg = 0;
+  l.offXT = 0;
   const long long nL = partial_offsets(U, Z, Z.batch, l.ioffL);
   for (int j = 0; j <= U.d; ++j) l.ioffR[j] = l.ioffL[j];
   l.gsize = 0;
@@ -397,6 +398,10 @@ static PsumLayout psum_layout(const TTV& U, const TTV& Z, bool bwd) {
     o += align256(sizeof(float) * nL);
     l.offW = o;
     o += align256(sizeof(float) * l.gsize);
+    if (psweep_supported(U, Z)) {  // transposed V, U, W for the right sweep and the gradients
+      l.offXT = o;
+      o += align256(sizeof(float) * 3 * xtranspose_offsets(U, nullptr));
+    }
     l.jchunk = 0;
     l.nchunks = 0;
     l.offPart = 0;
@@ -406,6 +411,8 @@ static PsumLayout psum_layout(const TTV& U, const TTV& Z, bool bwd) {
     l.offPart = o;
     o += align256(sizeof(float) * l.gsize * l.nchunks);
     l.offP = l.offQ = l.offW = 0;
+    l.offXT = o;  // transposed V for the right sweep
+    o += align256(sizeof(float) * xtranspose_offsets(U, nullptr));
     if (psweep_tc_supported(U, Z)) {  // operand images of the TF32 sweeps
       l.offImg = o;
       o += align256(psweep_tc_img_bytes(U));
@@ -474,7 +481,13 @@ extern "C" t3f_status t3f_project_sum(const t3f_tt* U, const t3f_tt* V, const t3
     int* err = static_cast<int*>(ws);
     if (cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
     T3F_CHECK(run_psweep(vu, vz, 0, static_cast<const float*>(vu.p), nullptr, nullptr, Lst, nullptr, l.ioffL, s, err));
-    T3F_CHECK(run_psweep(vv, vz, 1, static_cast<const float*>(vv.p), nullptr, nullptr, Rst, nullptr, l.ioffR, s, err));
+    // the right sweep stages its slices from a transposed copy of V (16-byte copies)
+    float* VT = reinterpret_cast<float*>(w + l.offXT);
+    long long toff[T3F_MAX_D];
+    xtranspose_offsets(vv, toff);
+    const float* vsrc[1] = {static_cast<const float*>(vv.p)};
+    T3F_CHECK(run_xtranspose(vv, vsrc, 1, VT, s));
+    T3F_CHECK(run_psweep(vv, vz, 1, VT, nullptr, nullptr, Rst, nullptr, l.ioffR, s, err, toff));
     T3F_CHECK(run_passemble(vu, vz, Lst, Rst, l.ioffL, c, part, l.nchunks, s));
     k_reduce_chunks<<<256, 256, 0, s>>>(part, l.nchunks, l.gsize, part);
     T3F_CHECK(launch_status());
@@ -538,9 +551,17 @@ extern "C" t3f_status t3f_project_sum_backward(const t3f_tt* U, const t3f_tt* V,
     int* err = static_cast<int*>(ws);
     if (cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess) return T3F_ERR_CUDA;
     T3F_CHECK(run_psweep(vu, vz, 0, Up, Vp, Wc, Lst, Pst, l.ioffL, s, err));
-    T3F_CHECK(run_psweep(vu, vz, 1, Vp, Up, Wc, Rst, Qst, l.ioffL, s, err));
-    return run_pgrad(vu, vz, Up, Vp, Wc, Lst, Rst, Pst, Qst, l.ioffL, c, dZ ? static_cast<float*>(vdz.p) : nullptr,
-                     dc, s);
+    // the right sweep and the gradient kernel stage their slices from transposed copies of
+    // V, U and W (16-byte copies)
+    float* XT = reinterpret_cast<float*>(w + l.offXT);
+    long long toff[T3F_MAX_D];
+    const long long tsz = xtranspose_offsets(vu, toff);
+    const float* srcs[3] = {Vp, Up, Wc};
+    T3F_CHECK(run_xtranspose(vu, srcs, 3, XT, s));
+    const float *VT = XT, *UT = XT + tsz, *WT = XT + 2 * tsz;
+    T3F_CHECK(run_psweep(vu, vz, 1, VT, UT, WT, Rst, Qst, l.ioffL, s, err, toff));
+    return run_pgrad(vu, vz, UT, VT, WT, Lst, Rst, Pst, Qst, l.ioffL, c, dZ ? static_cast<float*>(vdz.p) : nullptr,
+                     dc, s, toff);
   }
   T3F_CHECK(run_pair_sweep(vu, vz, 0, nullptr, Lst, l.ioffL, s));
   T3F_CHECK(run_pair_sweep(vv, vz, 1, nullptr, Rst, l.ioffR, s));

@@ -34,6 +34,7 @@ struct PSweepArgs {
   long long ioff[T3F_MAX_D + 1];
   int J, SPLIT;
   int* err;  // device error word (nullable): a bounded wait that ran out
+  int xt;    // right sweep: A / B1 / B2 are transposed copies (r1 x n x r0 cores, see k_xtranspose)
 };
 
 __device__ __forceinline__ void fma4x4(float (&acc)[4][4], const float4 a, const float4 b) {
@@ -70,6 +71,30 @@ __device__ __forceinline__ void stage_x_slice_async(float* dst, const float* cor
     const float* src = ok ? core + ((long long)row * n + i) * r1 + col : core;
     const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + e);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(ok ? 4 : 0));
+  }
+}
+
+// Transposed copies Y_k[c][i][r] = X_k[r][i][c] of up to three X-side TTs (batch 1), core k
+// at toff[k] (a multiple of 4 floats) of set t's block of tsize floats. A right-style slice
+// As[K][m] = X_k[m][i][K] is then the left-style slice Y_k[K][i][m], which the right sweeps and
+// the gradient kernel stage with 16-byte copies. One block per (set, core); writes coalesced.
+struct XTransArgs {
+  const float* src[3];
+  long long soff[T3F_MAX_D], toff[T3F_MAX_D];
+  int r[T3F_MAX_D + 1], n[T3F_MAX_D];
+  int d;
+  long long tsize;
+  float* dst;
+};
+
+__global__ void __launch_bounds__(256) k_xtranspose(const __grid_constant__ XTransArgs a) {
+  const int t = (int)blockIdx.x / a.d, k = (int)blockIdx.x % a.d;
+  const int r0 = a.r[k], r1 = a.r[k + 1], n = a.n[k], nr0 = n * r0;
+  const float* X = a.src[t] + a.soff[k];
+  float* Y = a.dst + (long long)t * a.tsize + a.toff[k];
+  for (int e = threadIdx.x; e < r1 * nr0; e += blockDim.x) {
+    const int c = e / nr0, rem = e - c * nr0, i = rem / r0, r = rem - i * r0;
+    Y[e] = __ldg(X + ((long long)r * n + i) * r1 + c);
   }
 }
 
@@ -137,12 +162,14 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
     const int kx = a.dir == 0 ? st : d - 1 - st;
     const int xr0 = a.ra[kx], xr1 = a.ra[kx + 1], xn = Z.n[kx];
     float* X0 = Xs + (size_t)buf * NX * SP * RU * RU;
+    // transposed copies (right sweep): the left-style staging of the r1 x n x r0 cores
+    const int sr0 = a.xt ? xr1 : xr0, sr1 = a.xt ? xr0 : xr1, sdir = a.xt ? 0 : a.dir;
     for (int hh = 0; hh < SP; ++hh) {
       const int i = ib * SP + hh;
-      stage_x_slice_async<RU>(X0 + (size_t)hh * RU * RU, a.A + a.Aoff[kx], xr0, xn, xr1, i, a.dir, i < xn);
+      stage_x_slice_async<RU>(X0 + (size_t)hh * RU * RU, a.A + a.Aoff[kx], sr0, xn, sr1, i, sdir, i < xn);
       if (MIXED) {
-        stage_x_slice_async<RU>(X0 + (size_t)(SP + hh) * RU * RU, a.B1 + a.B1off[kx], xr0, xn, xr1, i, a.dir, i < xn);
-        stage_x_slice_async<RU>(X0 + (size_t)(2 * SP + hh) * RU * RU, a.B2 + a.B2off[kx], xr0, xn, xr1, i, a.dir,
+        stage_x_slice_async<RU>(X0 + (size_t)(SP + hh) * RU * RU, a.B1 + a.B1off[kx], sr0, xn, sr1, i, sdir, i < xn);
+        stage_x_slice_async<RU>(X0 + (size_t)(2 * SP + hh) * RU * RU, a.B2 + a.B2off[kx], sr0, xn, sr1, i, sdir,
                                 i < xn);
       }
     }
@@ -453,6 +480,7 @@ struct PGradFastArgs {
   float* dZ;
   float* dc;
   int J, SPLIT, ntiles;
+  int xt;  // U / V / W are transposed copies (r1 x n x r0 cores, see k_xtranspose)
 };
 
 template <int RU>
@@ -490,11 +518,12 @@ __global__ void __launch_bounds__(RU == 32 ? 512 : 256) k_pgrad(const __grid_con
   // slices of batch ib, right-style (As[K][m] = X_k[m][i][K]), as one commit group; the next
   // batch is issued once the current one has been consumed, so its copies overlap the dZ step
   auto issue_batch = [&](int ib) {
+    const int sr0 = a.xt ? r1 : r0, sr1 = a.xt ? r0 : r1, sdir = a.xt ? 0 : 1;
     for (int hh = 0; hh < SP; ++hh) {
       const int i = ib * SP + hh;
-      stage_x_slice_async<RU>(Xs + (size_t)(0 * SP + hh) * RU * RU, a.V + a.Xoff[k], r0, n, r1, i, 1, i < n);
-      stage_x_slice_async<RU>(Xs + (size_t)(1 * SP + hh) * RU * RU, a.W + a.Xoff[k], r0, n, r1, i, 1, i < n);
-      stage_x_slice_async<RU>(Xs + (size_t)(2 * SP + hh) * RU * RU, a.U + a.Xoff[k], r0, n, r1, i, 1, i < n);
+      stage_x_slice_async<RU>(Xs + (size_t)(0 * SP + hh) * RU * RU, a.V + a.Xoff[k], sr0, n, sr1, i, sdir, i < n);
+      stage_x_slice_async<RU>(Xs + (size_t)(1 * SP + hh) * RU * RU, a.W + a.Xoff[k], sr0, n, sr1, i, sdir, i < n);
+      stage_x_slice_async<RU>(Xs + (size_t)(2 * SP + hh) * RU * RU, a.U + a.Xoff[k], sr0, n, sr1, i, sdir, i < n);
     }
     asm volatile("cp.async.commit_group;\n" ::);
   };
@@ -616,7 +645,7 @@ static t3f_status launch_psweep_t(PSweepArgs& a, cudaStream_t s) {
 
 // dir 0: left sweep (A = U [, B1 = V, B2 = W]); dir 1: right sweep (A = V [, B1 = U, B2 = W]).
 t3f_status run_psweep(const TTV& X, const TTV& Z, int dir, const float* A, const float* B1, const float* B2,
-                      float* st1, float* st2, const long long* ioff, cudaStream_t s, int* err) {
+                      float* st1, float* st2, const long long* ioff, cudaStream_t s, int* err, const long long* xtoff) {
   PSweepArgs a;
   memset(&a, 0, sizeof(a));
   a.err = err;
@@ -624,7 +653,8 @@ t3f_status run_psweep(const TTV& X, const TTV& Z, int dir, const float* A, const
   a.A = A;
   a.B1 = B1;
   a.B2 = B2;
-  for (int k = 0; k < X.d; ++k) a.Aoff[k] = a.B1off[k] = a.B2off[k] = X.off[k];
+  a.xt = xtoff != nullptr && dir == 1;
+  for (int k = 0; k < X.d; ++k) a.Aoff[k] = a.B1off[k] = a.B2off[k] = a.xt ? xtoff[k] : X.off[k];
   for (int k = 0; k <= X.d; ++k) {
     a.ra[k] = X.r[k];
     a.ioff[k] = ioff[k];
@@ -640,6 +670,32 @@ t3f_status run_psweep(const TTV& X, const TTV& Z, int dir, const float* A, const
     case 16: return mixed ? launch_psweep_t<16, true>(a, s) : launch_psweep_t<16, false>(a, s);
     default: return mixed ? launch_psweep_t<32, true>(a, s) : launch_psweep_t<32, false>(a, s);
   }
+}
+
+long long xtranspose_offsets(const TTV& X, long long* toff) {
+  long long o = 0;
+  for (int k = 0; k < X.d; ++k) {
+    if (toff) toff[k] = o;
+    o += (X.osz[k] + 3) & ~3LL;
+  }
+  return o;
+}
+
+t3f_status run_xtranspose(const TTV& X, const float* const* srcs, int nsets, float* dst, cudaStream_t s) {
+  if (nsets < 1 || nsets > 3 || (reinterpret_cast<uintptr_t>(dst) & 15)) return T3F_ERR_ARG;
+  XTransArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int t = 0; t < nsets; ++t) a.src[t] = srcs[t];
+  a.d = X.d;
+  a.dst = dst;
+  a.tsize = xtranspose_offsets(X, a.toff);
+  for (int k = 0; k < X.d; ++k) {
+    a.soff[k] = X.off[k];
+    a.n[k] = X.n[k];
+  }
+  for (int k = 0; k <= X.d; ++k) a.r[k] = X.r[k];
+  k_xtranspose<<<(unsigned)(nsets * X.d), 256, 0, s>>>(a);
+  return launch_status();
 }
 
 int passemble_ranges(const TTV& Z) {
@@ -707,14 +763,15 @@ static t3f_status launch_pgrad_t(PGradFastArgs& a, cudaStream_t s) {
 
 t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V, const float* W, const float* L,
                      const float* R, const float* P, const float* Q, const long long* ioff, const float* c, float* dZ,
-                     float* dc, cudaStream_t s) {
+                     float* dc, cudaStream_t s, const long long* xtoff) {
   PGradFastArgs a;
   memset(&a, 0, sizeof(a));
   a.Z = Z;
   a.U = U;
   a.V = V;
   a.W = W;
-  for (int k = 0; k < X.d; ++k) a.Xoff[k] = X.off[k];
+  a.xt = xtoff != nullptr;
+  for (int k = 0; k < X.d; ++k) a.Xoff[k] = a.xt ? xtoff[k] : X.off[k];
   for (int k = 0; k <= X.d; ++k) {
     a.ra[k] = X.r[k];
     a.ioff[k] = ioff[k];

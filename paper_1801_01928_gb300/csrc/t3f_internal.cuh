@@ -73,8 +73,15 @@ t3f_status run_gauge_project(const TTV& U, const float* Z, float* out, cudaStrea
 
 // Register-tiled project_sum sweeps (psweep.cu): X side ranks <= 32, Z ranks <= 8.
 bool psweep_supported(const TTV& X, const TTV& Z);
+// xtoff (right sweep only): A / B1 / B2 are transposed copies written by run_xtranspose, core k
+// at xtoff[k]
 t3f_status run_psweep(const TTV& X, const TTV& Z, int dir, const float* A, const float* B1, const float* B2,
-                      float* st1, float* st2, const long long* ioff, cudaStream_t s, int* err = nullptr);
+                      float* st1, float* st2, const long long* ioff, cudaStream_t s, int* err = nullptr,
+                      const long long* xtoff = nullptr);
+// Transposed copies Y_k[c][i][r] = X_k[r][i][c] of nsets (<= 3) X-shaped TTs into dst (16-byte
+// aligned; set t at t * xtranspose_offsets(X, nullptr) floats, core k at toff[k]).
+long long xtranspose_offsets(const TTV& X, long long* toff);
+t3f_status run_xtranspose(const TTV& X, const float* const* srcs, int nsets, float* dst, cudaStream_t s);
 int passemble_ranges(const TTV& Z);
 // Tensor-core (TF32) form of the project_sum sweeps (psweep_tc.cu): X ranks <= 32, Z ranks
 // <= 8, modes 8 or 16; the left (U) and right (V) sweeps in one launch after a pre-pass that
@@ -87,7 +94,7 @@ t3f_status run_passemble(const TTV& X, const TTV& Z, const float* L, const float
                          const float* c, float* part, int nranges, cudaStream_t s);
 t3f_status run_pgrad(const TTV& X, const TTV& Z, const float* U, const float* V, const float* W, const float* L,
                      const float* R, const float* P, const float* Q, const long long* ioff, const float* c, float* dZ,
-                     float* dc, cudaStream_t s);
+                     float* dc, cudaStream_t s, const long long* xtoff = nullptr);
 
 // Tiled Gram sweep (gram_tile.cu): ranks <= 64, F32 or BF16 cores.
 bool gram_tile_supported(const TTV& A, const TTV& B);

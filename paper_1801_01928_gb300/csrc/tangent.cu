@@ -627,7 +627,7 @@ t3f_status coords_view(const t3f_tt* t, const TTV& U, int batch, TTV* v) {
 
 struct ProjectLayout {
   long long ioff[T3F_MAX_D + 1];
-  size_t offL, offR, total;
+  size_t offL, offR, offXT, total;
 };
 
 ProjectLayout project_layout(const TTV& U, const TTV& Z) {
@@ -635,7 +635,8 @@ ProjectLayout project_layout(const TTV& U, const TTV& Z) {
   const long long nL = partial_offsets(U, Z, Z.batch, l.ioff);
   l.offL = kWsHeader;
   l.offR = l.offL + align256(sizeof(float) * nL);
-  l.total = l.offR + align256(sizeof(float) * nL);
+  l.offXT = l.offR + align256(sizeof(float) * nL);  // transposed V for the right sweep
+  l.total = l.offXT + align256(sizeof(float) * xtranspose_offsets(U, nullptr));
   return l;
 }
 
@@ -683,7 +684,13 @@ extern "C" t3f_status t3f_project(const t3f_tt* U, const t3f_tt* V, const t3f_tt
   float* Rst = reinterpret_cast<float*>(w + l.offR);
   if (psweep_supported(vu, vz)) {
     T3F_CHECK(run_psweep(vu, vz, 0, static_cast<const float*>(vu.p), nullptr, nullptr, Lst, nullptr, l.ioff, s));
-    T3F_CHECK(run_psweep(vv, vz, 1, static_cast<const float*>(vv.p), nullptr, nullptr, Rst, nullptr, l.ioff, s));
+    // the right sweep stages its slices from a transposed copy of V (16-byte copies)
+    float* VT = reinterpret_cast<float*>(w + l.offXT);
+    long long toff[T3F_MAX_D];
+    xtranspose_offsets(vv, toff);
+    const float* vsrc[1] = {static_cast<const float*>(vv.p)};
+    T3F_CHECK(run_xtranspose(vv, vsrc, 1, VT, s));
+    T3F_CHECK(run_psweep(vv, vz, 1, VT, nullptr, nullptr, Rst, nullptr, l.ioff, s, nullptr, toff));
   } else {
     T3F_CHECK(run_pair_sweep(vu, vz, 0, nullptr, Lst, l.ioff, s));
     T3F_CHECK(run_pair_sweep(vv, vz, 1, nullptr, Rst, l.ioff, s));
