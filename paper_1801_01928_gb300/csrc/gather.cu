@@ -901,8 +901,9 @@ extern "C" t3f_status t3f_gather_backward(const t3f_tt* X, const int32_t* idx, i
   // the compact gradient layout equals the packed layout of a batch-1 descriptor
   float* target = out;
   if (riemannian) {
-    // reduce into the tail of the workspace region? reuse the first partial slot instead
-    target = gp;  // partial 0 is overwritten by the sum (read before write per element)
+    // the Riemannian form sums into partial slot 0 (every element is read before it is
+    // written) and the gauge projection writes the output from there
+    target = gp;
   }
   k_reduce_partials<<<num_sms() * 4, 256, 0, s>>>(gp, lay.grid, g.gsize, target);
   T3F_CHECK(launch_status());

@@ -12,13 +12,16 @@
 //   Q_d = 0, Q_k = sum_i (U_k Q_{k+1} + W_k R_{k+1}) Z_k^T                (mixed right sweep)
 //   dZ_j^k[:, i, :] = c_j (P_k^T V_k R_{k+1} + L_k^T W_k R_{k+1} + L_k^T U_k Q_{k+1})
 //   dc_j = P_d
+#include <algorithm>
+
 #include "t3f_internal.cuh"
 
 namespace t3f {
 
 // ---------------------------------------------------------------------------------------
 // Gauge projection: out_k = Z_k - U_k (U_k^T Z_k) on the (r_{k-1} n_k) x r_k unfoldings.
-// One CTA per core.
+// One CTA per core: staged in shared memory (gauge_core_staged) when the largest core fits,
+// else both steps read global memory.
 // ---------------------------------------------------------------------------------------
 struct GaugeArgs {
   TTV U;
@@ -28,8 +31,8 @@ struct GaugeArgs {
 };
 
 __global__ void __launch_bounds__(256) k_gauge(const __grid_constant__ GaugeArgs a) {
-  extern __shared__ float sm[];
-  const int k = blockIdx.x;
+  extern __shared__ __align__(16) float sm[];
+  const int k = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const TTV& U = a.U;
   const int r0 = U.r[k], n = U.n[k], r1 = U.r[k + 1];
   const int m = r0 * n;
@@ -37,35 +40,25 @@ __global__ void __launch_bounds__(256) k_gauge(const __grid_constant__ GaugeArgs
   const float* Zk = a.Z + U.off[k];
   float* Ok = a.out + U.off[k];
   if (k == U.d - 1) {
-    for (int e = threadIdx.x; e < m * r1; e += blockDim.x) Ok[e] = Zk[e];
+    for (int e = tid; e < m * r1; e += nth) Ok[e] = Zk[e];
     return;
   }
-  // U_k and Z_k staged in shared memory when they fit (the host sizes the launch), else read
-  // from global memory
-  float* G = sm;  // r1 x r1: G = U^T Z
-  const bool staged = a.staged;
-  float* Us = G + U.rmax * U.rmax;
-  float* Zs = Us + (staged ? m * r1 : 0);
-  if (staged) {
-    for (int e = threadIdx.x; e < m * r1; e += blockDim.x) {
-      Us[e] = __ldg(Uk + e);
-      Zs[e] = Zk[e];
-    }
-    __syncthreads();
+  if (a.staged) {
+    gauge_core_staged(Uk, Zk, Ok, m, r1, sm);
+    return;
   }
-  const float* Ur = staged ? Us : Uk;
-  const float* Zr = staged ? Zs : Zk;
-  for (int e = threadIdx.x; e < r1 * r1; e += blockDim.x) {
+  float* G = sm;  // r1 x r1: G = U^T Z
+  for (int e = tid; e < r1 * r1; e += nth) {
     const int a1 = e / r1, b1 = e % r1;
     float s = 0.0f;
-    for (int q = 0; q < m; ++q) s = fmaf(Ur[q * r1 + a1], Zr[q * r1 + b1], s);
+    for (int q = 0; q < m; ++q) s = fmaf(__ldg(Uk + q * r1 + a1), Zk[q * r1 + b1], s);
     G[e] = s;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < m * r1; e += blockDim.x) {
+  for (int e = tid; e < m * r1; e += nth) {
     const int q = e / r1, b1 = e % r1;
-    float s = Zr[e];
-    for (int a1 = 0; a1 < r1; ++a1) s = fmaf(-Ur[q * r1 + a1], G[a1 * r1 + b1], s);
+    float s = Zk[e];
+    for (int a1 = 0; a1 < r1; ++a1) s = fmaf(-__ldg(Uk + q * r1 + a1), G[a1 * r1 + b1], s);
     Ok[e] = s;
   }
 }
@@ -75,12 +68,11 @@ t3f_status run_gauge_project(const TTV& U, const float* Z, float* out, cudaStrea
   a.U = U;
   a.Z = Z;
   a.out = out;
-  long long mr = 0;
-  for (int k = 0; k + 1 < U.d; ++k) mr = mr > U.osz[k] ? mr : U.osz[k];
+  long long full = 0;
+  for (int k = 0; k + 1 < U.d; ++k) full = std::max(full, gauge_staged_floats(U.r[k] * U.n[k], U.r[k + 1]));
   const size_t base = sizeof(float) * U.rmax * U.rmax;
-  const size_t full = base + sizeof(float) * 2 * (size_t)mr;
-  a.staged = full <= 200 * 1024 ? 1 : 0;
-  const size_t smem = a.staged ? full : base;
+  a.staged = sizeof(float) * (size_t)full <= 200 * 1024 ? 1 : 0;
+  const size_t smem = a.staged ? std::max(sizeof(float) * (size_t)full, base) : base;
   if (cudaFuncSetAttribute(k_gauge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return T3F_ERR_CUDA;
   k_gauge<<<U.d, 256, smem, s>>>(a);

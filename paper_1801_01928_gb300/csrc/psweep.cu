@@ -77,7 +77,8 @@ __device__ __forceinline__ void stage_x_slice_async(float* dst, const float* cor
 // Transposed copies Y_k[c][i][r] = X_k[r][i][c] of up to three X-side TTs (batch 1), core k
 // at toff[k] (a multiple of 4 floats) of set t's block of tsize floats. A right-style slice
 // As[K][m] = X_k[m][i][K] is then the left-style slice Y_k[K][i][m], which the right sweeps and
-// the gradient kernel stage with 16-byte copies. One block per (set, core); writes coalesced.
+// the gradient kernel stage with 16-byte copies. kXtParts blocks per (set, core), each a
+// contiguous range of the output; writes coalesced.
 struct XTransArgs {
   const float* src[3];
   long long soff[T3F_MAX_D], toff[T3F_MAX_D];
@@ -87,12 +88,16 @@ struct XTransArgs {
   float* dst;
 };
 
+constexpr int kXtParts = 8;
+
 __global__ void __launch_bounds__(256) k_xtranspose(const __grid_constant__ XTransArgs a) {
-  const int t = (int)blockIdx.x / a.d, k = (int)blockIdx.x % a.d;
-  const int r0 = a.r[k], r1 = a.r[k + 1], n = a.n[k], nr0 = n * r0;
+  const int part = (int)blockIdx.x % kXtParts, tk = (int)blockIdx.x / kXtParts;
+  const int t = tk / a.d, k = tk % a.d;
+  const int r0 = a.r[k], r1 = a.r[k + 1], n = a.n[k], nr0 = n * r0, sz = r1 * nr0;
   const float* X = a.src[t] + a.soff[k];
   float* Y = a.dst + (long long)t * a.tsize + a.toff[k];
-  for (int e = threadIdx.x; e < r1 * nr0; e += blockDim.x) {
+  const int e1 = (int)(((long long)(part + 1) * sz) / kXtParts);
+  for (int e = (int)(((long long)part * sz) / kXtParts) + threadIdx.x; e < e1; e += blockDim.x) {
     const int c = e / nr0, rem = e - c * nr0, i = rem / r0, r = rem - i * r0;
     Y[e] = __ldg(X + ((long long)r * n + i) * r1 + c);
   }
@@ -694,7 +699,7 @@ t3f_status run_xtranspose(const TTV& X, const float* const* srcs, int nsets, flo
     a.n[k] = X.n[k];
   }
   for (int k = 0; k <= X.d; ++k) a.r[k] = X.r[k];
-  k_xtranspose<<<(unsigned)(nsets * X.d), 256, 0, s>>>(a);
+  k_xtranspose<<<(unsigned)(nsets * X.d * kXtParts), 256, 0, s>>>(a);
   return launch_status();
 }
 

@@ -46,6 +46,86 @@ __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p, long
 constexpr size_t kWsHeader = 256;
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Gauge projection of one core on its m x r1 unfolding, staged in shared memory (paper
+// Section 3.2: out = Z - U (U^T Z), U with orthonormal columns): U and Z land with their
+// columns zero-padded to R4 = r1 rounded up to 4; G = U^T Z is formed in 4 x 4 register
+// blocks with the row range split over the threads left over (partial blocks summed in
+// shared memory); each thread item of the update takes one row and four columns of Z - U G.
+// Z is read completely before out is written, so out may alias Z. Every thread of the block
+// calls it; sm holds gauge_staged_floats(m, r1) floats, 16-byte aligned.
+__host__ __device__ inline int gauge_parts(int r1) {
+  const int q = (r1 + 3) / 4, nb = q * q, p = 256 / nb;
+  return p < 1 ? 1 : (p > 8 ? 8 : p);
+}
+__host__ __device__ inline long long gauge_staged_floats(int m, int r1) {
+  const long long R4 = (r1 + 3) & ~3;
+  return R4 * R4 * (1 + gauge_parts(r1)) + 2LL * m * R4;
+}
+__device__ __forceinline__ void gauge_core_staged(const float* Uk, const float* Zk, float* Ok, int m, int r1,
+                                                  float* sm) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int R4 = (r1 + 3) & ~3, Q = R4 / 4, nblk = Q * Q, parts = gauge_parts(r1);
+  float* G = sm;                        // R4 x R4
+  float* Gp = G + R4 * R4;              // parts x R4 x R4 partial blocks
+  float* Us = Gp + parts * R4 * R4;     // m x R4
+  float* Zs = Us + m * R4;              // m x R4
+  for (int e = tid; e < m * R4; e += nth) {
+    const int q = e / R4, c = e - q * R4;
+    Us[e] = c < r1 ? __ldg(Uk + q * r1 + c) : 0.0f;
+    Zs[e] = c < r1 ? Zk[q * r1 + c] : 0.0f;
+  }
+  __syncthreads();
+  for (int w = tid; w < nblk * parts; w += nth) {
+    const int blk = w % nblk, p = w / nblk, ga = blk / Q, gb = blk - ga * Q;
+    const int q0 = (int)(((long long)p * m) / parts), q1 = (int)(((long long)(p + 1) * m) / parts);
+    float acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.0f;
+    for (int q = q0; q < q1; ++q) {
+      const float4 u = *reinterpret_cast<const float4*>(Us + q * R4 + 4 * ga);
+      const float4 z = *reinterpret_cast<const float4*>(Zs + q * R4 + 4 * gb);
+      const float uv[4] = {u.x, u.y, u.z, u.w}, zv[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(uv[x], zv[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+      *reinterpret_cast<float4*>(Gp + (size_t)p * R4 * R4 + (4 * ga + x) * R4 + 4 * gb) =
+          make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
+  }
+  __syncthreads();
+  for (int e = tid; e < R4 * R4; e += nth) {
+    float s = 0.0f;
+    for (int p = 0; p < parts; ++p) s += Gp[(size_t)p * R4 * R4 + e];
+    G[e] = s;
+  }
+  __syncthreads();
+  for (int w = tid; w < m * Q; w += nth) {
+    const int q = w / Q, gb = w - q * Q;
+    const float4 z = *reinterpret_cast<const float4*>(Zs + q * R4 + 4 * gb);
+    float o[4] = {z.x, z.y, z.z, z.w};
+    for (int a4 = 0; a4 < R4; a4 += 4) {
+      const float4 u = *reinterpret_cast<const float4*>(Us + q * R4 + a4);
+      const float uv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const float4 g = *reinterpret_cast<const float4*>(G + (a4 + x) * R4 + 4 * gb);
+        o[0] = fmaf(-uv[x], g.x, o[0]);
+        o[1] = fmaf(-uv[x], g.y, o[1]);
+        o[2] = fmaf(-uv[x], g.z, o[2]);
+        o[3] = fmaf(-uv[x], g.w, o[3]);
+      }
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+      if (4 * gb + y < r1) Ok[q * r1 + 4 * gb + y] = o[y];
+  }
+}
+
 t3f_status check_ws(void* ws, size_t ws_bytes, size_t need);
 t3f_status launch_status();  // cudaGetLastError() mapped to a status
 

@@ -22,21 +22,27 @@ constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------------------------------
 // Batched gauge projection, in place: D_j,k <- D_j,k - U_k (U_k^T D_j,k) on the
-// (r_{k-1} n_k) x r_k unfoldings, k < d. One CTA per (object j, core k).
+// (r_{k-1} n_k) x r_k unfoldings, k < d. One CTA per (object j, core k), staged in shared
+// memory (gauge_core_staged) when the largest core fits.
 // ---------------------------------------------------------------------------------------
 struct GaugeBatchArgs {
   TTV U;     // batch 1
   TTV D;     // batch P, U's shape (coordinates, modified in place)
+  int staged;
 };
 
 __global__ void __launch_bounds__(kThreads) k_gauge_batch(const __grid_constant__ GaugeBatchArgs a) {
-  extern __shared__ float G[];  // r1 x r1
+  extern __shared__ __align__(16) float G[];  // r1 x r1, or the staged buffers
   const int dm1 = a.U.d - 1;
   const int k = blockIdx.x % dm1, j = blockIdx.x / dm1;
   const int r0 = a.U.r[k], n = a.U.n[k], r1 = a.U.r[k + 1];
   const int m = r0 * n;
   const float* Uk = static_cast<const float*>(a.U.p) + a.U.off[k];
   float* Dk = static_cast<float*>(a.D.p) + core_base(a.D, k, j);
+  if (a.staged) {
+    gauge_core_staged(Uk, Dk, Dk, m, r1, G);
+    return;
+  }
   for (int e = threadIdx.x; e < r1 * r1; e += blockDim.x) {
     const int p = e / r1, q = e % r1;
     float s = 0.0f;
@@ -57,9 +63,16 @@ t3f_status gauge_batch(const TTV& U, const TTV& D, cudaStream_t s) {
   GaugeBatchArgs a;
   a.U = U;
   a.D = D;
+  long long full = 0;
+  for (int k = 0; k + 1 < U.d; ++k) full = std::max(full, gauge_staged_floats(U.r[k] * U.n[k], U.r[k + 1]));
+  const size_t base = sizeof(float) * U.rmax * U.rmax;
+  a.staged = sizeof(float) * (size_t)full <= 200 * 1024 ? 1 : 0;
+  const size_t smem = a.staged ? std::max(sizeof(float) * (size_t)full, base) : base;
+  if (cudaFuncSetAttribute(k_gauge_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return T3F_ERR_CUDA;
   const long long grid = (long long)(U.d - 1) * D.batch;
   if (grid > 0x7fffffffLL) return T3F_ERR_UNSUPPORTED;
-  k_gauge_batch<<<(unsigned)grid, kThreads, sizeof(float) * U.rmax * U.rmax, s>>>(a);
+  k_gauge_batch<<<(unsigned)grid, kThreads, smem, s>>>(a);
   return launch_status();
 }
 
