@@ -278,9 +278,10 @@ extern "C" t3f_status t3f_norm(const t3f_tt* A, double* out, void* ws, size_t ws
   if (va.rmax > T3F_MAX_RANK) return T3F_ERR_UNSUPPORTED;
   if (!out) return T3F_ERR_ARG;
   T3F_CHECK(check_ws(ws, ws_bytes, ws_norm(va)));
+  if (va.batch == 0) return T3F_OK;
   float* sq = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeader);
   cudaStream_t s = (cudaStream_t)stream;
-  T3F_CHECK(run_zip_sweep(va, va, sq, s));
+  T3F_CHECK(run_self_sweep(va, sq, s));
   k_sqrt64<<<(va.batch + 255) / 256, 256, 0, s>>>(sq, out, va.batch);
   return launch_status();
 }

@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(512) k_passemble(const __grid_constant__ PAsse
 #pragma unroll
     for (int y = 0; y < 16; ++y) acc[x][y] = 0.0f;
   const int jb = rg * a.range, je = min(Z.batch, jb + a.range);
-  const unsigned mn = 0xffffffffu / (unsigned)n + 1u, mNC = 0xffffffffu / (unsigned)NC + 1u;
+  const unsigned mn = 0xffffffffu / (unsigned)n + 1u;
   for (int j0 = jb; j0 < je; j0 += kAsmChunk) {
     __syncthreads();
     for (int e = tid; e < kAsmChunk * kRZ * RU; e += blockDim.x) {
@@ -410,24 +410,28 @@ __global__ void __launch_bounds__(512) k_passemble(const __grid_constant__ PAsse
       Zk[e] = v;
     }
     __syncthreads();
-    // S^T[o][b][(i, a')] = sum_delta R[a'][delta] Z[b][i][delta]
-    for (int e = tid; e < kAsmChunk * kRZ * NC; e += blockDim.x) {
-      const unsigned qn = __umulhi((unsigned)e, mNC);  // e / NC, exact for e < 2^16
-      const int col = e - (int)qn * NC, b = (int)(qn & 7), o = (int)(qn >> 3);
+    // S^T[o][b][(i, a')] = sum_delta R[a'][delta] Z[b][i][delta]: a thread item is (o, (i, a'))
+    // for all eight b, R's row loaded once; both 8-float rows are 32-byte aligned (two 16-byte
+    // loads each) and a warp's lanes share i, so the Z rows are broadcasts
+    for (int e = tid; e < kAsmChunk * NC; e += blockDim.x) {
+      const int o = e / NC, col = e - o * NC;
       const int i = col / RU, ap = col % RU;
-      // both 8-float rows are 32-byte aligned: two 16-byte loads each
       const float4* rr = reinterpret_cast<const float4*>(Rk + (o * RU + ap) * kRZ);
-      const float4* zz = reinterpret_cast<const float4*>(Zk + ((o * kRZ + b) * n + i) * kRZ);
-      const float4 r0 = rr[0], r1 = rr[1], q0 = zz[0], q1 = zz[1];
-      float s = r0.x * q0.x;
-      s = fmaf(r0.y, q0.y, s);
-      s = fmaf(r0.z, q0.z, s);
-      s = fmaf(r0.w, q0.w, s);
-      s = fmaf(r1.x, q1.x, s);
-      s = fmaf(r1.y, q1.y, s);
-      s = fmaf(r1.z, q1.z, s);
-      s = fmaf(r1.w, q1.w, s);
-      ST[((size_t)o * kRZ + b) * NCP + col] = s;
+      const float4 r0 = rr[0], r1 = rr[1];
+#pragma unroll
+      for (int b = 0; b < kRZ; ++b) {
+        const float4* zz = reinterpret_cast<const float4*>(Zk + ((o * kRZ + b) * n + i) * kRZ);
+        const float4 q0 = zz[0], q1 = zz[1];
+        float s = r0.x * q0.x;
+        s = fmaf(r0.y, q0.y, s);
+        s = fmaf(r0.z, q0.z, s);
+        s = fmaf(r0.w, q0.w, s);
+        s = fmaf(r1.x, q1.x, s);
+        s = fmaf(r1.y, q1.y, s);
+        s = fmaf(r1.z, q1.z, s);
+        s = fmaf(r1.w, q1.w, s);
+        ST[((size_t)o * kRZ + b) * NCP + col] = s;
+      }
     }
     __syncthreads();
     if (tc * 16 < NC) {

@@ -240,6 +240,100 @@ static t3f_status launch_sweep(const TTV& A, const TTV& B, int dir, bool zip, fl
   return launch_status();
 }
 
+// Squared norms <A_a, A_a> (paper Section 4, 'norm'): one CTA per object, whole cores staged
+// in shared memory (the next core's copies in flight while the current one computes). Per core
+// every slice's T_i = M A_i is formed in one pass (n r0 r1 outputs, K = r0) and
+// M' = sum_i A_i^T T_i in a second (r1 x r1 outputs, K = n r0): two barrier intervals per
+// core instead of a slice-by-slice walk.
+struct SelfSweepArgs {
+  TTV A;
+  float* out;
+  int maxcore;  // floats of the largest core, rounded up to 4
+};
+
+template <typename ST>
+__global__ void __launch_bounds__(256) k_self_sweep(const __grid_constant__ SelfSweepArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const TTV& A = a.A;
+  const int obj = blockIdx.x, tid = threadIdx.x, nth = blockDim.x, d = A.d;
+  float* M = sm + 2 * a.maxcore;     // r0 x r0 (current partial)
+  float* T = M + A.rmax * A.rmax;    // [i][al][be]
+  const ST* Ap = static_cast<const ST*>(A.p);
+  auto stage = [&](int k) {
+    float* buf = sm + (k & 1) * a.maxcore;
+    const long long base = core_base(A, k, obj), sz = A.osz[k];
+    for (long long e = tid; e < sz; e += nth) {
+      if (sizeof(ST) == 4) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(buf + e);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(reinterpret_cast<const float*>(Ap) + base + e));
+      } else {
+        buf[e] = ldf<ST>(Ap, base + e);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  if (tid == 0) M[0] = 1.0f;
+  stage(0);
+  for (int k = 0; k < d; ++k) {
+    if (k + 1 < d) {
+      stage(k + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    const float* C = sm + (k & 1) * a.maxcore;  // A_k[al][i][be] at (al n + i) r1 + be
+    const int r0 = A.r[k], n = A.n[k], r1 = A.r[k + 1];
+    for (int e = tid; e < n * r0 * r1; e += nth) {
+      const int i = e / (r0 * r1), q = e - i * r0 * r1, al = q / r1, be = q - al * r1;
+      float acc = 0.0f;
+      for (int c = 0; c < r0; ++c) acc = fmaf(M[al * r0 + c], C[(c * n + i) * r1 + be], acc);
+      T[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < r1 * r1; e += nth) {
+      const int ap = e / r1, bp = e - ap * r1;
+      float acc = 0.0f;
+      for (int i = 0; i < n; ++i)
+        for (int al = 0; al < r0; ++al) acc = fmaf(C[(al * n + i) * r1 + ap], T[(i * r0 + al) * r1 + bp], acc);
+      M[e] = acc;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) a.out[obj] = M[0];
+}
+
+static size_t self_sweep_smem(const TTV& A, int* maxcore) {
+  long long mc = 0;
+  for (int k = 0; k < A.d; ++k) mc = std::max(mc, A.osz[k]);
+  mc = (mc + 3) & ~3LL;
+  *maxcore = (int)mc;
+  return sizeof(float) * (size_t)(3 * mc + (long long)A.rmax * A.rmax);
+}
+
+t3f_status run_self_sweep(const TTV& A, float* out, cudaStream_t s) {
+  SelfSweepArgs args;
+  args.A = A;
+  args.out = out;
+  const size_t smem = self_sweep_smem(A, &args.maxcore);
+  if (smem > 96 * 1024 || A.batch > 0x7fffffff) return run_zip_sweep(A, A, out, s);
+  if (A.batch == 0) return T3F_OK;
+  if (A.dtype == T3F_F32) {
+    auto kern = k_self_sweep<float>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<(unsigned)A.batch, 256, smem, s>>>(args);
+  } else if (A.dtype == T3F_BF16) {
+    auto kern = k_self_sweep<__nv_bfloat16>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return T3F_ERR_CUDA;
+    kern<<<(unsigned)A.batch, 256, smem, s>>>(args);
+  } else {
+    return T3F_ERR_DTYPE;
+  }
+  return launch_status();
+}
+
 t3f_status run_pair_sweep(const TTV& A, const TTV& B, int dir, float* out, float* store,
                           const long long* ioff, cudaStream_t s) {
   return launch_sweep(A, B, dir, false, out, store, ioff, s);

@@ -144,6 +144,8 @@ t3f_status run_pair_sweep(const TTV& A, const TTV& B, int dir, float* out, float
 
 // Diagonal pairs (a, a): out[a] = <A_a, B_a> (A and B of equal batch).
 t3f_status run_zip_sweep(const TTV& A, const TTV& B, float* out, cudaStream_t s);
+// <A_a, A_a> for every object: whole-core staging when the cores fit, else the zip sweep.
+t3f_status run_self_sweep(const TTV& A, float* out, cudaStream_t s);
 
 // Interface offsets for a partial store of bA*bB pairs; returns total floats.
 long long partial_offsets(const TTV& A, const TTV& B, long long pairs, long long* ioff);
