@@ -74,6 +74,9 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
   // B left, B right]; the products skip the 4 x 4 blocks and K steps beyond them (boundary
   // cores have rank 1 on their outer side)
   __shared__ int s_er[2][4];
+  // the same ranks unpadded: K loops stop there (the operands are zero beyond them, so the
+  // dropped terms are exact zeros)
+  __shared__ int s_ek[2][4];
   const int tid = threadIdx.x, nth = blockDim.x;
 
   for (int it = 0;; ++it) {
@@ -182,6 +185,8 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
         if (t == 0) {
           s_er[par][2 * side] = max(4, (m0 + 3) & ~3);
           s_er[par][2 * side + 1] = max(4, (m1 + 3) & ~3);
+          s_ek[par][2 * side] = max(1, m0);
+          s_ek[par][2 * side + 1] = max(1, m1);
         }
       }
     };
@@ -287,9 +292,10 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
       __syncthreads();
       const float* Asb = stg[cur];
       const float* Bsb = stg[cur] + szA;
-      const int eA0 = s_er[k & 1][0], eA1 = s_er[k & 1][1], eB0 = s_er[k & 1][2], eB1 = s_er[k & 1][3];
+      const int eA0 = s_er[k & 1][0], eA1 = s_er[k & 1][1], eB1 = s_er[k & 1][3];
+      const int kA0 = s_ek[k & 1][0], kB0 = s_ek[k & 1][2];
       // GEMM1: T[a][al][b][bp] = sum_be MT[b][be][a][al] Bs[b][be][bp]  (al < eA0, bp < eB1,
-      // be < eB0)
+      // be < kB0)
 #pragma unroll
       for (int q = 0; q < kGTMaxBlk; ++q) {
         if (g1m[q] < 0) continue;
@@ -301,7 +307,7 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
           for (int y = 0; y < 4; ++y) t4[x][y] = 0.0f;
         const float* mrow = MT + g1m[q];
         const float* brow = Bsb + (g1b[q] & 0xfffff);
-        for (int be = 0; be < eB0; ++be)
+        for (int be = 0; be < kB0; ++be)
           fma44(t4, *reinterpret_cast<const float4*>(mrow + be * mstep), *reinterpret_cast<const float4*>(brow + be * RB));
         const int unit = (g1b[q] >> 20) & 0xff;
         const int row0t = g1t[q] & 0xffff;
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
       }
       __syncthreads();
       // GEMM2: acc[a][ap][b][bp] += sum_al As[a][al][ap] T[a][al][b][bp]  (ap < eA1, bp < eB1,
-      // al < eA0)
+      // al < kA0)
 #pragma unroll
       for (int q = 0; q < kGTMaxBlk; ++q) {
         if (g2w[q] < 0) continue;
@@ -322,7 +328,7 @@ __global__ void __launch_bounds__(512) k_gram_tile(const __grid_constant__ GramT
         const float* arow = Asb + (g2a[q] & 0xfffff);
         const int unit = (g2a[q] >> 20) & 0xff;
         const int rbase = g2t[q] & 0xffff;
-        for (int al = 0; al < eA0; ++al) {
+        for (int al = 0; al < kA0; ++al) {
           const int r = rbase + al;
           fma44(acc[q], *reinterpret_cast<const float4*>(arow + al * RA),
                 *reinterpret_cast<const float4*>(TT + r * TR + 4 * (unit ^ ((r >> 2) & 7))));

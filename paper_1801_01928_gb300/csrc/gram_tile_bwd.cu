@@ -80,6 +80,9 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
   // B left, B right]; products skip the 4 x 4 blocks and K steps beyond them (boundary cores
   // have rank 1 on their outer side)
   __shared__ int s_er[2][4];
+  // the same ranks unpadded: K loops stop there (the operands are zero beyond them, so the
+  // dropped terms are exact zeros)
+  __shared__ int s_ek[2][4];
   const int tid = threadIdx.x, nth = blockDim.x;
   float* scr = g.scratch + (long long)blockIdx.x * g.scratch_stride;
   for (int it = 0;; ++it) {
@@ -212,6 +215,8 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         if (t == 0) {
           s_er[par][2 * side] = max(4, (m0 + 3) & ~3);
           s_er[par][2 * side + 1] = max(4, (m1 + 3) & ~3);
+          s_ek[par][2 * side] = max(1, m0);
+          s_ek[par][2 * side + 1] = max(1, m1);
         }
       }
     };
@@ -307,16 +312,17 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         __syncthreads();
         const float* As = Sg + cur * szS;  // [a][al][ap]
         const float* Bs = As + szA;        // [b][be][bp]
-        const int eA0 = s_er[k & 1][0], eA1 = s_er[k & 1][1], eB0 = s_er[k & 1][2], eB1 = s_er[k & 1][3];
+        const int eA0 = s_er[k & 1][0], eA1 = s_er[k & 1][1], eB1 = s_er[k & 1][3];
+        const int kA0 = s_ek[k & 1][0], kB0 = s_ek[k & 1][2];
         // T[a][al][b][bp] = sum_be M[a][al][b][be] B[b][be][bp]  (T in RT's storage; in split
-        // mode the second half of the be range goes to T1); al < eA0, bp < eB1, be < eB0
+        // mode the second half of the be range goes to T1); al < eA0, bp < eB1, be < kB0
         for (int blk = ks == 2 ? bb : tid; blk < nblk && hb < ks; blk += (ks == 2 ? nblk : nth)) {
           const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
           if (4 * qa >= eA0 || 4 * qb >= eB1) {
             if (ks == 2) break;
             continue;
           }
-          const int be0 = ks == 2 ? hb * (eB0 / 2) : 0, be1 = (ks == 2 && hb == 0) ? eB0 / 2 : eB0;
+          const int be0 = ks == 2 ? hb * (kB0 / 2) : 0, be1 = (ks == 2 && hb == 0) ? kB0 / 2 : kB0;
           float t4[4][4];
 #pragma unroll
           for (int x = 0; x < 4; ++x)
@@ -334,11 +340,11 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
           if (ks == 2) break;
         }
         __syncthreads();
-        // M'[a][ap][b][bp] += sum_al A[a][al][ap] T[a][al][b][bp]; ap < eA1, bp < eB1, al < eA0
+        // M'[a][ap][b][bp] += sum_al A[a][al][ap] T[a][al][b][bp]; ap < eA1, bp < eB1, al < kA0
         if (ks == 2) {
           const int dv = dP[bb], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
           if (hb < 2 && 4 * qa < eA1 && 4 * qb < eB1) {
-            const int al0 = hb * (eA0 / 2), al1 = hb == 0 ? eA0 / 2 : eA0;
+            const int al0 = hb * (kA0 / 2), al1 = hb == 0 ? kA0 / 2 : kA0;
             for (int al = al0; al < al1; ++al) {
               const size_t o = (((size_t)a * RA + al) * nb + b) * RB + 4 * qb;
               const float4 t0 = *reinterpret_cast<const float4*>(RT + o);
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             const int blk = tid + q * nth;
             if (blk < nblk) {
               const int dv = dP[blk], qb = dv >> 12, b = (dv >> 8) & 15, qa = (dv >> 4) & 15, a = dv & 15;
-              const int al1 = (4 * qa < eA1 && 4 * qb < eB1) ? eA0 : 0;
+              const int al1 = (4 * qa < eA1 && 4 * qb < eB1) ? kA0 : 0;
               for (int al = 0; al < al1; ++al)
                 fma44b(acc[q], *reinterpret_cast<const float4*>(As + ((size_t)a * RA + al) * RA + 4 * qa),
                        *reinterpret_cast<const float4*>(RT + (((size_t)a * RA + al) * nb + b) * RB + 4 * qb));
@@ -513,8 +519,9 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
         const float* AT = Sg + cur * szS;  // [a][ap][al]  (A_i transposed)
         const float* BT = AT + szA;        // [b][bp][be]  (B_i transposed)
         const int eA0 = s_er[k & 1][0], eA1 = s_er[k & 1][1], eB0 = s_er[k & 1][2], eB1 = s_er[k & 1][3];
-        // (1) X[a][al][b][bp] = sum_ap A[al][ap] R[ap][bp] (al < eA0, bp < eB1, ap < eA1);
-        //     Y'[b][be][a][ap] = g sum_bp B[be][bp] R[ap][bp] (be < eB0, ap < eA1, bp < eB1)
+        const int kA1 = s_ek[k & 1][1], kB1 = s_ek[k & 1][3];
+        // (1) X[a][al][b][bp] = sum_ap A[al][ap] R[ap][bp] (al < eA0, bp < eB1, ap < kA1);
+        //     Y'[b][be][a][ap] = g sum_bp B[be][bp] R[ap][bp] (be < eB0, ap < eA1, bp < kB1)
         const int nx = na * QA * nb * QB, ny = nb * QB * na * QA;
         for (int blk = tid; blk < nx + ny; blk += nth) {
           float t4[4][4];
@@ -527,7 +534,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             if (4 * qa >= eA0 || 4 * qb >= eB1) continue;
             const float* rr = Rm + (size_t)(a * nb + b) * PS + 4 * qb;  // + ap * RB
             const float* at = AT + (size_t)a * RA * RA + 4 * qa;        // + ap * RA
-            for (int ap = 0; ap < eA1; ++ap)
+            for (int ap = 0; ap < kA1; ++ap)
               fma44b(t4, *reinterpret_cast<const float4*>(at + ap * RA), *reinterpret_cast<const float4*>(rr + ap * RB));
 #pragma unroll
             for (int x = 0; x < 4; ++x)
@@ -546,7 +553,7 @@ __global__ void __launch_bounds__(512) k_gram_tile_bwd(const __grid_constant__ G
             if (4 * qb >= eB0 || 4 * qa >= eA1) continue;
             const float* rt = RT + (size_t)(a * nb + b) * PS + 4 * qa;  // + bp * RA
             const float* bt = BT + (size_t)b * RB * RB + 4 * qb;        // + bp * RB
-            for (int bp = 0; bp < eB1; ++bp)
+            for (int bp = 0; bp < kB1; ++bp)
               fma44b(t4, *reinterpret_cast<const float4*>(bt + bp * RB), *reinterpret_cast<const float4*>(rt + bp * RA));
             const float gg = gsm[a * nb + b];
 #pragma unroll
