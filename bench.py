@@ -261,10 +261,11 @@ class Workload:
         for k, v in self.host.items():
             self.devbuf[k].copy_(v, non_blocking=True)
 
-    # inputs in the order the step first reads them (the orthogonalisation chain's X5 group
-    # early, as its stream reaches orth5 after about a millisecond)
-    UPLOAD_GROUPS = (("X2", "idx", "y"), ("X5", "Z5", "c5"), ("A3", "B3", "dG"), ("Am", "xv", "dC"),
-                     ("X4", "dG4"))
+    # inputs in the order the step first reads them: the main stream takes the completion
+    # loss, then the uneven batch, then the Gram and matvec calls; the side stream reaches
+    # orth5 (the X5 group) after a few milliseconds, and dC (128 MB) is read last
+    UPLOAD_GROUPS = (("X2", "idx", "y"), ("X4", "dG4"), ("A3", "B3", "dG"), ("X5", "Z5", "c5"),
+                     ("Am", "xv", "dC"))
 
     def upload_async(self, copy_stream):
         """Every input copied from pinned host memory on `copy_stream`, one group at a time;
@@ -403,7 +404,7 @@ def op_graph_times(w, flush, stream):
     return out
 
 
-def run_step(w, timers=None, stream=None, side=None, ready=None):
+def run_step(w, timers=None, stream=None, side=None, ready=None, emit=None):
     """All hot-path operations once; returns the outputs a user reads back.
 
     With `side` (a second CUDA stream) the orthogonalisation chain (orth2 -> Riemannian
@@ -413,7 +414,10 @@ def run_step(w, timers=None, stream=None, side=None, ready=None):
     the other SMs take the independent work meanwhile. Without `side` every operation runs
     in order on the main stream (the per-operation timings come from that form). With
     `ready` (input name -> event of its host-to-device copy) each operation first waits for
-    the copies of its own inputs."""
+    the copies of its own inputs; with `emit` (name, tensor, stream) each result is handed
+    over as soon as the operation that writes it has been issued (for the read-back). The
+    uneven batch runs right after the completion loss, so the Gram and matvec calls that
+    follow it overlap the read-back of its gradient."""
     t3f, torch = w.t3f, w.torch
     out = {}
     main = stream if stream is not None else torch.cuda.current_stream(w.dev)
@@ -422,6 +426,11 @@ def run_step(w, timers=None, stream=None, side=None, ready=None):
         if ready is not None:
             for ev in {id(ready[k]): ready[k] for k in keys}.values():
                 st.wait_event(ev)
+
+    def give(st, **kv):
+        if emit is not None:
+            for k, v in kv.items():
+                emit(k, v, st)
 
     def timed(name, fn, st):
         if timers is not None:
@@ -445,11 +454,14 @@ def run_step(w, timers=None, stream=None, side=None, ready=None):
         need(st, "X2", "idx", "y")
         U2, V2 = timed("orth2", lambda: t3f.orthogonalize(X2), st)
         res["dU2"], _ = timed("rgrad", lambda: t3f.gather_backward(None, idx, y=y, riemannian=True, U=U2, V=V2), st)
+        give(st, dU2=res["dU2"].data)
         need(st, "X5", "Z5", "c5")
         U5, V5 = timed("orth5", lambda: t3f.orthogonalize(X5), st)
         res["dU5"] = timed("psum", lambda: t3f.project_sum(U5, V5, Z5, c5), st)
+        give(st, dU5=res["dU5"].data)
         # adjoint of 1/2 ||project_sum||^2: the cotangent of the coordinates is dU5 itself
         res["dZ"], res["dc"] = timed("psum_bwd", lambda: t3f.project_sum_backward(U5, V5, Z5, c5, res["dU5"]), st)
+        give(st, dc=res["dc"])
 
     if side is not None:
         side.wait_stream(main)
@@ -457,20 +469,25 @@ def run_step(w, timers=None, stream=None, side=None, ready=None):
             orth_chain(side)
     need(main, "X2", "idx", "y")
     dX, loss = timed("completion", lambda: t3f.gather_backward(X2, idx, y=y, want_loss=True), main)
+    give(main, loss=loss, dX=dX.data)
     if side is None:
         orth_chain(main)
+    need(main, "X4", "dG4")
+    timed("uneven", lambda: w.graph4f.replay(), main)
+    give(main, G4=w.G4, n4=w.n4)
+    timed("uneven_bwd", lambda: w.graph4b.replay(), main)
+    give(main, dX4=w.dX4)
     A3, B3 = w.tt("A3"), w.tt("B3")
     need(main, "A3", "B3", "dG")
     G = timed("gram", lambda: t3f.gram(A3, B3), main)
     dA, dB = timed("gram_bwd", lambda: t3f.gram_backward(A3, B3, w.devbuf["dG"]), main)
     nrm = timed("norm", lambda: t3f.norm(A3), main)
+    give(main, G=G, dA=dA.data, dB=dB.data, norm=nrm)
     Am, xv = w.tt("Am"), w.tt("xv")
     need(main, "Am", "xv", "dC")
     C = timed("matvec", lambda: t3f.matvec(Am, xv), main)
     dAm, dxv = timed("matvec_bwd", lambda: t3f.matvec_backward(Am, xv, w.tt("dC")), main)
-    need(main, "X4", "dG4")
-    timed("uneven", lambda: w.graph4f.replay(), main)
-    timed("uneven_bwd", lambda: w.graph4b.replay(), main)
+    give(main, dAm=dAm.data, dxv=dxv.data)
     if side is not None:
         main.wait_stream(side)
     out.update(loss=loss, dX=dX.data, dU2=res["dU2"].data, G=G, dA=dA.data, dB=dB.data, norm=nrm,
@@ -1185,8 +1202,25 @@ def gpu_arm(args):
     # per-operation device times (each operation replayed as its own CUDA graph)
     op_ms = op_graph_times(w, flush, stream)
 
-    # end-to-end: pinned host inputs copied in, results read back, every step
-    d2h = 0
+    # end-to-end: pinned host inputs copied in, results read back, every step. Each result is
+    # copied into pinned host memory on its own stream as soon as the operation writing it has
+    # been issued; the step ends when the last copy has landed. The pinned result buffers are
+    # sized by one untimed step.
+    d2h_stream = torch.cuda.Stream(dev)
+    copy_stream.wait_stream(stream)
+    out0 = run_step(w, None, stream, side, w.upload_async(copy_stream))
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out0.items() if k != "_bulk"}
+    del out0
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+
+    def emit(name, t, st):
+        ev = torch.cuda.Event()
+        ev.record(st)
+        d2h_stream.wait_event(ev)
+        t.record_stream(d2h_stream)
+        with torch.cuda.stream(d2h_stream):
+            host_out[name].copy_(t, non_blocking=True)
+
     e2e_ev = []
     barrier()
     torch.cuda.synchronize(dev)
@@ -1196,12 +1230,12 @@ def gpu_arm(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         copy_stream.wait_stream(stream)
+        d2h_stream.wait_stream(stream)
         ready = w.upload_async(copy_stream)
-        out = run_step(w, None, stream, side, ready)
-        host_out = {k: v.to("cpu", non_blocking=True) for k, v in out.items() if k != "_bulk"}
+        run_step(w, None, stream, side, ready, emit)
+        stream.wait_stream(d2h_stream)
         e1.record(stream)
         e2e_ev.append((e0, e1))
-        d2h = sum(v.numel() * v.element_size() for v in host_out.values())
     torch.cuda.synchronize(dev)
     barrier()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
