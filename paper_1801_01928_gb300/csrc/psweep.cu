@@ -281,15 +281,17 @@ __global__ void __launch_bounds__(512) k_psweep(const __grid_constant__ PSweepAr
         }
       }
       __syncthreads();
-      // accumulate step: Next[m][b] += sum_K As[K][m] T[K][b]
+      // accumulate step: Next[m][b] += sum_K As[K][m] T[K][b], K below the contracted X rank
+      // (r0 left, r1 right; the staged operands are zero beyond it)
       if (i < n) {
         const float* As = XsB + (size_t)h * RU * RU;
         const float* tb1 = T1 + ((size_t)ol * SP + h) * TS;
         const float* Bs1 = XsB + (size_t)(SP + h) * RU * RU;
         const float* Bs2 = XsB + (size_t)(2 * SP + h) * RU * RU;
         const float* tb2 = T2 + ((size_t)ol * SP + h) * TS;
+        const int kr = a.dir == 0 ? r0 : r1;
 #pragma unroll 4
-        for (int K = 0; K < RU; ++K) {
+        for (int K = 0; K < kr; ++K) {
           const float4 tv1 = *reinterpret_cast<const float4*>(tb1 + K * kRZ + 4 * qb);
           const float4 av = *reinterpret_cast<const float4*>(As + K * RU + 4 * qa);
           fma4x4(acc1, av, tv1);
@@ -555,8 +557,9 @@ __global__ void __launch_bounds__(RU == 32 ? 512 : 256) k_pgrad(const __grid_con
       const float* Us = Xs + (size_t)(2 * SP + h) * RU * RU;
       const float* Rm = RQ + (size_t)ol * 2 * TS;
       const float* Qm = Rm + TS;
+      // K below the X rank r1 (the staged slices and R, Q are zero beyond it)
 #pragma unroll 4
-      for (int K = 0; K < RU; ++K) {
+      for (int K = 0; K < r1; ++K) {
         const float4 rv = *reinterpret_cast<const float4*>(Rm + K * kRZ + 4 * qb);
         const float4 qv = *reinterpret_cast<const float4*>(Qm + K * kRZ + 4 * qb);
         fma4x4(x1, *reinterpret_cast<const float4*>(Vs + K * RU + 4 * qa), rv);
