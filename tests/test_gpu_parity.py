@@ -86,6 +86,22 @@ def test_norm(lib):
     assert rel_err(nrm, ref) < TOL["fp32"]
 
 
+def test_norm_dtypes_ranks_and_large_cores(lib):
+    # BF16-stored cores (exact in FP32 arithmetic), ranks that change from core to core, d = 1,
+    # and a core too large for whole-core staging (16 x 16 x 64: two copies and the slice
+    # products exceed the budget, so the slice-by-slice sweep takes the batch)
+    from tests._util import round_bf16
+    rng = np.random.default_rng(150)
+    cases = [(S.random_tt(rng, 9, [3, 5, 2, 4], [1, 6, 11, 3, 1], 0.4), torch.bfloat16, True),
+             (S.random_tt(rng, 5, [6], [1, 1], 1.0), torch.float32, False),
+             (S.random_tt(rng, 3, [16, 16, 16], [1, 16, 64, 1], 0.125), torch.float32, False)]
+    for A, dt, bf in cases:
+        A = round_bf16(A) if bf else round32(A)
+        nrm = lib.norm(dev_tt(lib, A, dt)).cpu().numpy()
+        ref = np.array([O.norm(a) for a in objects(A)])
+        assert rel_err(nrm, ref) < TOL["fp32"], (dt, len(A))
+
+
 def test_gram_backward(lib):
     rng = np.random.default_rng(102)
     n = [3, 4, 2, 3, 5]
