@@ -251,12 +251,25 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
             // same bucket: the b runs start at the a run, the diagonal tile covers its square
             for (size_t ib = (p == q ? ia : 0); ib < tb.size(); ++ib) {
               const int sym = (p == q && ib == ia) ? 0 : 1;
-              std::vector<std::pair<int, int>> todo{tb[ib]};
+              std::pair<int, int> brun = tb[ib];
+              bool merged = false;
+              // single objects on both sides (high ranks, where no 2 x 2 square fits): a 1 x 1
+              // tile fills at most half of the CTA's threads, so two neighbouring single b runs
+              // form one 1 x 2 tile when its blocks and shared memory fit (both pairs off the
+              // diagonal; the staging loop takes any number of rows per thread)
+              if (na == 1 && brun.second == 1 && sym == 1 && ib + 1 < tb.size() && tb[ib + 1].second == 1 &&
+                  (RA / 4) * 2 * (padr(brun.first, 2) / 4) <= 1024 &&
+                  gram_tile_smem(1, 2, RA, padr(brun.first, 2)) <= 200 * 1024) {
+                brun.second = 2;
+                merged = true;
+                ++ib;
+              }
+              std::vector<std::pair<int, int>> todo{brun};
               while (!todo.empty()) {
                 const int b0 = todo.back().first, nb = todo.back().second;
                 todo.pop_back();
                 const int RB = padr(b0, nb);
-                if (!tile_ok(na, nb, RA, RB)) {
+                if (!(merged && nb == 2) && !tile_ok(na, nb, RA, RB)) {
                   if (nb == 1) return T3F_ERR_UNSUPPORTED;
                   todo.push_back({b0 + nb / 2, nb - nb / 2});
                   todo.push_back({b0, nb / 2});
