@@ -261,10 +261,11 @@ class Workload:
         for k, v in self.host.items():
             self.devbuf[k].copy_(v, non_blocking=True)
 
-    # inputs in the order the step first reads them: the main stream takes the completion
-    # loss, then the uneven batch, then the Gram and matvec calls; the side stream reaches
-    # orth5 (the X5 group) after a few milliseconds, and dC (128 MB) is read last
-    UPLOAD_GROUPS = (("X2", "idx", "y"), ("X4", "dG4"), ("A3", "B3", "dG"), ("X5", "Z5", "c5"),
+    # inputs in the order the step first reads them: the main stream starts with the Gram
+    # matrix and norms (8 MB of inputs), then takes the completion loss, the uneven batch, the
+    # Gram adjoint and the matvec calls; the side stream reaches orth5 (the X5 group) after a
+    # few milliseconds, and dC (128 MB) is read last
+    UPLOAD_GROUPS = (("A3", "B3", "dG"), ("X2", "idx", "y"), ("X4", "dG4"), ("X5", "Z5", "c5"),
                      ("Am", "xv", "dC"))
 
     def upload_async(self, copy_stream):
@@ -416,8 +417,10 @@ def run_step(w, timers=None, stream=None, side=None, ready=None, emit=None):
     `ready` (input name -> event of its host-to-device copy) each operation first waits for
     the copies of its own inputs; with `emit` (name, tensor, stream) each result is handed
     over as soon as the operation that writes it has been issued (for the read-back). The
-    uneven batch runs right after the completion loss, so the Gram and matvec calls that
-    follow it overlap the read-back of its gradient."""
+    main stream starts with the Gram matrix and norms, whose inputs are small, while the
+    completion inputs are still being copied; the uneven batch runs after the completion loss,
+    so the Gram adjoint and matvec calls that follow it overlap the read-back of its
+    gradient."""
     t3f, torch = w.t3f, w.torch
     out = {}
     main = stream if stream is not None else torch.cuda.current_stream(w.dev)
@@ -467,6 +470,11 @@ def run_step(w, timers=None, stream=None, side=None, ready=None, emit=None):
         side.wait_stream(main)
         with torch.cuda.stream(side):
             orth_chain(side)
+    A3, B3 = w.tt("A3"), w.tt("B3")
+    need(main, "A3", "B3", "dG")
+    G = timed("gram", lambda: t3f.gram(A3, B3), main)
+    nrm = timed("norm", lambda: t3f.norm(A3), main)
+    give(main, G=G, norm=nrm)
     need(main, "X2", "idx", "y")
     dX, loss = timed("completion", lambda: t3f.gather_backward(X2, idx, y=y, want_loss=True), main)
     give(main, loss=loss, dX=dX.data)
@@ -477,12 +485,8 @@ def run_step(w, timers=None, stream=None, side=None, ready=None, emit=None):
     give(main, G4=w.G4, n4=w.n4)
     timed("uneven_bwd", lambda: w.graph4b.replay(), main)
     give(main, dX4=w.dX4)
-    A3, B3 = w.tt("A3"), w.tt("B3")
-    need(main, "A3", "B3", "dG")
-    G = timed("gram", lambda: t3f.gram(A3, B3), main)
     dA, dB = timed("gram_bwd", lambda: t3f.gram_backward(A3, B3, w.devbuf["dG"]), main)
-    nrm = timed("norm", lambda: t3f.norm(A3), main)
-    give(main, G=G, dA=dA.data, dB=dB.data, norm=nrm)
+    give(main, dA=dA.data, dB=dB.data)
     Am, xv = w.tt("Am"), w.tt("xv")
     need(main, "Am", "xv", "dC")
     C = timed("matvec", lambda: t3f.matvec(Am, xv), main)
