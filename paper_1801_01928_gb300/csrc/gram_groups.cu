@@ -250,18 +250,21 @@ t3f_status build_plan(const t3f_tt_ragged* X, int ngroups, const int* gstart, co
             const int a0 = ta[ia].first, na = ta[ia].second, RA = padr(a0, na);
             // same bucket: the b runs start at the a run, the diagonal tile covers its square
             for (size_t ib = (p == q ? ia : 0); ib < tb.size(); ++ib) {
-              const int sym = (p == q && ib == ia) ? 0 : 1;
+              int sym = (p == q && ib == ia) ? 0 : 1;
               std::pair<int, int> brun = tb[ib];
               bool merged = false;
               // single objects on both sides (high ranks, where no 2 x 2 square fits): a 1 x 1
               // tile fills at most half of the CTA's threads, so two neighbouring single b runs
-              // form one 1 x 2 tile when its blocks and shared memory fit (both pairs off the
-              // diagonal; the staging loop takes any number of rows per thread)
-              if (na == 1 && brun.second == 1 && sym == 1 && ib + 1 < tb.size() && tb[ib + 1].second == 1 &&
+              // form one 1 x 2 tile when its blocks and shared memory fit (the staging loop
+              // takes any number of rows per thread). The tile writes both G_ab and G_ba
+              // (sym = 1); an object's pair with itself may be the first of the two, its entry
+              // is then written twice with the same value.
+              if (na == 1 && brun.second == 1 && ib + 1 < tb.size() && tb[ib + 1].second == 1 &&
                   (RA / 4) * 2 * (padr(brun.first, 2) / 4) <= 1024 &&
                   gram_tile_smem(1, 2, RA, padr(brun.first, 2)) <= 200 * 1024) {
                 brun.second = 2;
                 merged = true;
+                sym = 1;
                 ++ib;
               }
               std::vector<std::pair<int, int>> todo{brun};
