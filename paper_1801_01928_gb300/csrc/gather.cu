@@ -626,24 +626,7 @@ static int gather_grid(long long N, int maxCtas) {
 }
 
 // SM count of the current device, looked up once per device index.
-static int num_sms() {
-  constexpr int kMaxDev = 64;
-  static std::atomic<int> cache[kMaxDev];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
-    cudaGetLastError();
-    return 152;
-  }
-  int sms = cache[dev].load(std::memory_order_relaxed);
-  if (sms <= 0) {
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
-      cudaGetLastError();
-      return 152;
-    }
-    cache[dev].store(sms, std::memory_order_relaxed);
-  }
-  return sms;
-}
+static int num_sms() { return device_sm_count(); }
 
 struct GatherLayout {
   int R;

@@ -8,10 +8,13 @@
 // the workspace once.
 // Forward (t3f_gram_groups): one persistent launch of the tiled sweep kernel whose CTAs
 // take tiles from the work list through an atomic counter, then the FP64 norms.
-// Adjoint (t3f_gram_groups_backward): one persistent launch of the tiled adjoint kernel over
-// a second work list of smaller tiles (the adjoint keeps seven partial tiles in shared
-// memory); off-diagonal tiles use the symmetrised cotangent g_ab + g_ba. Both calls only
-// enqueue memsets and kernels, so they can be captured in a CUDA graph after one prepare.
+// Adjoint (t3f_gram_groups_backward): two persistent launches of the tiled adjoint kernel over
+// work lists of smaller tiles (the adjoint keeps seven partial tiles in shared memory): tiles
+// that need more than half an SM on 512-thread CTAs, one per SM, then the rest on 256-thread
+// CTAs, two per SM; off-diagonal tiles use the symmetrised cotangent g_ab + g_ba. With a
+// tensor-core math the sweeps over the tile list and the (tile, core, side) gradient items
+// run instead. Every call only enqueues memsets and kernels, so it can be captured in a CUDA
+// graph after one prepare.
 #include <algorithm>
 #include <math.h>
 #include <vector>
@@ -53,15 +56,7 @@ constexpr int kMmaR[kBuckets] = {16, 16, 32, 64};  // tensor-core padded rank of
 const int kBucketMax[kBuckets] = {8, 16, 32, 64};
 const int kDefaultTiles[kBuckets] = {10, 6, 3, 1};
 
-int sm_count_gg() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
-  return sms;
-}
+int sm_count_gg() { return device_sm_count(); }
 
 struct Range {
   int begin, end, R;  // sorted positions [begin, end), padded inner rank

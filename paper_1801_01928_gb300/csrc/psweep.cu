@@ -613,16 +613,7 @@ bool psweep_supported(const TTV& X, const TTV& Z) {
   return pick_RU(X.rmax) != 0 && Z.rmax <= kRZ && Z.nmax <= 64;
 }
 
-static int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
-  return sms;
-}
+static int sm_count() { return device_sm_count(); }
 
 static void plan_tiles(int RU, int batch, int* J, int* SP) {
   const int G = (RU / 4) * (kRZ / 4);

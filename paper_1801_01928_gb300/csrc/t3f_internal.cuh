@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "t3f.h"
 
 namespace t3f {
@@ -45,6 +47,27 @@ __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p, long
 // Workspace header: the first 256 bytes of every workspace hold the device error word.
 constexpr size_t kWsHeader = 256;
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// SM count of the current device, looked up once per device index (152 when the lookup
+// fails; the pending runtime error is then cleared).
+inline int device_sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 152;
+  }
+  int sms = cache[dev].load(std::memory_order_relaxed);
+  if (sms <= 0) {
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+      cudaGetLastError();
+      return 152;
+    }
+    cache[dev].store(sms, std::memory_order_relaxed);
+  }
+  return sms;
+}
 
 // Gauge projection of one core on its m x r1 unfolding, staged in shared memory (paper
 // Section 3.2: out = Z - U (U^T Z), U with orthonormal columns): U and Z land with their
